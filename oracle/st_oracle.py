@@ -1,0 +1,611 @@
+"""FP64 CPU oracle for the space-time FE heat-conduction solve (arXiv 2508.09589).
+
+TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the CPU
+baseline leg of bench.py may import this module.  The product path (the CUDA
+library and its Python binding) never calls it and shares no code with it.
+
+Everything here is plain and slow on purpose: element integrals by Gauss
+quadrature of the weak form, global assembly into a scipy sparse matrix, a
+direct sparse solve, and sparse matrix products for the multigrid transfer
+and Galerkin operators.  Each function names the passage of the paper it
+follows.  Readings of points the paper leaves open are marked "Reading".
+
+Notation follows the paper: s (state, nodal temperatures), J (system matrix),
+f (source vector), Lambda (adjoint), gamma (design), C and k (capacity and
+conductivity by modified SIMP), tau (final time), Delta x, Delta t.
+
+Node numbering: C order over (t, [z,] y, x) with x fastest and time slowest.
+Element numbering: C order over (slab, [z,] y, x).  Local element node a has
+bits (a_t, [a_z,] a_y, a_x) with a_x the lowest bit.
+
+Parity status: every function below is pinned by a CPU test (tests/test_oracle_*.py);
+none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import itertools
+import math
+from dataclasses import dataclass, field
+from typing import Callable, List, Optional, Sequence, Tuple
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+
+# ----------------------------------------------------------------------------
+# Material interpolation (Sec. 2.2, modified SIMP equations)
+# ----------------------------------------------------------------------------
+@dataclass(frozen=True)
+class Material:
+    C_ins: float = 0.5
+    C_con: float = 1.0
+    k_ins: float = 0.03
+    k_con: float = 3.0
+    p_c: int = 2
+    p_k: int = 3
+
+
+def simp_C(m: Material, g):
+    """C(gamma) = C_ins + (C_con - C_ins) gamma^p_c."""
+    return m.C_ins + (m.C_con - m.C_ins) * g ** m.p_c
+
+
+def simp_k(m: Material, g):
+    """k(gamma) = k_ins + (k_con - k_ins) gamma^p_k."""
+    return m.k_ins + (m.k_con - m.k_ins) * g ** m.p_k
+
+
+def simp_dC(m: Material, g):
+    """dC/dgamma."""
+    return m.p_c * (m.C_con - m.C_ins) * g ** (m.p_c - 1)
+
+
+def simp_dk(m: Material, g):
+    """dk/dgamma."""
+    return m.p_k * (m.k_con - m.k_ins) * g ** (m.p_k - 1)
+
+
+# ----------------------------------------------------------------------------
+# Mesh (Sec. 3.1.2: regular cuboid mesh of trilinear space-time elements)
+# ----------------------------------------------------------------------------
+@dataclass(frozen=True)
+class Mesh:
+    ns: Tuple[int, ...]                 # spatial element counts, x first
+    nt: int                             # time element count
+    ext: Tuple[float, ...] = ()         # spatial extents (default unit length per axis)
+    tau: float = 1.0                    # final time
+    mat: Material = Material()
+    bc: str = "patch_left"              # patch_left | patch_bottom | all_walls | none
+    bc_width: float = 0.1               # patch width as a fraction of the edge length
+
+    def __post_init__(self):
+        if not self.ext:
+            object.__setattr__(self, "ext", tuple(1.0 for _ in self.ns))
+
+    @property
+    def sd(self) -> int:
+        return len(self.ns)
+
+    @property
+    def h(self) -> Tuple[float, ...]:
+        return tuple(e / n for e, n in zip(self.ext, self.ns))
+
+    @property
+    def dt(self) -> float:
+        return self.tau / self.nt
+
+    @property
+    def node_shape(self) -> Tuple[int, ...]:
+        return (self.nt + 1,) + tuple(n + 1 for n in reversed(self.ns))
+
+    @property
+    def elem_shape(self) -> Tuple[int, ...]:
+        return (self.nt,) + tuple(reversed(self.ns))
+
+    @property
+    def n_nodes(self) -> int:
+        return int(np.prod(self.node_shape))
+
+    @property
+    def n_elem(self) -> int:
+        return int(np.prod(self.elem_shape))
+
+    @property
+    def nv(self) -> int:
+        return 2 ** (self.sd + 1)
+
+
+def with_size(m: Mesh, ns: Sequence[int], nt: int, tau: Optional[float] = None) -> Mesh:
+    return Mesh(tuple(ns), nt, m.ext, m.tau if tau is None else tau, m.mat, m.bc, m.bc_width)
+
+
+def element_connectivity(m: Mesh) -> np.ndarray:
+    """conn[e, a] = global node of local node a of element e."""
+    shape = m.node_shape
+    strides = np.cumprod((1,) + tuple(reversed(shape[1:])))[::-1]  # C-order strides
+    eidx = np.indices(m.elem_shape).reshape(len(shape), -1)  # (axis, e)
+    conn = np.zeros((m.n_elem, m.nv), dtype=np.int64)
+    for a in range(m.nv):
+        # bit d of a (d = 0 is x) -> offset along spatial axis d; top bit -> time
+        off = [0] * len(shape)
+        off[0] = (a >> m.sd) & 1
+        for d in range(m.sd):
+            off[len(shape) - 1 - d] = (a >> d) & 1
+        idx = sum((eidx[ax] + off[ax]) * strides[ax] for ax in range(len(shape)))
+        conn[:, a] = idx
+    return conn
+
+
+def node_coords(m: Mesh) -> List[np.ndarray]:
+    """[t, (z,) y, x] coordinates of every node, each flattened in node order."""
+    grids = [np.arange(m.nt + 1) * m.dt] + [np.arange(n + 1) * hh for n, hh in
+                                              zip(reversed(m.ns), reversed(m.h))]
+    mesh = np.meshgrid(*grids, indexing="ij")
+    return [g.reshape(-1) for g in mesh]
+
+
+# ----------------------------------------------------------------------------
+# Dirichlet set.  Reading: T = 0 on the whole t = 0 plane (initial condition),
+# plus the spatial sink, applied at every time.  A patch of relative width w
+# centred on an edge (or face) contains node j of an axis with n elements iff
+# |2 j - n| <= w n (+1e-9), i.e. |x_j - L/2| <= w L / 2.
+# ----------------------------------------------------------------------------
+def _patch_mask_1d(n: int, width: float) -> np.ndarray:
+    j = np.arange(n + 1)
+    return np.abs(2 * j - n) <= width * n + 1e-9
+
+
+def dirichlet_mask(m: Mesh) -> np.ndarray:
+    """Boolean node mask, True where T is prescribed (= 0)."""
+    shape = m.node_shape
+    D = np.zeros(shape, dtype=bool)
+    D[0] = True  # t = 0 plane
+    sd = m.sd
+    # spatial axes in array order: axis 1 + (sd-1-d) holds spatial direction d
+    ax = lambda d: 1 + (sd - 1 - d)
+    if m.bc == "none":
+        pass
+    elif m.bc == "all_walls":
+        for d in range(sd):
+            sl = [slice(None)] * len(shape)
+            sl[ax(d)] = 0
+            D[tuple(sl)] = True
+            sl[ax(d)] = -1
+            D[tuple(sl)] = True
+    elif m.bc in ("patch_left", "patch_bottom"):
+        face_dir = 0 if m.bc == "patch_left" else 1
+        sel = np.ones(shape[1:], dtype=bool)
+        for d in range(sd):
+            a = ax(d) - 1
+            bshape = [1] * sd
+            bshape[a] = m.ns[d] + 1
+            if d == face_dir:
+                v = np.zeros(m.ns[d] + 1, dtype=bool)
+                v[0] = True
+            else:
+                v = _patch_mask_1d(m.ns[d], m.bc_width)
+            sel = sel & v.reshape(bshape)
+        D[:] |= sel[None]
+    else:
+        raise ValueError(m.bc)
+    return D.reshape(-1)
+
+
+# ----------------------------------------------------------------------------
+# Element matrices (Sec. 3.1.1 weak form with time artificial diffusion
+# k_ad = C dt / 2) by Gauss quadrature on one Delta x ... x Delta t brick.
+# ----------------------------------------------------------------------------
+def gauss_1d(n: int) -> Tuple[np.ndarray, np.ndarray]:
+    """Gauss-Legendre points and weights on [0, 1]."""
+    x, w = np.polynomial.legendre.leggauss(n)
+    return 0.5 * (x + 1.0), 0.5 * w
+
+
+def _basis_1d(xi):
+    """Linear 1D shape functions and derivatives on [0,1]: phi_0 = 1 - xi, phi_1 = xi."""
+    return (np.array([1.0 - xi, xi]), np.array([-1.0, 1.0]))
+
+
+def element_matrices(h: Sequence[float], dt: float, ngauss: int = 3):
+    """Unit-coefficient element matrices of the weak form.
+
+    Jc[a, b] = int N_a dN_b/dt + (dt/2) dN_a/dt dN_b/dt  (capacity part, C = 1,
+               including the stabilising time diffusion k_ad = C dt / 2)
+    Jk[a, b] = int sum_d dN_a/dx_d dN_b/dx_d             (conductivity part, k = 1)
+    Row index a is the test function, column b the trial function.
+    """
+    sd = len(h)
+    nv = 2 ** (sd + 1)
+    gp, gw = gauss_1d(ngauss)
+    sizes = list(h) + [dt]  # physical size per local axis: x, y, (z), t
+    Jc = np.zeros((nv, nv))
+    Jk = np.zeros((nv, nv))
+    for q in itertools.product(range(ngauss), repeat=sd + 1):
+        # q[d] for spatial d, q[sd] for time
+        wq = np.prod([gw[qi] * sizes[d] for d, qi in enumerate(q)])
+        N = np.ones(nv)
+        dN = np.ones((sd + 1, nv))  # physical derivatives
+        for a in range(nv):
+            for d in range(sd + 1):
+                bit = (a >> d) & 1
+                phi, dphi = _basis_1d(gp[q[d]])
+                N[a] *= phi[bit]
+                for dd in range(sd + 1):
+                    dN[dd, a] *= (dphi[bit] / sizes[d]) if dd == d else phi[bit]
+        dNt = dN[sd]
+        Jc += wq * (np.outer(N, dNt) + 0.5 * dt * np.outer(dNt, dNt))
+        for d in range(sd):
+            Jk += wq * np.outer(dN[d], dN[d])
+    return Jc, Jk
+
+
+# ----------------------------------------------------------------------------
+# Design -> per-element coefficients (Sec. 2.2.1: extruded or space-time design)
+# ----------------------------------------------------------------------------
+def element_gamma(m: Mesh, gamma: np.ndarray) -> np.ndarray:
+    """Per-element design, flattened in element order.  A design with the spatial
+    shape only is extruded along time (Sec. 3.4.1); a full shape is a space-time design."""
+    g = np.asarray(gamma)
+    sp_shape = tuple(reversed(m.ns))
+    if g.shape == sp_shape or g.size == int(np.prod(sp_shape)):
+        g = np.broadcast_to(g.reshape(sp_shape)[None], m.elem_shape)
+    return np.ascontiguousarray(g).reshape(-1)
+
+
+# ----------------------------------------------------------------------------
+# Assembly (Sec. 3.1.2) and the constrained system
+# ----------------------------------------------------------------------------
+def assemble_unconstrained(m: Mesh, gamma: np.ndarray, ngauss: int = 3) -> sp.csr_matrix:
+    """J = sum_e [C(gamma_e) Jc + k(gamma_e) Jk], no boundary conditions."""
+    ge = element_gamma(m, gamma)
+    C = simp_C(m.mat, ge)
+    k = simp_k(m.mat, ge)
+    Jc, Jk = element_matrices(m.h, m.dt, ngauss)
+    conn = element_connectivity(m)
+    nv = m.nv
+    rows = np.repeat(conn, nv, axis=1).reshape(-1)
+    cols = np.tile(conn, (1, nv)).reshape(-1)
+    vals = (C[:, None, None] * Jc[None] + k[:, None, None] * Jk[None]).reshape(-1)
+    return sp.csr_matrix((vals, (rows, cols)), shape=(m.n_nodes, m.n_nodes))
+
+
+def constrain(A: sp.spmatrix, dmask: np.ndarray) -> sp.csr_matrix:
+    """Rows and columns of prescribed nodes replaced by the identity:
+    A_bc = D A D + (I - D), D = diag(free)."""
+    free = (~dmask).astype(np.float64)
+    D = sp.diags(free)
+    return (D @ A @ D + sp.diags(1.0 - free)).tocsr()
+
+
+def assemble(m: Mesh, gamma: np.ndarray, ngauss: int = 3) -> sp.csr_matrix:
+    return constrain(assemble_unconstrained(m, gamma, ngauss), dirichlet_mask(m))
+
+
+# ----------------------------------------------------------------------------
+# Source vector f_i = int N_i Q dV (Sec. 3.1.2), zero at prescribed nodes.
+# Reading: the time integral uses 2-point Gauss per element; for sources that
+# are uniform in space the spatial integral is then exact.
+# ----------------------------------------------------------------------------
+def source_fn(kind: str, q0: float = 1.0, a: float = 1.0, b: float = 0.5, f: float = 4.0):
+    if kind == "uniform":
+        return lambda t, *x: q0 * np.ones_like(t)
+    if kind == "sin_t":
+        return lambda t, *x: q0 * (a + b * np.sin(2.0 * math.pi * f * t))
+    raise ValueError(kind)
+
+
+def assemble_source(m: Mesh, Q: Callable, nq: int = 2, constrained: bool = True) -> np.ndarray:
+    """f_a = sum_e int_e N_a Q dV by nq-point Gauss per axis.  Q(t, [z,] y, x)."""
+    sd = m.sd
+    gp, gw = gauss_1d(nq)
+    conn = element_connectivity(m)
+    eidx = np.indices(m.elem_shape).reshape(sd + 1, -1)  # (t, [z], y, x)
+    sizes = list(m.h) + [m.dt]
+    f = np.zeros(m.n_nodes)
+    for q in itertools.product(range(nq), repeat=sd + 1):
+        wq = np.prod([gw[qi] * sizes[d] for d, qi in enumerate(q)])
+        # physical coordinates of this quadrature point in every element
+        t = (eidx[0] + gp[q[sd]]) * m.dt
+        xs = [(eidx[sd - d] + gp[q[d]]) * m.h[d] for d in range(sd)]  # x, y, (z)
+        Qv = Q(t, *reversed(xs))
+        for a in range(m.nv):
+            Na = 1.0
+            for d in range(sd + 1):
+                bit = (a >> d) & 1
+                Na *= (1.0 - gp[q[d]]) if bit == 0 else gp[q[d]]
+            np.add.at(f, conn[:, a], wq * Na * Qv)
+    if constrained:
+        f[dirichlet_mask(m)] = 0.0
+    return f
+
+
+# ----------------------------------------------------------------------------
+# Direct solves (the plain definition of what the FGMRES + multigrid solve reaches)
+# ----------------------------------------------------------------------------
+def factor(A: sp.spmatrix):
+    """Sparse LU (SuperLU, minimum-degree ordering on A^T + A)."""
+    return spla.splu(sp.csc_matrix(A), permc_spec="MMD_AT_PLUS_A")
+
+
+def solve_direct(A: sp.spmatrix, b: np.ndarray, lu=None, transpose: bool = False) -> np.ndarray:
+    lu = factor(A) if lu is None else lu
+    return lu.solve(np.asarray(b), trans="T" if transpose else "N")
+
+
+def solve_block_tridiag_time(A: sp.spmatrix, b: np.ndarray, nt: int) -> np.ndarray:
+    """Direct solve by block elimination in time.  With time the slowest index the
+    matrix is block tridiagonal (the M_t coupling reaches one plane forward and one
+    back), so Gaussian elimination over the nt+1 plane blocks needs no fill outside them."""
+    import scipy.linalg as sl
+    A = sp.csr_matrix(A)
+    N = A.shape[0]
+    P = N // (nt + 1)
+    blk = lambda i, j: A[i * P:(i + 1) * P, j * P:(j + 1) * P]
+    lus, ys = [sl.lu_factor(blk(0, 0).toarray())], [np.array(b[:P], dtype=A.dtype)]
+    for n in range(1, nt + 1):
+        Lt = sl.lu_solve(lus[-1], blk(n, n - 1).T.toarray(), trans=1)
+        S = blk(n, n).toarray() - (blk(n - 1, n).T @ Lt).T
+        ys.append(b[n * P:(n + 1) * P] - Lt.T @ ys[-1])
+        lus.append(sl.lu_factor(S))
+    x = np.zeros(N, dtype=np.result_type(A.dtype, b.dtype))
+    x[nt * P:] = sl.lu_solve(lus[nt], ys[nt])
+    for n in range(nt - 1, -1, -1):
+        x[n * P:(n + 1) * P] = sl.lu_solve(lus[n], ys[n] - blk(n, n + 1) @ x[(n + 1) * P:(n + 2) * P])
+    return x
+
+
+def solve_dense(A: sp.spmatrix, b: np.ndarray) -> np.ndarray:
+    return np.linalg.solve(A.toarray(), b)
+
+
+@dataclass
+class Solution:
+    s: np.ndarray
+    f: np.ndarray
+    A: sp.csr_matrix
+    lu: object = None
+
+
+def forward(m: Mesh, gamma: np.ndarray, source: str = "uniform", q0: float = 1.0,
+            **src) -> Solution:
+    A = assemble(m, gamma)
+    f = assemble_source(m, source_fn(source, q0, **src))
+    lu = factor(A)
+    return Solution(solve_direct(A, f, lu), f, A, lu)
+
+
+# ----------------------------------------------------------------------------
+# Objectives and adjoint (Sec. 3.3.1 and 3.3.3)
+# ----------------------------------------------------------------------------
+def compliance(f: np.ndarray, s: np.ndarray) -> float:
+    """Thermal compliance phi = f^T s; d phi / d s = f^T."""
+    return float(f @ s)
+
+
+def pnorm(m: Mesh, s: np.ndarray, P: int = 20):
+    """phi = (sum_e T_avg,e^P)^(1/P) with T_avg,e the mean of the element's nodal
+    values, and its assembled gradient theta^((1-P)/P) T_avg,e^(P-1) / n_v per
+    element node (Sec. 3.3.3; n_v = 8 for (2+1)D elements)."""
+    conn = element_connectivity(m)
+    Tavg = s[conn].mean(axis=1)
+    theta = np.sum(Tavg ** P)
+    phi = theta ** (1.0 / P)
+    per_e = theta ** ((1.0 - P) / P) * Tavg ** (P - 1) / m.nv
+    g = np.zeros_like(s)
+    np.add.at(g, conn.reshape(-1), np.repeat(per_e, m.nv))
+    return float(phi), g
+
+
+def adjoint(A: sp.spmatrix, dphids: np.ndarray, dmask: np.ndarray, lu=None) -> np.ndarray:
+    """J^T Lambda = (d phi / d s)^T, with Lambda = 0 at prescribed nodes."""
+    rhs = np.where(dmask, 0.0, dphids)
+    return solve_direct(A, rhs, lu, transpose=True)
+
+
+def sensitivities(m: Mesh, gamma: np.ndarray, s: np.ndarray, lam: np.ndarray,
+                  extruded: Optional[bool] = None) -> np.ndarray:
+    """d phi / d gamma_e = - Lambda_e^T (dC/dgamma Jc + dk/dgamma Jk) s_e (Sec. 3.3.3;
+    f does not depend on the design).  For an extruded design the element
+    sensitivities are summed along time (transpose of the extrusion, Sec. 3.4.1)."""
+    ge = element_gamma(m, gamma)
+    dC = simp_dC(m.mat, ge)
+    dk = simp_dk(m.mat, ge)
+    Jc, Jk = element_matrices(m.h, m.dt)
+    conn = element_connectivity(m)
+    se = s[conn]
+    le = lam[conn]
+    g = -(dC * np.einsum("ea,ab,eb->e", le, Jc, se) + dk * np.einsum("ea,ab,eb->e", le, Jk, se))
+    g = g.reshape(m.elem_shape)
+    if extruded is None:
+        extruded = np.asarray(gamma).size == int(np.prod(m.ns))
+    if extruded:
+        return g.sum(axis=0)
+    return g
+
+
+# ----------------------------------------------------------------------------
+# Semi-coarsening hierarchy (Algorithm 1) with lambda_crit (Sec. 3.2.1)
+# ----------------------------------------------------------------------------
+@dataclass(frozen=True)
+class Level:
+    ns: Tuple[int, ...]
+    nt: int
+    h: Tuple[float, ...]
+    dt: float
+    to_next: str = ""  # "space" | "time" | "" (coarsest)
+
+    @property
+    def n_nodes(self) -> int:
+        n = self.nt + 1
+        for k in self.ns:
+            n *= k + 1
+        return n
+
+
+def d_eff(mat: Material) -> float:
+    """D_eff = sqrt(k_con k_ins / (C_con C_ins))."""
+    return math.sqrt(mat.k_con * mat.k_ins / (mat.C_con * mat.C_ins))
+
+
+def hierarchy(m: Mesh, lam_crit: float = 0.5, n_levels: Optional[int] = None,
+              coarse_cap: Optional[int] = None, mode: str = "semi") -> List[Level]:
+    """Algorithm 1.  lambda = D_eff dt / dx^2; lambda < lambda_crit -> coarsen time,
+    else coarsen space (all spatial axes).  Reading for unequal spatial sizes: dx is
+    the smallest spatial element size.  Stop after n_levels levels, or once the
+    level has at most coarse_cap nodes.  If the chosen axis cannot be halved
+    (odd count, or spatial count below 4 / time count below 2) the other is used;
+    if neither can, the hierarchy ends.  mode="full" halves space and time together."""
+    D = d_eff(m.mat)
+    ns, nt, h, dt = tuple(m.ns), m.nt, tuple(m.h), m.dt
+    levels = []
+    while True:
+        cur = Level(ns, nt, h, dt)
+        done = (n_levels is not None and len(levels) + 1 >= n_levels) or \
+               (coarse_cap is not None and cur.n_nodes <= coarse_cap)
+        can_s = all(n % 2 == 0 and n >= 4 for n in ns)
+        can_t = nt % 2 == 0 and nt >= 2
+        if mode == "full":
+            kind = "full" if (can_s and can_t) else ""
+        else:
+            lam = D * dt / min(h) ** 2
+            kind = "time" if lam < lam_crit else "space"
+            if kind == "time" and not can_t:
+                kind = "space" if can_s else ""
+            elif kind == "space" and not can_s:
+                kind = "time" if can_t else ""
+        if done or not kind:
+            levels.append(cur)
+            return levels
+        levels.append(Level(ns, nt, h, dt, kind))
+        if kind in ("space", "full"):
+            ns = tuple(n // 2 for n in ns)
+            h = tuple(2 * x for x in h)
+        if kind in ("time", "full"):
+            nt //= 2
+            dt *= 2
+
+
+# ----------------------------------------------------------------------------
+# Transfer operators and Galerkin coarse operators (Sec. 3.2, J_{l+1} = P^T J_l P)
+# ----------------------------------------------------------------------------
+def interp_1d(nc: int) -> sp.csr_matrix:
+    """Linear interpolation from nc+1 coarse nodes to 2nc+1 vertex-nested fine nodes."""
+    nf = 2 * nc
+    rows, cols, vals = [], [], []
+    for i in range(nf + 1):
+        if i % 2 == 0:
+            rows.append(i); cols.append(i // 2); vals.append(1.0)
+        else:
+            rows += [i, i]; cols += [i // 2, i // 2 + 1]; vals += [0.5, 0.5]
+    return sp.csr_matrix((vals, (rows, cols)), shape=(nf + 1, nc + 1))
+
+
+def prolongation(fine: Level, coarse: Level) -> sp.csr_matrix:
+    """Trilinear space-time interpolation P (fine x coarse), as a Kronecker product
+    over the axes (t, [z,] y, x).  Axes that are not coarsened use the identity."""
+    facs = []
+    if coarse.nt != fine.nt:
+        facs.append(interp_1d(coarse.nt))
+    else:
+        facs.append(sp.identity(fine.nt + 1, format="csr"))
+    for nf, nc in zip(reversed(fine.ns), reversed(coarse.ns)):
+        facs.append(interp_1d(nc) if nc != nf else sp.identity(nf + 1, format="csr"))
+    P = facs[0]
+    for F in facs[1:]:
+        P = sp.kron(P, F, format="csr")
+    return P
+
+
+def inject_mask(fine_mask: np.ndarray, fine: Level, coarse: Level) -> np.ndarray:
+    """Coarse prescribed set: coarse nodes whose coincident fine node is prescribed."""
+    shp = (fine.nt + 1,) + tuple(n + 1 for n in reversed(fine.ns))
+    M = fine_mask.reshape(shp)
+    sl = [slice(None, None, 2) if coarse.nt != fine.nt else slice(None)]
+    for nf, nc in zip(reversed(fine.ns), reversed(coarse.ns)):
+        sl.append(slice(None, None, 2) if nc != nf else slice(None))
+    return np.ascontiguousarray(M[tuple(sl)]).reshape(-1)
+
+
+def galerkin(A: sp.spmatrix, P: sp.spmatrix, fmask: np.ndarray, cmask: np.ndarray):
+    """Reading (Dirichlet in Galerkin): A_c = Pt^T A Pt + (I - D_c), with the
+    masked prolongation Pt = D_f P D_c, so prescribed nodes stay prescribed on
+    every level.  Returns (A_c, Pt)."""
+    Df = sp.diags((~fmask).astype(np.float64))
+    Dc = sp.diags((~cmask).astype(np.float64))
+    Pt = (Df @ P @ Dc).tocsr()
+    Ac = (Pt.T @ A @ Pt + sp.diags(cmask.astype(np.float64))).tocsr()
+    return Ac, Pt
+
+
+@dataclass
+class MGLevel:
+    level: Level
+    A: sp.csr_matrix
+    mask: np.ndarray
+    Pt: Optional[sp.csr_matrix] = None  # masked prolongation from the next coarser level
+
+
+def build_mg(m: Mesh, gamma: np.ndarray, levels: List[Level]) -> List[MGLevel]:
+    A0 = assemble(m, gamma)
+    mask0 = dirichlet_mask(m)
+    out = [MGLevel(levels[0], A0, mask0)]
+    for l in range(1, len(levels)):
+        fine, coarse = levels[l - 1], levels[l]
+        P = prolongation(fine, coarse)
+        cmask = inject_mask(out[-1].mask, fine, coarse)
+        Ac, Pt = galerkin(out[-1].A, P, out[-1].mask, cmask)
+        out[-1].Pt = Pt
+        out.append(MGLevel(coarse, Ac, cmask))
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Jacobi-preconditioned GMRES smoother and the V-cycle (Sec. 3.2).
+# Reading: right Jacobi preconditioning, exactly m iterations, no early exit
+# except an exact breakdown; pre-smoothing starts from zero, post-smoothing
+# from the current iterate; the coarsest level is solved directly.
+# ----------------------------------------------------------------------------
+def gmres_jacobi(A: sp.spmatrix, b: np.ndarray, x0: np.ndarray, m: int = 10,
+                 breakdown_tol: float = 0.0) -> np.ndarray:
+    """m steps of GMRES on A D^{-1} y = b - A x0, x = x0 + D^{-1} y (Arnoldi with
+    modified Gram-Schmidt, least squares by numpy.linalg.lstsq)."""
+    dinv = 1.0 / A.diagonal()
+    r = b - A @ x0
+    beta = np.linalg.norm(r)
+    if beta == 0.0:
+        return x0.copy()
+    n = b.size
+    V = np.zeros((m + 1, n))
+    H = np.zeros((m + 1, m))
+    V[0] = r / beta
+    k = m
+    for j in range(m):
+        w = A @ (dinv * V[j])
+        for i in range(j + 1):
+            H[i, j] = w @ V[i]
+            w = w - H[i, j] * V[i]
+        H[j + 1, j] = np.linalg.norm(w)
+        if H[j + 1, j] <= breakdown_tol * beta:
+            k = j + 1
+            break
+        V[j + 1] = w / H[j + 1, j]
+    e1 = np.zeros(k + 1)
+    e1[0] = beta
+    y = np.linalg.lstsq(H[: k + 1, :k], e1, rcond=None)[0]
+    return x0 + dinv * (V[:k].T @ y)
+
+
+def vcycle(mg: List[MGLevel], b: np.ndarray, l: int = 0, nsmooth: int = 10,
+           transpose: bool = False) -> np.ndarray:
+    """One V-cycle for A_l x = b (A_l^T for transpose=True, which uses the same
+    hierarchy since (P^T A P)^T = P^T A^T P)."""
+    A = mg[l].A.T.tocsr() if transpose else mg[l].A
+    if l == len(mg) - 1:
+        return np.linalg.solve(A.toarray(), b)
+    x = gmres_jacobi(A, b, np.zeros_like(b), nsmooth)
+    r = b - A @ x
+    Pt = mg[l].Pt
+    xc = vcycle(mg, Pt.T @ r, l + 1, nsmooth, transpose)
+    x = x + Pt @ xc
+    return gmres_jacobi(A, b, x, nsmooth)

@@ -1,0 +1,536 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: closed forms
+derived by hand, textbook 1D finite-element matrices combined by Kronecker
+products, brute-force integration of global hat functions, exact discrete
+solutions, conservation, convergence orders, the hierarchies printed in the
+paper, finite differences and complex-step derivatives.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import st_oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+UNITCAP = O.Material(C_ins=1.0, C_con=1.0, k_ins=1e-3, k_con=1.0, p_c=1, p_k=3)
+
+
+# ---------------------------------------------------------------- textbook 1D matrices
+def mass1(h):
+    return h / 6.0 * np.array([[2.0, 1.0], [1.0, 2.0]])
+
+
+def stiff1(h):
+    return np.array([[1.0, -1.0], [-1.0, 1.0]]) / h
+
+
+UPWIND = np.array([[0.0, 0.0], [-1.0, 1.0]])
+
+
+def kron_all(*ms):
+    out = ms[0]
+    for m in ms[1:]:
+        out = np.kron(out, m)
+    return out
+
+
+def glob_mass(n, h):
+    d = np.full(n + 1, 4.0); d[0] = d[-1] = 2.0
+    return sp.diags([np.full(n, 1.0), d, np.full(n, 1.0)], [-1, 0, 1]) * (h / 6.0)
+
+
+def glob_stiff(n, h):
+    d = np.full(n + 1, 2.0); d[0] = d[-1] = 1.0
+    return sp.diags([np.full(n, -1.0), d, np.full(n, -1.0)], [-1, 0, 1]) / h
+
+
+def glob_upwind(n):
+    d = np.ones(n + 1); d[0] = 0.0
+    return sp.diags([-np.ones(n), d], [-1, 0])
+
+
+def kron_spatial_mass_stiff(ns, hs):
+    """Global spatial mass and stiffness for Q1 on a tensor grid, axes (z, y, x)."""
+    Ms = [glob_mass(n, h) for n, h in zip(reversed(ns), reversed(hs))]
+    Ks = [glob_stiff(n, h) for n, h in zip(reversed(ns), reversed(hs))]
+    M = Ms[0]
+    for X in Ms[1:]:
+        M = sp.kron(M, X)
+    K = None
+    for d in range(len(ns)):
+        term = Ks[0] if d == 0 else Ms[0]
+        for e in range(1, len(ns)):
+            term = sp.kron(term, Ks[e] if e == d else Ms[e])
+        K = term if K is None else K + term
+    return M.tocsr(), K.tocsr()
+
+
+# ---------------------------------------------------------------- SIMP
+def test_simp_endpoints_and_derivatives():
+    m = O.Material(C_ins=0.5, C_con=1.0, k_ins=0.03, k_con=3.0, p_c=2, p_k=3)
+    assert O.simp_C(m, 0.0) == 0.5 and O.simp_C(m, 1.0) == 1.0
+    assert O.simp_k(m, 0.0) == 0.03 and O.simp_k(m, 1.0) == 3.0
+    g = np.linspace(0.05, 0.95, 7)
+    h = 1e-6
+    np.testing.assert_allclose(O.simp_dC(m, g), (O.simp_C(m, g + h) - O.simp_C(m, g - h)) / (2 * h), rtol=1e-8)
+    np.testing.assert_allclose(O.simp_dk(m, g), (O.simp_k(m, g + h) - O.simp_k(m, g - h)) / (2 * h), rtol=1e-8)
+    np.testing.assert_allclose(O.simp_k(m, 0.5), 0.03 + 2.97 * 0.125)
+
+
+# ---------------------------------------------------------------- P1 element closed form
+@pytest.mark.parametrize("h,dt", [((0.25, 0.25), 0.1), ((0.1, 0.3), 0.07), ((0.2, 0.5, 0.125), 0.3)])
+def test_element_matrices_kronecker_closed_form(h, dt):
+    """With k_ad = C dt / 2 the capacity part is exactly upwind (x) spatial mass and the
+    conductivity part is time mass (x) spatial stiffness."""
+    Jc, Jk = O.element_matrices(h, dt)
+    sd = len(h)
+    Ms = [mass1(x) for x in reversed(h)]
+    Ks = [stiff1(x) for x in reversed(h)]
+    Mx = kron_all(*Ms)
+    Kx = sum(kron_all(*[Ks[e] if e == d else Ms[e] for e in range(sd)]) for d in range(sd))
+    np.testing.assert_allclose(Jc, np.kron(UPWIND, Mx), atol=1e-15)
+    np.testing.assert_allclose(Jk, np.kron(mass1(dt), Kx), atol=1e-14)
+
+
+# ---------------------------------------------------------------- P2 exact discrete solution
+@pytest.mark.parametrize("ns,nt,spacetime", [((6, 4), 5, False), ((5, 7), 9, True), ((3, 4, 2), 4, False)])
+def test_exact_discrete_solution_insulated(ns, nt, spacetime):
+    """Uniform C and Q, any conductivity design, insulated sides, T = 0 at t = 0:
+    T_n = n Q dt / C for n < N_t and T_N = (N_t - 1/2) Q dt / C, uniform in space."""
+    C, Q = 2.0, 3.0
+    mat = O.Material(C_ins=C, C_con=C, k_ins=0.1, k_con=1.0, p_c=1, p_k=3)
+    m = O.Mesh(ns, nt, tau=1.3, mat=mat, bc="none")
+    rng = np.random.default_rng(0)
+    g = rng.random(m.elem_shape if spacetime else tuple(reversed(ns)))
+    sol = O.forward(m, g, "uniform", Q)
+    T = sol.s.reshape(m.node_shape)
+    expect = np.array([n * Q * m.dt / C for n in range(nt)] + [(nt - 0.5) * Q * m.dt / C])
+    for n in range(nt + 1):
+        np.testing.assert_allclose(T[n], expect[n], rtol=1e-11, atol=1e-13)
+
+
+# ---------------------------------------------------------------- P3 energy balance
+def test_energy_balance_reactions():
+    """Time-constant capacity: (sum of sink reactions) + (sum of f) = int C T(x, tau) dx."""
+    mat = O.Material(C_ins=0.5, C_con=1.0, k_ins=0.03, k_con=3.0, p_c=2, p_k=3)
+    m = O.Mesh((8, 6), 7, mat=mat, bc="patch_left", bc_width=0.4)
+    g = np.random.default_rng(1).random((6, 8))
+    A_unc = O.assemble_unconstrained(m, g)
+    sol = O.forward(m, g, "sin_t", 2.0)
+    f_unc = O.assemble_source(m, O.source_fn("sin_t", 2.0), constrained=False)
+    dmask = O.dirichlet_mask(m)
+    R = A_unc @ sol.s - f_unc
+    np.testing.assert_allclose(R[~dmask], 0.0, atol=1e-12)
+    lhs = R[dmask].sum() + f_unc.sum()
+    # int_Omega C(x) T_h(x, tau) dx with the bilinear interpolant of the last plane: each
+    # element integrates exactly to C_e * (area / 4) * (sum of its 4 corner values).
+    T = sol.s.reshape(m.node_shape)[-1]
+    C = O.simp_C(mat, g)
+    corner_sum = T[:-1, :-1] + T[1:, :-1] + T[:-1, 1:] + T[1:, 1:]
+    rhs = np.sum(C * corner_sum) * m.h[0] * m.h[1] / 4.0
+    np.testing.assert_allclose(lhs, rhs, rtol=1e-12)
+
+
+# ---------------------------------------------------------------- P4 Kronecker form + block elimination
+@pytest.mark.parametrize("ns,nt", [((5, 4), 6), ((3, 3, 2), 3)])
+def test_uniform_coefficient_kronecker_assembly_and_block_solve(ns, nt):
+    mat = O.Material(C_ins=0.7, C_con=0.7, k_ins=0.2, k_con=0.2, p_c=1, p_k=1)
+    m = O.Mesh(ns, nt, tau=0.8, mat=mat, bc="patch_bottom", bc_width=0.5)
+    g = np.full(tuple(reversed(ns)), 0.3)
+    A_unc = O.assemble_unconstrained(m, g)
+    Mx, Kx = kron_spatial_mass_stiff(ns, m.h)
+    J = 0.7 * sp.kron(glob_upwind(nt), Mx) + 0.2 * sp.kron(glob_mass(nt, m.dt), Kx)
+    np.testing.assert_allclose(A_unc.toarray(), J.toarray(), atol=1e-14)
+    A = O.assemble(m, g)
+    f = O.assemble_source(m, O.source_fn("uniform", 1.0))
+    x1 = O.solve_direct(A, f)
+    x2 = O.solve_block_tridiag_time(A, f, nt)
+    np.testing.assert_allclose(x1, x2, rtol=1e-12, atol=1e-14)
+
+
+# ---------------------------------------------------------------- P5 manufactured solutions
+def _mms_error(nx, nt, g, gp, k=0.7, C=1.3, planes=None):
+    mat = O.Material(C_ins=C, C_con=C, k_ins=k, k_con=k, p_c=1, p_k=1)
+    m = O.Mesh((nx, nx), nt, mat=mat, bc="all_walls")
+    Q = lambda t, y, x: (C * gp(t) + 2 * k * math.pi ** 2 * g(t)) * np.sin(math.pi * x) * np.sin(math.pi * y)
+    A = O.assemble(m, np.zeros((nx, nx)))
+    f = O.assemble_source(m, Q, nq=4)
+    s = O.solve_direct(A, f)
+    t, y, x = O.node_coords(m)
+    ex = g(t) * np.sin(math.pi * x) * np.sin(math.pi * y)
+    err = np.abs(s - ex).reshape(m.node_shape)
+    if planes is not None:
+        err = err[planes(nt)]
+    return err.max()
+
+
+def test_manufactured_first_order_in_time():
+    """Stabilised scheme: first order in time (Sec. 3.1.1)."""
+    e = [_mms_error(24, nt, lambda t: t ** 2, lambda t: 2 * t) for nt in (16, 32, 64)]
+    orders = [math.log2(e[i] / e[i + 1]) for i in range(2)]
+    assert orders[0] > 0.7 and 0.85 < orders[1] < 1.2, (e, orders)
+
+
+def test_manufactured_time_only_first_order():
+    """Spatially uniform solution T = sin(3t) on an insulated box: no spatial error, so the
+    nodal error is the time error alone and halves with dt."""
+    errs = []
+    for nt in (16, 32, 64, 128):
+        mat = O.Material(C_ins=1.7, C_con=1.7, k_ins=0.4, k_con=0.4, p_c=1, p_k=1)
+        m = O.Mesh((2, 2), nt, mat=mat, bc="none")
+        A = O.assemble(m, np.zeros((2, 2)))
+        f = O.assemble_source(m, lambda t, y, x: 1.7 * 3 * np.cos(3 * t), nq=5)
+        s = O.solve_direct(A, f)
+        t = O.node_coords(m)[0]
+        errs.append(np.abs(s - np.sin(3 * t)).max())
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(3)]
+    assert all(0.9 < p < 1.1 for p in orders), (errs, orders)
+
+
+def test_manufactured_second_order_in_space():
+    """For a solution linear in time the time discretisation is exact away from the
+    final plane (whose half step is felt a few planes back through the time mass),
+    leaving the Q1 spatial error O(dx^2) on the first quarter of the planes."""
+    e = [_mms_error(nx, 8, lambda t: t, lambda t: np.ones_like(t), planes=lambda nt: slice(0, nt // 4 + 1))
+         for nx in (8, 16, 32)]
+    orders = [math.log2(e[i] / e[i + 1]) for i in range(2)]
+    assert all(1.9 < p < 2.1 for p in orders), (e, orders)
+
+
+# ---------------------------------------------------------------- P6 implicit time stepping
+def test_difference_to_implicit_euler_is_first_order():
+    """For a time-constant design the all-at-once solution differs from backward Euler
+    with consistent mass on the same mesh by O(dt)."""
+    mat = O.Material(C_ins=0.5, C_con=1.0, k_ins=0.03, k_con=3.0, p_c=2, p_k=3)
+    ns = (8, 8)
+    g = np.random.default_rng(3).random((8, 8))
+    diffs = []
+    for nt in (8, 16, 32, 64):
+        m = O.Mesh(ns, nt, mat=mat, bc="patch_left", bc_width=0.3)
+        sol = O.forward(m, g, "uniform", 1.0)
+        # backward Euler, written independently: (C-mass + dt K) T_n = C-mass T_{n-1} + dt F
+        C = O.simp_C(mat, g)
+        k = O.simp_k(mat, g)
+        Mc = np.zeros((81, 81)); Kk = np.zeros((81, 81)); F = np.zeros(81)
+        h = m.h[0]
+        Me = np.kron(mass1(h), mass1(h)); Ke = np.kron(stiff1(h), mass1(h)) + np.kron(mass1(h), stiff1(h))
+        for ey in range(8):
+            for ex in range(8):
+                idx = [(ey + a // 2) * 9 + ex + a % 2 for a in range(4)]
+                Mc[np.ix_(idx, idx)] += C[ey, ex] * Me
+                Kk[np.ix_(idx, idx)] += k[ey, ex] * Ke
+                F[idx] += Me.sum(axis=1)
+        dm = O.dirichlet_mask(m).reshape(nt + 1, 81)[1]
+        T = np.zeros(81)
+        traj = [T]
+        Lhs = Mc + m.dt * Kk
+        Lhs[dm] = 0; Lhs[:, dm] = 0; Lhs[dm, dm] = 1
+        for n in range(nt):
+            r = Mc @ T + m.dt * F
+            r[dm] = 0
+            T = np.linalg.solve(Lhs, r)
+            traj.append(T)
+        traj = np.array(traj)
+        st = sol.s.reshape(nt + 1, 81)
+        diffs.append(np.abs(st[: nt] - traj[: nt]).max())  # last plane excluded (half step)
+    orders = [math.log2(diffs[i] / diffs[i + 1]) for i in range(3)]
+    assert orders[-1] > 0.8 and orders[-2] > 0.7, (diffs, orders)
+
+
+# ---------------------------------------------------------------- P7 brute force on tiny meshes
+def _hat(x, X, h):
+    return np.maximum(0.0, 1.0 - np.abs(x - X) / h)
+
+
+def _dhat(x, X, h):
+    inside = np.abs(x - X) < h
+    return np.where(inside, -np.sign(x - X) / h, 0.0)
+
+
+def _bruteforce_J(ns, nt, tau, mat, ge):
+    """a(N_j, N_i) by integrating global hat functions cell by cell (3-point Gauss),
+    without element connectivity or local numbering."""
+    nx, ny = ns
+    hx, hy, dt = 1.0 / nx, 1.0 / ny, tau / nt
+    nodes = [(n, j, i) for n in range(nt + 1) for j in range(ny + 1) for i in range(nx + 1)]
+    N = len(nodes)
+    X = np.array([[i * hx, j * hy, n * dt] for (n, j, i) in nodes])
+    gp, gw = O.gauss_1d(3)
+    J = np.zeros((N, N))
+    for en in range(nt):
+        for ey in range(ny):
+            for ex in range(nx):
+                C = O.simp_C(mat, ge[en, ey, ex]); k = O.simp_k(mat, ge[en, ey, ex])
+                for a in range(3):
+                    for b in range(3):
+                        for c in range(3):
+                            x = (ex + gp[a]) * hx; y = (ey + gp[b]) * hy; t = (en + gp[c]) * dt
+                            w = gw[a] * gw[b] * gw[c] * hx * hy * dt
+                            hxv = _hat(x, X[:, 0], hx); hyv = _hat(y, X[:, 1], hy); htv = _hat(t, X[:, 2], dt)
+                            Nv = hxv * hyv * htv
+                            Nx = _dhat(x, X[:, 0], hx) * hyv * htv
+                            Ny = hxv * _dhat(y, X[:, 1], hy) * htv
+                            Nt = hxv * hyv * _dhat(t, X[:, 2], dt)
+                            J += w * (C * np.outer(Nv, Nt) + 0.5 * C * dt * np.outer(Nt, Nt)
+                                      + k * (np.outer(Nx, Nx) + np.outer(Ny, Ny)))
+    return J
+
+
+def test_bruteforce_assembly_and_dense_solves():
+    mat = O.Material()
+    ns, nt = (2, 3), 2
+    m = O.Mesh(ns, nt, tau=0.7, mat=mat, bc="patch_left", bc_width=0.4)
+    ge = np.random.default_rng(5).random(m.elem_shape)
+    Jb = _bruteforce_J(ns, nt, 0.7, mat, ge)
+    A_unc = O.assemble_unconstrained(m, ge).toarray()
+    np.testing.assert_allclose(A_unc, Jb, atol=1e-13)
+    # constrained dense solve and dense adjoint versus the oracle's sparse direct solves
+    dm = O.dirichlet_mask(m)
+    Jd = Jb.copy(); Jd[dm] = 0; Jd[:, dm] = 0; Jd[dm, dm] = 1
+    f = O.assemble_source(m, O.source_fn("uniform", 1.0))
+    sol = O.forward(m, ge, "uniform", 1.0)
+    np.testing.assert_allclose(sol.s, np.linalg.solve(Jd, f), rtol=1e-12, atol=1e-14)
+    lam = O.adjoint(sol.A, f, dm, sol.lu)
+    np.testing.assert_allclose(lam, np.linalg.solve(Jd.T, f), rtol=1e-12, atol=1e-14)
+    # the patch on x = 0 with width 0.4 of a 3-element edge holds node j iff |2j - 3| <= 1.2
+    T = dm.reshape(m.node_shape)
+    assert T[0].all() and T[1:, 1, 0].all() and T[1:, 2, 0].all()
+    assert not T[1:, 0, 0].any() and not T[1:, 3, 0].any() and not T[1:, :, 1:].any()
+
+
+def test_patch_node_counts():
+    """Left-edge patch of width L/10: nodes 15..17 on a 32-element edge, 25 nodes at 256."""
+    for n, cnt in ((32, 3), (256, 25), (64, 7)):
+        m = O.Mesh((n, n), 1, bc="patch_left")
+        T = O.dirichlet_mask(m).reshape(m.node_shape)[1]
+        assert T.sum() == cnt and T[:, 0].sum() == cnt
+    m = O.Mesh((64, 64, 64), 1, bc="patch_left")
+    assert O.dirichlet_mask(m).reshape(m.node_shape)[1].sum() == 49
+
+
+# ---------------------------------------------------------------- P8 Algorithm 1 versus the paper
+def _read_golden_hierarchies():
+    rows = []
+    with open(os.path.join(GOLDEN, "paper_hierarchies.txt")) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            case, tau, matl, levels = [p.strip() for p in line.split("|")]
+            Ci, Cc, ki, kc = map(float, matl.split())
+            lev = [tuple(map(int, L.split("x"))) for L in levels.split()]
+            rows.append((case, float(tau), O.Material(Ci, Cc, ki, kc), lev))
+    return rows
+
+
+@pytest.mark.parametrize("case,tau,mat,levels", _read_golden_hierarchies())
+def test_algorithm1_reproduces_paper_tables(case, tau, mat, levels):
+    m = O.Mesh((640, 640), 1280, tau=tau, mat=mat)
+    got = O.hierarchy(m, lam_crit=0.5, n_levels=len(levels))
+    assert [(l.ns[0], l.ns[1], l.nt) for l in got] == levels
+
+
+def test_dof_counts_match_paper():
+    with open(os.path.join(GOLDEN, "paper_dof_counts.txt")) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            mesh, dofs, _ = [p.strip() for p in line.split("|")]
+            dims = list(map(int, mesh.split("x")))
+            if len(dims) == 3:
+                m = O.Mesh((dims[0], dims[1]), dims[2])
+                assert m.n_nodes == int(dofs)
+            else:
+                assert (dims[0] + 1) * (dims[1] + 1) == int(dofs)
+
+
+# ---------------------------------------------------------------- transfers and P9 Galerkin
+def test_prolongation_reproduces_affine_functions():
+    for fine, coarse in (((8, 6), 4), ((8, 6), 2)):
+        mf = O.Mesh(fine, 4)
+        levels = O.hierarchy(mf, n_levels=2)
+        L0 = O.Level((8, 6), 4, mf.h, mf.dt)
+        L1 = O.Level((4, 3), 4, tuple(2 * x for x in mf.h), mf.dt) if coarse == 4 else \
+            O.Level((8, 6), 2, mf.h, 2 * mf.dt)
+        P = O.prolongation(L0, L1)
+        aff = lambda t, y, x: 0.3 + 1.7 * x - 0.9 * y + 2.1 * t
+        cm = O.Mesh(L1.ns, L1.nt, tau=L1.dt * L1.nt)
+        fm = O.Mesh(L0.ns, L0.nt, tau=L0.dt * L0.nt)
+        np.testing.assert_allclose(P @ aff(*O.node_coords(cm)), aff(*O.node_coords(fm)), atol=1e-13)
+
+
+def _interior_rows(m, margin=2):
+    idx = np.indices(m.node_shape).reshape(len(m.node_shape), -1)
+    ok = np.ones(idx.shape[1], dtype=bool)
+    for ax, n in enumerate(m.node_shape):
+        ok &= (idx[ax] >= margin) & (idx[ax] <= n - 1 - margin)
+    return np.nonzero(ok)[0]
+
+
+@pytest.mark.parametrize("kind", ["space", "time"])
+def test_galerkin_equals_rediscretisation_for_uniform_coefficients(kind):
+    """Uniform coefficients: on interior rows P^T J P is the coarse Q1 operator; for time
+    coarsening its stabilising diffusion keeps the fine dt (k_ad = C dt_fine / 2)."""
+    C, k = 0.8, 0.35
+    mat = O.Material(C_ins=C, C_con=C, k_ins=k, k_con=k, p_c=1, p_k=1)
+    mf = O.Mesh((8, 8), 8, mat=mat, bc="none")
+    L0 = O.Level(mf.ns, mf.nt, mf.h, mf.dt)
+    if kind == "space":
+        L1 = O.Level((4, 4), 8, tuple(2 * x for x in mf.h), mf.dt)
+    else:
+        L1 = O.Level((8, 8), 4, mf.h, 2 * mf.dt)
+    mg = O.build_mg(mf, np.zeros((8, 8)), [L0, L1])
+    Ac = mg[1].A
+    mc = O.Mesh(L1.ns, L1.nt, tau=1.0, mat=mat, bc="none")
+    Mx, Kx = kron_spatial_mass_stiff(L1.ns, L1.h)
+    dt_c = L1.dt
+    # coarse time factors written from the 1D integrals on a 2 dt_f slab with k_ad = C dt_f / 2
+    Dt_el = np.array([[-0.5, 0.5], [-0.5, 0.5]]) + 0.5 * mf.dt / dt_c * np.array([[1.0, -1.0], [-1.0, 1.0]])
+    nt = L1.nt
+    Dg = sp.lil_matrix((nt + 1, nt + 1))
+    for s in range(nt):
+        for a in range(2):
+            for b in range(2):
+                Dg[s + a, s + b] += Dt_el[a, b]
+    Jc = C * sp.kron(Dg.tocsr(), Mx) + k * sp.kron(glob_mass(nt, dt_c), Kx)
+    rows = _interior_rows(mc)
+    np.testing.assert_allclose(Ac[rows].toarray(), Jc.tocsr()[rows].toarray(), atol=1e-13)
+
+
+# ---------------------------------------------------------------- adjoint and gradients
+def test_adjoint_duality():
+    m = O.Mesh((6, 5), 6, mat=O.Material(), bc="patch_left", bc_width=0.4)
+    g = np.random.default_rng(7).random((5, 6))
+    sol = O.forward(m, g, "uniform", 1.0)
+    dm = O.dirichlet_mask(m)
+    rng = np.random.default_rng(8)
+    c = rng.standard_normal(m.n_nodes); c[dm] = 0
+    lam = O.adjoint(sol.A, c, dm, sol.lu)
+    # c^T s = Lambda^T f for a linear functional of the state
+    np.testing.assert_allclose(c @ sol.s, lam @ sol.f, rtol=1e-12)
+
+
+@pytest.mark.parametrize("spacetime", [False, True])
+def test_compliance_gradient_complex_step_and_fd(spacetime):
+    mat = O.Material(C_ins=0.5, C_con=1.0, k_ins=0.03, k_con=3.0, p_c=2, p_k=3)
+    m = O.Mesh((4, 4), 4, mat=mat, bc="patch_left", bc_width=0.5)
+    rng = np.random.default_rng(11)
+    g = 0.2 + 0.6 * rng.random(m.elem_shape if spacetime else (4, 4))
+    sol = O.forward(m, g, "sin_t", 1.0)
+    dm = O.dirichlet_mask(m)
+    lam = O.adjoint(sol.A, sol.f, dm, sol.lu)
+    grad = O.sensitivities(m, g, sol.s, lam, extruded=not spacetime)
+    for flat in rng.choice(g.size, 5, replace=False):
+        idx = np.unravel_index(flat, g.shape)
+        gc = g.astype(complex)
+        gc[idx] += 1e-30j
+        A = O.assemble(m, gc)
+        s = O.solve_direct(A, sol.f.astype(complex))
+        cs = np.imag(sol.f @ s) / 1e-30
+        np.testing.assert_allclose(grad[idx], cs, rtol=1e-10)
+        gp, gm = g.copy(), g.copy()
+        gp[idx] += 1e-6; gm[idx] -= 1e-6
+        fd = (O.forward(m, gp, "sin_t", 1.0).s @ sol.f - O.forward(m, gm, "sin_t", 1.0).s @ sol.f) / 2e-6
+        np.testing.assert_allclose(grad[idx], fd, rtol=1e-6)
+
+
+def test_pnorm_value_and_gradient():
+    m = O.Mesh((3, 3), 3, bc="none")
+    s = np.random.default_rng(2).random(m.n_nodes)
+    P = 20
+    phi, g = O.pnorm(m, s, P)
+    # value from the definition, element by element with explicit loops
+    T = s.reshape(m.node_shape)
+    acc = 0.0
+    for n in range(3):
+        for j in range(3):
+            for i in range(3):
+                acc += T[n:n + 2, j:j + 2, i:i + 2].mean() ** P
+    np.testing.assert_allclose(phi, acc ** (1.0 / P), rtol=1e-13)
+    for k in (0, 17, 40, 63):
+        e = np.zeros_like(s); e[k] = 1e-4
+        fd = (O.pnorm(m, s + e, P)[0] - O.pnorm(m, s - e, P)[0]) / 2e-4
+        np.testing.assert_allclose(g[k], fd, rtol=1e-5, atol=1e-9 * np.abs(g).max())
+
+
+# ---------------------------------------------------------------- source quadrature reading
+def test_source_quadrature_two_point_gauss_error_is_third_order():
+    """2-point Gauss on a slab of width dt errs by dt^5 f^(4) / 4320 with f = N_a q; since
+    N_a' = O(1/dt) the nodal load error relative to the nodal measure is O(dt^3)."""
+    errs = []
+    for nt in (32, 64, 128):
+        m = O.Mesh((2, 2), nt, bc="none")
+        f2 = O.assemble_source(m, O.source_fn("sin_t", 1.0), nq=2, constrained=False)
+        f6 = O.assemble_source(m, O.source_fn("sin_t", 1.0), nq=6, constrained=False)
+        errs.append(np.abs(f2 - f6).max() / (m.dt * m.h[0] * m.h[1]))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(2.8 < p < 3.2 for p in orders), (errs, orders)
+
+
+def test_uniform_source_is_integral_of_hat_functions():
+    m = O.Mesh((4, 3), 5, tau=2.0, bc="none")
+    f = O.assemble_source(m, O.source_fn("uniform", 2.5), constrained=False).reshape(m.node_shape)
+    wx = np.full(5, m.h[0]); wx[[0, -1]] /= 2
+    wy = np.full(4, m.h[1]); wy[[0, -1]] /= 2
+    wt = np.full(6, m.dt); wt[[0, -1]] /= 2
+    np.testing.assert_allclose(f, 2.5 * wt[:, None, None] * wy[None, :, None] * wx[None, None, :], rtol=1e-13)
+
+
+# ---------------------------------------------------------------- smoother and V-cycle
+def test_gmres_smoother_minimises_residual_over_krylov_space():
+    m = O.Mesh((6, 6), 6, mat=O.Material(), bc="patch_left", bc_width=0.4)
+    g = np.random.default_rng(4).random((6, 6))
+    A = O.assemble(m, g)
+    rng = np.random.default_rng(9)
+    b = rng.standard_normal(m.n_nodes); b[O.dirichlet_mask(m)] = 0
+    x0 = rng.standard_normal(m.n_nodes) * 0.1
+    x = O.gmres_jacobi(A, b, x0, 10)
+    dinv = 1.0 / A.diagonal()
+    r0 = b - A @ x0
+    K = [r0]
+    for _ in range(9):
+        K.append(A @ (dinv * K[-1]))
+    K = np.array(K).T
+    K, _ = np.linalg.qr(K)
+    y = np.linalg.lstsq(A @ (dinv[:, None] * K), r0, rcond=None)[0]
+    xb = x0 + dinv * (K @ y)
+    np.testing.assert_allclose(np.linalg.norm(b - A @ x), np.linalg.norm(b - A @ xb), rtol=1e-8)
+    np.testing.assert_allclose(x, xb, rtol=1e-6, atol=1e-8 * np.abs(xb).max())
+
+
+def test_vcycle_is_a_contraction_and_exact_on_one_level():
+    mat = O.Material(C_ins=1.0, C_con=1.0, k_ins=1e-3, k_con=1.0, p_c=1, p_k=3)
+    m = O.Mesh((16, 16), 16, mat=mat)
+    g = np.random.default_rng(6).random((16, 16))
+    levels = O.hierarchy(m, coarse_cap=400)
+    assert len(levels) >= 3
+    mg = O.build_mg(m, g, levels)
+    f = O.assemble_source(m, O.source_fn("uniform"))
+    x = np.zeros_like(f)
+    res = [np.linalg.norm(f)]
+    for _ in range(4):
+        x = x + O.vcycle(mg, f - mg[0].A @ x)
+        res.append(np.linalg.norm(f - mg[0].A @ x))
+    assert all(res[i + 1] < 0.5 * res[i] for i in range(4)), res
+    one = O.build_mg(m, g, levels[:1])
+    np.testing.assert_allclose(O.vcycle(one, f), O.solve_direct(mg[0].A, f), rtol=1e-10, atol=1e-14)
+    # coarse prescribed sets are the geometric rule evaluated on the coarse grids
+    for l in range(1, len(levels)):
+        L = levels[l]
+        cm = O.Mesh(L.ns, L.nt, mat=mat)
+        np.testing.assert_array_equal(mg[l].mask, O.dirichlet_mask(cm))
+
+
+def test_sin_source_moments_match_closed_form():
+    """q(t) = 1 + 0.5 sin(2 pi 4 t) on [0, 1]: sum_i f_i = |Omega| int q dt = 1 and, since the
+    hat functions interpolate t exactly, sum_i t_i f_i = int t q dt = 1/2 - 1/(16 pi)."""
+    m = O.Mesh((3, 2), 64, bc="none")
+    f = O.assemble_source(m, O.source_fn("sin_t", 1.0), nq=6, constrained=False)
+    t = O.node_coords(m)[0]
+    np.testing.assert_allclose(f.sum(), 1.0, rtol=1e-12)
+    np.testing.assert_allclose(t @ f, 0.5 - 1.0 / (16.0 * math.pi), rtol=1e-10)
+    f2 = O.assemble_source(m, O.source_fn("sin_t", 1.0), nq=2, constrained=False)
+    np.testing.assert_allclose(t @ f2, 0.5 - 1.0 / (16.0 * math.pi), rtol=1e-5)
