@@ -1,0 +1,253 @@
+/*
+ * st.h -- C ABI of the GB300 space-time heat-conduction solver.
+ *
+ * The library solves the all-at-once system J s = f of the stabilised
+ * continuous-Galerkin space-time finite-element discretisation of transient
+ * heat conduction (arXiv 2508.09589, Sec. 3.1: weak form with time artificial
+ * diffusion k_ad = C dt / 2, trilinear elements on a regular space-time mesh,
+ * all nodal temperatures in one vector), with capacity C and conductivity k
+ * interpolated from a density design by modified SIMP (Sec. 2.2).  The solver
+ * is flexible GMRES (FP64) preconditioned by a space-time multigrid V-cycle
+ * with semi-coarsening by Algorithm 1, Galerkin coarse operators, trilinear
+ * transfers and Jacobi-GMRES smoothing (Sec. 3.2), run in FP32 ("mixed") or
+ * FP64.  The adjoint system J^T Lambda = (d phi/d s)^T and the per-element
+ * sensitivities of Sec. 3.3.3 use the same hierarchy.
+ *
+ * Conventions
+ *  - Every call returns st_status; 0 is success, negative values are errors.
+ *    No call aborts the process.  st_last_error() returns a message for the
+ *    last failure on the calling thread.
+ *  - Node arrays are ordered with x fastest and time slowest:
+ *    index = ((n * (nz+1) + k) * (ny+1) + j) * (nx+1) + i  (nz = 0 in 2D).
+ *  - Element arrays use the same order over element indices; an extruded
+ *    (time-constant) design holds only the spatial elements.
+ *  - Pointer arguments tagged with a `mem` argument are host pointers when
+ *    mem == ST_MEM_HOST and device pointers (on the mesh's device) when
+ *    mem == ST_MEM_DEVICE.  The caller always owns these buffers; the library
+ *    copies inputs and writes outputs, and never keeps the pointer.
+ *  - All device memory used by a mesh is owned by the mesh and released by
+ *    st_destroy_mesh.  Work is queued on the mesh's stream (st_set_stream);
+ *    calls that return host results synchronise that stream.
+ *  - A mesh must be used from one thread at a time.
+ */
+#ifndef ST_H
+#define ST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int st_status;
+#define ST_OK 0
+#define ST_ERR_ARG (-1)            /* invalid argument (size, kind, null pointer) */
+#define ST_ERR_OOM (-2)            /* device allocation failed */
+#define ST_ERR_NOT_CONVERGED (-3)  /* rtol not reached within max_it; best iterate kept */
+#define ST_ERR_NUMERIC (-4)        /* NaN/Inf or a zero pivot was detected */
+#define ST_ERR_TIMEOUT (-5)        /* a bounded wait gave up */
+#define ST_ERR_CUDA (-6)           /* a CUDA runtime call failed */
+#define ST_ERR_BUSY (-7)           /* request refused by admission control */
+#define ST_ERR_STATE (-8)          /* call out of order (e.g. solve before set_design) */
+#define ST_ERR_NOT_FOUND (-9)      /* unknown ticket */
+
+enum { ST_BC_PATCH_LEFT = 0, ST_BC_PATCH_BOTTOM = 1, ST_BC_ALL_WALLS = 2, ST_BC_NONE = 3 };
+enum { ST_DESIGN_EXTRUDED = 0, ST_DESIGN_SPACETIME = 1 };
+enum { ST_MEM_HOST = 0, ST_MEM_DEVICE = 1 };
+enum { ST_PREC_MIXED = 0, ST_PREC_FP64 = 1 };
+enum { ST_SRC_UNIFORM = 0, ST_SRC_SIN_T = 1 };
+enum { ST_OBJ_COMPLIANCE = 0, ST_OBJ_PNORM = 1 };
+enum { ST_STATE_T = 0, ST_STATE_LAMBDA = 1, ST_STATE_RHS = 2, ST_STATE_ADJ_RHS = 3 };
+enum { ST_COARSEN_SEMI = 0, ST_COARSEN_FULL = 1 };
+
+/* Modified SIMP (Sec. 2.2): C = C_ins + (C_con - C_ins) g^p_c, k = k_ins + (k_con - k_ins) g^p_k.
+ * Integer powers p_c, p_k >= 1. */
+typedef struct {
+    double C_ins, C_con, k_ins, k_con;
+    int p_c, p_k;
+} st_material;
+
+/* Mesh and hierarchy description (Sec. 3.1.2 mesh, Algorithm 1 coarsening). */
+typedef struct {
+    int ndim_space;          /* 2 or 3 spatial dimensions */
+    int n[3];                /* spatial element counts (x, y, z); n[2] ignored in 2D */
+    int n_t;                 /* time element count */
+    double ext[3];           /* spatial extents; element size h_d = ext[d] / n[d] */
+    double tau;              /* final time (rescaled, Sec. 2.1) */
+    st_material mat;
+    int bc;                  /* ST_BC_*: sink patch on x=0 (LEFT) or y=0 (BOTTOM), all walls, none.
+                                T = 0 on the t = 0 plane always (initial condition). */
+    double bc_width;         /* patch width as a fraction of the edge length (paper: 0.1) */
+    double lambda_crit;      /* Algorithm 1 threshold (paper: 0.5) */
+    long long coarse_dof_cap;/* coarsen until a level has at most this many nodes (<= 4096) */
+    int max_levels;          /* 0 = no limit */
+    int coarsening;          /* ST_COARSEN_SEMI (Algorithm 1) or ST_COARSEN_FULL (ablation) */
+    int device;              /* CUDA device ordinal */
+} st_mesh_desc;
+
+typedef struct {
+    int kind;                /* ST_SRC_UNIFORM: Q = q0; ST_SRC_SIN_T: Q = q0 (a + b sin(2 pi f t)) */
+    double q0, a, b, f;
+} st_source;
+
+typedef struct {
+    double rtol;             /* stop when ||f - J s||_2 <= rtol ||f||_2 (true residual) */
+    int max_it;              /* cap on outer iterations (all restarts together) */
+    int restart;             /* FGMRES restart length m (<= 32) */
+    int precision;           /* ST_PREC_MIXED: FP32 multigrid, or ST_PREC_FP64 */
+    int warm_start;          /* 1: start from the stored state (Sec. 3.2 warm start) */
+    int smooth_steps;        /* Jacobi-GMRES smoothing iterations per pre/post step (<= 16) */
+    int use_graphs;          /* 1: replay the V-cycle as a captured CUDA graph */
+} st_options;
+
+typedef struct {
+    int kind;                /* ST_OBJ_COMPLIANCE: phi = f^T s; ST_OBJ_PNORM: Sec. 3.3.1 p-norm */
+    int P;                   /* p-norm exponent (paper: 20) */
+} st_objective;
+
+typedef struct {
+    int outer_its;           /* FGMRES iterations (= V-cycles applied) */
+    int restarts;
+    int converged;
+    double rel_res;          /* true ||f - J s|| / ||f|| at exit */
+    double rel_res_est;      /* FGMRES estimate at exit */
+    double seconds;          /* wall time of the call */
+    double norm_f;
+} st_stats;
+
+typedef struct {
+    int n_levels;
+    long long n_nodes;       /* fine-level DOFs (Dirichlet nodes included) */
+    long long n_elem;
+    long long device_bytes;  /* device memory currently held by the mesh */
+} st_mesh_info;
+
+typedef struct {
+    int n[3];
+    int n_t;
+    long long n_nodes;
+    int to_next;             /* 0 space, 1 time, 2 full, -1 coarsest */
+    double h[3], dt;
+} st_level_info;
+
+typedef struct st_mesh st_mesh;
+
+const char* st_version(void);
+const char* st_last_error(void);
+void st_mesh_desc_default(st_mesh_desc* d);
+void st_options_default(st_options* o);
+
+/* Host-only: the multigrid hierarchy Algorithm 1 gives for d (no device work).  Writes up to
+ * max_out levels to out (finest first) and the level count to *n_levels. */
+st_status st_plan_hierarchy(const st_mesh_desc* d, st_level_info* out, int max_out, int* n_levels);
+
+/* Create a mesh: validates d, builds the hierarchy by Algorithm 1 (host) and
+ * allocates its device memory.  *out receives the handle. */
+st_status st_create_mesh(const st_mesh_desc* d, st_mesh** out);
+st_status st_destroy_mesh(st_mesh* m);
+st_status st_mesh_info_get(const st_mesh* m, st_mesh_info* info);
+st_status st_level_info_get(const st_mesh* m, int level, st_level_info* info);
+/* Queue the mesh's work on `stream` (a cudaStream_t; NULL = the mesh's own stream). */
+st_status st_set_stream(st_mesh* m, void* stream);
+st_status st_synchronize(st_mesh* m);
+
+/* Set the density design (Sec. 2.2.1).  layout ST_DESIGN_EXTRUDED: count = nx*ny(*nz),
+ * constant along time (Sec. 3.4.1); ST_DESIGN_SPACETIME: count = number of elements.
+ * Values are clipped to [0, 1].  Builds the Galerkin coarse operators (J_{l+1} = P^T J_l P,
+ * Sec. 3.2), the Jacobi diagonals and the inverse of the coarsest operator. */
+st_status st_set_design(st_mesh* m, const double* gamma, int layout, size_t count, int mem);
+
+/* Forward solve J s = f (Sec. 3.1.2) with f from `q` (2-point Gauss in time per element).
+ * ST_ERR_NOT_CONVERGED keeps the best iterate and fills stats. */
+st_status st_solve_forward(st_mesh* m, const st_source* q, const st_options* o, st_stats* stats);
+
+/* Objective phi (*phi_out) from the stored state and the adjoint solve J^T Lambda =
+ * (d phi / d s)^T (Sec. 3.3.3), Lambda = 0 at prescribed nodes.  Needs a forward solve. */
+st_status st_solve_adjoint(st_mesh* m, const st_objective* obj, const st_options* o,
+                           double* phi_out, st_stats* stats);
+
+/* Sensitivities d phi / d gamma_e = -Lambda_e^T (dJ_e / d gamma_e) s_e (Sec. 3.3.3); for
+ * an extruded design summed over time (transpose of the extrusion, Sec. 3.4.1).
+ * count must equal the design size. */
+st_status st_sensitivities(st_mesh* m, double* out, size_t count, int mem);
+
+/* Copy a stored node vector (ST_STATE_*) to `out` (count = fine DOFs). */
+st_status st_get_state(st_mesh* m, int which, double* out, size_t count, int mem);
+/* Overwrite the stored state s (e.g. an initial guess for a warm start). */
+st_status st_set_state(st_mesh* m, const double* s, size_t count, int mem);
+
+/* ---- Component entry points (used by the parity tests; same kernels as the solve) ----
+ * precision selects the multigrid copy: ST_PREC_MIXED -> float vectors (level 0 applies
+ * with the BF16 design), ST_PREC_FP64 -> double vectors.  level 0 with precision
+ * ST_PREC_FP64 is also the FP64 operator of the outer Krylov solver.  All vectors are
+ * device pointers of the level's node count. */
+st_status st_op_apply(st_mesh* m, int level, int precision, int transpose, const void* x, void* y);
+st_status st_op_diag(st_mesh* m, int level, int precision, void* d);
+/* r_c = P^T r_f (masked), from `level` to level + 1. */
+st_status st_restrict(st_mesh* m, int level, int precision, const void* r_f, void* r_c);
+/* x_f += P x_c (masked), from level + 1 to `level`. */
+st_status st_prolong(st_mesh* m, int level, int precision, const void* x_c, void* x_f);
+/* x <- `steps` Jacobi-GMRES iterations on A_level x = b starting from x (zero_init: from 0). */
+st_status st_smooth(st_mesh* m, int level, int precision, int transpose, const void* b, void* x,
+                    int steps, int zero_init);
+/* x = V-cycle(b) on level 0, i.e. one application of the preconditioner. */
+st_status st_vcycle(st_mesh* m, int precision, int transpose, const void* b, void* x);
+/* Export level `level` (>= 1) element matrices in FP64 block form: for each stored element,
+ * 4 blocks (a_t, b_t) in order 00, 01, 10, 11 of the packed upper triangle of the symmetric
+ * spatial block (row-major, i <= j).  Extruded designs store 2 versions (first slab, other
+ * slabs) per spatial element.  count is in doubles; host pointer. */
+st_status st_level_elements(st_mesh* m, int level, double* out, size_t count);
+/* Copy the FP64 inverse of the coarsest operator (n x n, row-major) to a host buffer. */
+st_status st_coarse_inverse(st_mesh* m, double* out, size_t count);
+
+/* ---- Serving: continuous batching of forward + adjoint + sensitivity requests ---- */
+typedef struct {
+    st_mesh_desc mesh;
+    const double* gamma;     /* host design, copied at submit */
+    int layout;
+    size_t count;
+    st_source source;
+    st_objective objective;
+    st_options options;
+    int want_gradient;       /* 1: keep the sensitivities for st_poll */
+} st_request;
+
+typedef struct {
+    st_status status;
+    double phi;
+    st_stats forward, adjoint;
+    double latency_s;        /* submit -> completion */
+    double queue_s;          /* submit -> admission */
+    long long footprint;     /* admitted device bytes */
+} st_result;
+
+typedef struct {
+    long long hbm_budget;    /* device bytes the server may hold for requests */
+    int max_inflight;        /* concurrent requests on the device (slots) */
+    int device;
+} st_server_desc;
+
+typedef struct st_server st_server;
+
+st_status st_server_create(const st_server_desc* d, st_server** out);
+/* Waits for in-flight requests, then releases everything. */
+st_status st_server_destroy(st_server* s);
+/* Queue a request; *ticket identifies it.  ST_ERR_BUSY if its footprint can never fit. */
+st_status st_submit(st_server* s, const st_request* r, uint64_t* ticket);
+/* *done = 1 once finished; out filled then.  grad (host, may be NULL) receives the
+ * sensitivities if requested (count = design size).  A finished ticket is released by the
+ * first st_poll that returns done = 1. */
+st_status st_poll(st_server* s, uint64_t ticket, st_result* out, double* grad, size_t count, int* done);
+/* Number of kernels this library has launched in the process so far (kernels inside
+ * replayed CUDA graphs included); a diagnostic for benchmarks. */
+long long st_kernel_launches(void);
+
+/* Device-memory estimate used by admission control for a mesh description. */
+long long st_footprint_bytes(const st_mesh_desc* d, int precision, int restart);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ST_H */

@@ -609,3 +609,49 @@ def vcycle(mg: List[MGLevel], b: np.ndarray, l: int = 0, nsmooth: int = 10,
     xc = vcycle(mg, Pt.T @ r, l + 1, nsmooth, transpose)
     x = x + Pt @ xc
     return gmres_jacobi(A, b, x, nsmooth)
+
+
+# ----------------------------------------------------------------------------
+# Single rows of the constrained system, for checks on meshes too large to assemble.
+# ----------------------------------------------------------------------------
+def apply_rows(m: Mesh, gamma: np.ndarray, x: np.ndarray, rows: np.ndarray) -> np.ndarray:
+    """(A x)_i for the listed nodes i, element by element: the sum over the elements that
+    contain node i of row a(i) of C_e Jc + k_e Jk applied to the element's (masked) values;
+    prescribed rows are the identity."""
+    sd = m.sd
+    shape = m.node_shape
+    dm = dirichlet_mask(m)
+    Jc, Jk = element_matrices(m.h, m.dt)
+    ge_shape = m.elem_shape
+    g = np.asarray(gamma)
+    extruded = g.size == int(np.prod(m.ns))
+    g = g.reshape(tuple(reversed(m.ns)) if extruded else ge_shape)
+    out = np.zeros(len(rows))
+    for r, node in enumerate(np.asarray(rows)):
+        if dm[node]:
+            out[r] = x[node]
+            continue
+        idx = np.unravel_index(node, shape)  # (t, [z], y, x)
+        acc = 0.0
+        for e_off in itertools.product((0, 1), repeat=sd + 1):  # element = node - 1 + offset
+            e = tuple(i - 1 + o for i, o in zip(idx, e_off))
+            if any(v < 0 or v >= n for v, n in zip(e, ge_shape)):
+                continue
+            gm = g[e[1:]] if extruded else g[e]
+            C, k = simp_C(m.mat, gm), simp_k(m.mat, gm)
+            # local index of the node inside element e: bit d of spatial d, top bit time
+            loc = [i - v for i, v in zip(idx, e)]
+            a = loc[0] << sd
+            for d in range(sd):
+                a |= loc[len(shape) - 1 - d] << d
+            for b in range(m.nv):
+                bi = [0] * len(shape)
+                bi[0] = e[0] + ((b >> sd) & 1)
+                for d in range(sd):
+                    bi[len(shape) - 1 - d] = e[len(shape) - 1 - d] + ((b >> d) & 1)
+                q = np.ravel_multi_index(tuple(bi), shape)
+                if dm[q]:
+                    continue
+                acc += (C * Jc[a, b] + k * Jk[a, b]) * x[q]
+        out[r] = acc
+    return out

@@ -1,0 +1,284 @@
+"""Python binding over the C ABI (argument marshalling only; every step runs in libst.so).
+
+Host inputs are numpy arrays; device inputs are CUDA torch tensors, passed by
+pointer.  Calls that hand device pointers to the library first synchronise the
+current torch stream, and the library synchronises its own stream before it
+returns from a component call, so no ordering hazard crosses the boundary.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Dict, Optional, Sequence
+
+import numpy as np
+
+from . import _lib as L
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _sync_torch(x=None):
+    if x is None or _is_torch(x):
+        try:
+            import torch
+            if torch.cuda.is_available():
+                torch.cuda.current_stream().synchronize()
+        except ImportError:
+            pass
+
+
+def _material(m: Optional[dict]) -> L.Material:
+    d = dict(C_ins=0.5, C_con=1.0, k_ins=0.03, k_con=3.0, p_c=2, p_k=3)
+    if m:
+        d.update(m)
+    return L.Material(float(d["C_ins"]), float(d["C_con"]), float(d["k_ins"]), float(d["k_con"]),
+                      int(d["p_c"]), int(d["p_k"]))
+
+
+def mesh_desc(ns: Sequence[int], nt: int, *, ext: Optional[Sequence[float]] = None, tau: float = 1.0,
+              material: Optional[dict] = None, bc: str = "patch_left", bc_width: float = 0.1,
+              lambda_crit: float = 0.5, coarse_dof_cap: int = 2000, max_levels: int = 0,
+              coarsening: str = "semi", device: int = 0) -> L.MeshDesc:
+    d = L.MeshDesc()
+    L.lib().st_mesh_desc_default(C.byref(d))
+    d.ndim_space = len(ns)
+    for q, v in enumerate(ns):
+        d.n[q] = int(v)
+    d.n_t = int(nt)
+    ext = list(ext) if ext else [1.0] * len(ns)
+    for q, v in enumerate(ext):
+        d.ext[q] = float(v)
+    d.tau = float(tau)
+    d.mat = _material(material)
+    d.bc = L.BC[bc]
+    d.bc_width = float(bc_width)
+    d.lambda_crit = float(lambda_crit)
+    d.coarse_dof_cap = int(coarse_dof_cap)
+    d.max_levels = int(max_levels)
+    d.coarsening = L.COARSEN[coarsening]
+    d.device = int(device)
+    return d
+
+
+def options(rtol: float = 1e-8, max_it: int = 200, restart: int = 30, precision: str = "mixed",
+            warm_start: bool = False, smooth_steps: int = 10, use_graphs: bool = True) -> L.Options:
+    o = L.Options()
+    L.lib().st_options_default(C.byref(o))
+    o.rtol = float(rtol)
+    o.max_it = int(max_it)
+    o.restart = int(restart)
+    o.precision = L.PREC[precision]
+    o.warm_start = int(bool(warm_start))
+    o.smooth_steps = int(smooth_steps)
+    o.use_graphs = int(bool(use_graphs))
+    return o
+
+
+def source(kind: str = "uniform", q0: float = 1.0, a: float = 1.0, b: float = 0.5, f: float = 4.0) -> L.Source:
+    return L.Source(L.SRC[kind], float(q0), float(a), float(b), float(f))
+
+
+class Mesh:
+    """One space-time problem on one GPU (st_create_mesh ... st_destroy_mesh)."""
+
+    def __init__(self, ns: Sequence[int], nt: int, **kw):
+        self.desc = mesh_desc(ns, nt, **kw)
+        self.ns = tuple(int(v) for v in ns)
+        self.nt = int(nt)
+        h = C.c_void_p()
+        L.check(L.lib().st_create_mesh(C.byref(self.desc), C.byref(h)), "st_create_mesh")
+        self._h = h
+        info = L.MeshInfo()
+        L.check(L.lib().st_mesh_info_get(self._h, C.byref(info)), "st_mesh_info_get")
+        self.n_levels = info.n_levels
+        self.n_nodes = info.n_nodes
+        self.n_elem = info.n_elem
+        self.layout = None
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            L.lib().st_destroy_mesh(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- info
+    @property
+    def node_shape(self):
+        return (self.nt + 1,) + tuple(n + 1 for n in reversed(self.ns))
+
+    @property
+    def device_bytes(self) -> int:
+        info = L.MeshInfo()
+        L.check(L.lib().st_mesh_info_get(self._h, C.byref(info)), "st_mesh_info_get")
+        return info.device_bytes
+
+    def levels(self):
+        out = []
+        for l in range(self.n_levels):
+            li = L.LevelInfo()
+            L.check(L.lib().st_level_info_get(self._h, l, C.byref(li)), "st_level_info_get")
+            sd = len(self.ns)
+            out.append(dict(ns=tuple(li.n[q] for q in range(sd)), nt=li.n_t, n_nodes=li.n_nodes,
+                            to_next={0: "space", 1: "time", 2: "full", -1: ""}[li.to_next],
+                            h=tuple(li.h[q] for q in range(sd)), dt=li.dt))
+        return out
+
+    def set_stream(self, stream_ptr: int = 0):
+        L.check(L.lib().st_set_stream(self._h, C.c_void_p(stream_ptr)), "st_set_stream")
+
+    def synchronize(self):
+        L.check(L.lib().st_synchronize(self._h), "st_synchronize")
+
+    # -- design and solves
+    def set_design(self, gamma, layout: Optional[str] = None):
+        sp = int(np.prod(self.ns))
+        if _is_torch(gamma):
+            assert gamma.is_cuda and gamma.dtype.__repr__().endswith("float64") and gamma.is_contiguous()
+            n = gamma.numel()
+            ptr, mem = gamma.data_ptr(), L.MEM_DEVICE
+            _sync_torch(gamma)
+        else:
+            arr = np.ascontiguousarray(np.asarray(gamma, dtype=np.float64))
+            n = arr.size
+            self._gkeep = arr
+            ptr, mem = arr.ctypes.data, L.MEM_HOST
+        if layout is None:
+            layout = "extruded" if n == sp else "spacetime"
+        L.check(L.lib().st_set_design(self._h, C.c_void_p(ptr), L.LAYOUT[layout], n, mem), "st_set_design")
+        self.layout = layout
+        self.design_size = n
+
+    def solve_forward(self, src: Optional[L.Source] = None, opts: Optional[L.Options] = None,
+                      allow_not_converged: bool = False, **kw) -> Dict:
+        src = src or source(**{k: v for k, v in kw.items() if k in ("kind", "q0", "a", "b", "f")})
+        opts = opts or options(**{k: v for k, v in kw.items() if k not in ("kind", "q0", "a", "b", "f")})
+        st = L.Stats()
+        code = L.lib().st_solve_forward(self._h, C.byref(src), C.byref(opts), C.byref(st))
+        L.check(code, "st_solve_forward", allow=(-3,) if allow_not_converged else ())
+        d = st.as_dict()
+        d["status"] = code
+        return d
+
+    def solve_adjoint(self, objective: str = "compliance", P: int = 20, opts: Optional[L.Options] = None,
+                      allow_not_converged: bool = False, **kw):
+        obj = L.Objective(L.OBJ[objective], int(P))
+        opts = opts or options(**kw)
+        st = L.Stats()
+        phi = C.c_double()
+        code = L.lib().st_solve_adjoint(self._h, C.byref(obj), C.byref(opts), C.byref(phi), C.byref(st))
+        L.check(code, "st_solve_adjoint", allow=(-3,) if allow_not_converged else ())
+        d = st.as_dict()
+        d["status"] = code
+        return phi.value, d
+
+    def sensitivities(self, out=None):
+        n = self.design_size
+        if out is not None and _is_torch(out):
+            _sync_torch(out)
+            L.check(L.lib().st_sensitivities(self._h, C.c_void_p(out.data_ptr()), n, L.MEM_DEVICE),
+                    "st_sensitivities")
+            return out
+        arr = np.empty(n, dtype=np.float64)
+        L.check(L.lib().st_sensitivities(self._h, C.c_void_p(arr.ctypes.data), n, L.MEM_HOST), "st_sensitivities")
+        return arr
+
+    def state(self, which: str = "T", out=None):
+        n = self.n_nodes
+        if out is not None and _is_torch(out):
+            _sync_torch(out)
+            L.check(L.lib().st_get_state(self._h, L.WHICH[which], C.c_void_p(out.data_ptr()), n, L.MEM_DEVICE),
+                    "st_get_state")
+            return out
+        arr = np.empty(n, dtype=np.float64)
+        L.check(L.lib().st_get_state(self._h, L.WHICH[which], C.c_void_p(arr.ctypes.data), n, L.MEM_HOST),
+                "st_get_state")
+        return arr
+
+    def set_state(self, s):
+        arr = np.ascontiguousarray(np.asarray(s, dtype=np.float64))
+        L.check(L.lib().st_set_state(self._h, C.c_void_p(arr.ctypes.data), arr.size, L.MEM_HOST), "st_set_state")
+
+    # -- component entry points (device tensors)
+    def _p(self, t):
+        assert _is_torch(t) and t.is_cuda and t.is_contiguous()
+        return C.c_void_p(t.data_ptr())
+
+    def apply(self, level: int, x, y, precision: str = "fp64", transpose: bool = False):
+        _sync_torch()
+        L.check(L.lib().st_op_apply(self._h, level, L.PREC[precision], int(transpose), self._p(x), self._p(y)),
+                "st_op_apply")
+        return y
+
+    def diag(self, level: int, d, precision: str = "fp64"):
+        _sync_torch()
+        L.check(L.lib().st_op_diag(self._h, level, L.PREC[precision], self._p(d)), "st_op_diag")
+        return d
+
+    def restrict(self, level: int, rf, rc, precision: str = "fp64"):
+        _sync_torch()
+        L.check(L.lib().st_restrict(self._h, level, L.PREC[precision], self._p(rf), self._p(rc)), "st_restrict")
+        return rc
+
+    def prolong(self, level: int, xc, xf, precision: str = "fp64"):
+        _sync_torch()
+        L.check(L.lib().st_prolong(self._h, level, L.PREC[precision], self._p(xc), self._p(xf)), "st_prolong")
+        return xf
+
+    def smooth(self, level: int, b, x, steps: int = 10, zero_init: bool = False, precision: str = "fp64",
+               transpose: bool = False):
+        _sync_torch()
+        L.check(L.lib().st_smooth(self._h, level, L.PREC[precision], int(transpose), self._p(b), self._p(x),
+                                  int(steps), int(zero_init)), "st_smooth")
+        return x
+
+    def vcycle(self, b, x, precision: str = "fp64", transpose: bool = False):
+        _sync_torch()
+        L.check(L.lib().st_vcycle(self._h, L.PREC[precision], int(transpose), self._p(b), self._p(x)), "st_vcycle")
+        return x
+
+    def level_elements(self, level: int) -> np.ndarray:
+        lv = self.levels()[level]
+        sd = len(self.ns)
+        nsym = (2 ** sd) * (2 ** sd + 1) // 2
+        sp = int(np.prod(lv["ns"]))
+        nstore = 2 * sp if self.layout == "extruded" else sp * lv["nt"]
+        out = np.empty(nstore * 4 * nsym, dtype=np.float64)
+        L.check(L.lib().st_level_elements(self._h, level, C.c_void_p(out.ctypes.data), out.size),
+                "st_level_elements")
+        return out.reshape(nstore, 4, nsym)
+
+    def coarse_inverse(self) -> np.ndarray:
+        n = self.levels()[-1]["n_nodes"]
+        out = np.empty(n * n, dtype=np.float64)
+        L.check(L.lib().st_coarse_inverse(self._h, C.c_void_p(out.ctypes.data), out.size), "st_coarse_inverse")
+        return out.reshape(n, n)
+
+
+def plan_hierarchy(ns, nt, **kw):
+    """Algorithm 1 levels for a mesh description (host only, no GPU needed)."""
+    d = mesh_desc(ns, nt, **kw)
+    arr = (L.LevelInfo * 64)()
+    n = C.c_int()
+    L.check(L.lib().st_plan_hierarchy(C.byref(d), arr, 64, C.byref(n)), "st_plan_hierarchy")
+    sd = len(ns)
+    return [dict(ns=tuple(arr[l].n[q] for q in range(sd)), nt=arr[l].n_t, n_nodes=arr[l].n_nodes,
+                 to_next={0: "space", 1: "time", 2: "full", -1: ""}[arr[l].to_next]) for l in range(n.value)]
+
+
+def footprint_bytes(ns, nt, precision: str = "mixed", restart: int = 30, **kw) -> int:
+    d = mesh_desc(ns, nt, **kw)
+    return int(L.lib().st_footprint_bytes(C.byref(d), L.PREC[precision], int(restart)))

@@ -1,0 +1,744 @@
+// Solve-phase kernels: operator applies, Jacobi diagonal, residual, multigrid
+// transfers, the Jacobi-GMRES smoother, the coarsest solve and the FP64 flexible
+// GMRES kernels (arXiv 2508.09589, Sec. 3.2).
+#include <math.h>
+
+#include <atomic>
+
+#include "st_device.cuh"
+
+namespace st {
+
+static std::atomic<long long> g_launches{0};
+
+void note_launch(cudaStream_t s, long long n) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) return;
+    g_launches += n;
+}
+
+void note_graph_launch(long long kernels) { g_launches += kernels; }
+
+long long kernel_launches() { return g_launches.load(); }
+
+LaunchCfg node_cfg(const Geom& g) {
+    LaunchCfg c;
+    c.block = dim3(32, 8, 1);
+    const int gx = (g.nx1 + 31) / 32, gy = (g.ny1 + 7) / 8;
+    const int planes = g.nz1 * g.nt1;
+    long long gz = (long long)kMaxBlocks / ((long long)gx * gy);
+    if (gz < 1) gz = 1;
+    if (gz > planes) gz = planes;
+    c.grid = dim3(gx, gy, (unsigned)gz);
+    return c;
+}
+
+// ---------------------------------------------------------------- applies
+template <int SD, typename T, int LV, bool TR>
+__global__ void __launch_bounds__(256) k_apply(OpL0<T> o0, OpLc<T> oc, const T* __restrict__ x, T* __restrict__ y) {
+    const Geom& g = LV == 0 ? o0.g : oc.g;
+    LoadPlain<T, T> ld{x};
+    ST_NODE_LOOP_BEGIN(g)
+    T v;
+    if (is_free<SD>(g, i_, j_, k_, n_))
+        v = op_row<SD, T, LV, TR>(o0, oc, i_, j_, k_, n_, ld);
+    else
+        v = x[idx_];
+    y[idx_] = v;
+    ST_NODE_LOOP_END
+}
+
+template <int SD, typename T, int LV>
+__global__ void __launch_bounds__(256) k_diag(OpL0<T> o0, OpLc<T> oc, T* __restrict__ d, int invert) {
+    const Geom& g = LV == 0 ? o0.g : oc.g;
+    ST_NODE_LOOP_BEGIN(g)
+    T v = T(1);
+    if (is_free<SD>(g, i_, j_, k_, n_)) {
+        if constexpr (LV == 0)
+            v = diag_l0<SD, T>(o0, i_, j_, k_, n_);
+        else
+            v = diag_lc<SD, T>(oc, i_, j_, k_, n_);
+    }
+    d[idx_] = invert ? T(1) / v : v;
+    ST_NODE_LOOP_END
+}
+
+template <int SD, typename T, int LV, bool TR>
+__global__ void __launch_bounds__(256) k_residual(OpL0<T> o0, OpLc<T> oc, const T* __restrict__ b,
+                                                  const T* __restrict__ x, T* __restrict__ r) {
+    const Geom& g = LV == 0 ? o0.g : oc.g;
+    LoadPlain<T, T> ld{x};
+    ST_NODE_LOOP_BEGIN(g)
+    T v;
+    if (is_free<SD>(g, i_, j_, k_, n_))
+        v = b[idx_] - op_row<SD, T, LV, TR>(o0, oc, i_, j_, k_, n_, ld);
+    else
+        v = b[idx_] - x[idx_];
+    r[idx_] = v;
+    ST_NODE_LOOP_END
+}
+
+// ---------------------------------------------------------------- transfers
+// kind: 0 = space (all spatial axes halved), 1 = time, 2 = both.
+// Restriction r_c = D_c P^T D_f r_f (P trilinear, vertex nested).
+template <int SD, typename T>
+__global__ void __launch_bounds__(256) k_restrict(Geom gf, Geom gc, int kind, const T* __restrict__ rf,
+                                                  T* __restrict__ rc) {
+    const bool cs = kind != 1, ct = kind != 0;
+    ST_NODE_LOOP_BEGIN(gc)
+    T acc = 0;
+    if (is_free<SD>(gc, i_, j_, k_, n_)) {
+        const int I = cs ? 2 * i_ : i_, J = cs ? 2 * j_ : j_, K = (cs && SD == 3) ? 2 * k_ : k_;
+        const int N = ct ? 2 * n_ : n_;
+        const int rs = cs ? 1 : 0, rt = ct ? 1 : 0, rz = (cs && SD == 3) ? 1 : 0;
+        for (int dn = -rt; dn <= rt; ++dn) {
+            const int fn = N + dn;
+            if (fn < 0 || fn >= gf.nt1) continue;
+            const T wn = dn == 0 ? T(1) : T(0.5);
+            for (int dk = -rz; dk <= rz; ++dk) {
+                const int fk = K + dk;
+                if (fk < 0 || fk >= gf.nz1) continue;
+                const T wk = dk == 0 ? T(1) : T(0.5);
+                for (int dj = -rs; dj <= rs; ++dj) {
+                    const int fj = J + dj;
+                    if (fj < 0 || fj >= gf.ny1) continue;
+                    const T wj = dj == 0 ? T(1) : T(0.5);
+                    for (int di = -rs; di <= rs; ++di) {
+                        const int fi = I + di;
+                        if (fi < 0 || fi >= gf.nx1) continue;
+                        if (!is_free<SD>(gf, fi, fj, fk, fn)) continue;
+                        const T wi = di == 0 ? T(1) : T(0.5);
+                        acc += wn * wk * wj * wi * rf[(((long long)fn * gf.nz1 + fk) * gf.ny1 + fj) * gf.nx1 + fi];
+                    }
+                }
+            }
+        }
+    }
+    rc[idx_] = acc;
+    ST_NODE_LOOP_END
+}
+
+// Prolongation x_f += D_f P D_c x_c.
+template <int SD, typename T>
+__global__ void __launch_bounds__(256) k_prolong(Geom gf, Geom gc, int kind, const T* __restrict__ xc,
+                                                 T* __restrict__ xf) {
+    const bool cs = kind != 1, ct = kind != 0;
+    ST_NODE_LOOP_BEGIN(gf)
+    if (is_free<SD>(gf, i_, j_, k_, n_)) {
+        int lo[4], hi[4];
+        const int f[4] = {i_, j_, k_, n_};
+        const bool c[4] = {cs, cs, cs && SD == 3, ct};
+        for (int d = 0; d < 4; ++d) {
+            if (c[d]) {
+                lo[d] = f[d] >> 1;
+                hi[d] = (f[d] + 1) >> 1;
+            } else {
+                lo[d] = hi[d] = f[d];
+            }
+        }
+        T acc = 0;
+        for (int cn = lo[3]; cn <= hi[3]; ++cn) {
+            const T wn = lo[3] == hi[3] ? T(1) : T(0.5);
+            for (int ck = lo[2]; ck <= hi[2]; ++ck) {
+                const T wk = lo[2] == hi[2] ? T(1) : T(0.5);
+                for (int cj = lo[1]; cj <= hi[1]; ++cj) {
+                    const T wj = lo[1] == hi[1] ? T(1) : T(0.5);
+                    for (int ci = lo[0]; ci <= hi[0]; ++ci) {
+                        if (!is_free<SD>(gc, ci, cj, ck, cn)) continue;
+                        const T wi = lo[0] == hi[0] ? T(1) : T(0.5);
+                        acc += wn * wk * wj * wi * xc[(((long long)cn * gc.nz1 + ck) * gc.ny1 + cj) * gc.nx1 + ci];
+                    }
+                }
+            }
+        }
+        xf[idx_] += acc;
+    }
+    ST_NODE_LOOP_END
+}
+
+// ---------------------------------------------------------------- Jacobi-GMRES smoother
+// Right-preconditioned GMRES on A D^{-1} y = b - A x0, x = x0 + D^{-1} y, with the
+// basis kept unnormalised (u_j) and scales s_j = 1 / ||u_j|| (classical Gram-Schmidt,
+// one reduction per step); Givens rotations are applied as columns arrive.
+__device__ void sm_givens_column(SmState* st, int j) {
+    double* H = st->H;
+    double col[kMaxSmooth + 1];
+    for (int q = 0; q <= j + 1; ++q) col[q] = H[q * kMaxSmooth + j];
+    for (int q = 0; q < j; ++q) {
+        const double c = st->cs[q], s = st->sn[q];
+        const double a = col[q], b = col[q + 1];
+        col[q] = c * a + s * b;
+        col[q + 1] = -s * a + c * b;
+    }
+    const double a = col[j], b = col[j + 1];
+    const double r = hypot(a, b);
+    const double c = r > 0 ? a / r : 1.0, s = r > 0 ? b / r : 0.0;
+    st->cs[j] = c;
+    st->sn[j] = s;
+    col[j] = r;
+    col[j + 1] = 0;
+    st->g[j + 1] = -s * st->g[j];
+    st->g[j] = c * st->g[j];
+    for (int q = 0; q <= j + 1; ++q) st->R[q * kMaxSmooth + j] = col[q];
+}
+
+__device__ void sm_backsolve(SmState* st, int k) {
+    double y[kMaxSmooth];
+    for (int q = k - 1; q >= 0; --q) {
+        double a = st->g[q];
+        for (int l = q + 1; l < k; ++l) a -= st->R[q * kMaxSmooth + l] * y[l];
+        const double d = st->R[q * kMaxSmooth + q];
+        y[q] = d != 0 ? a / d : 0.0;
+    }
+    for (int q = 0; q < kMaxSmooth; ++q) st->coef[q] = q < k ? y[q] * st->s[q] : 0.0;
+}
+
+template <int SD, typename T, int LV, bool TR, bool ZERO>
+__global__ void __launch_bounds__(256) k_sm_start(OpL0<T> o0, OpLc<T> oc, const T* __restrict__ b,
+                                                  const T* __restrict__ x, T* __restrict__ u0, int steps,
+                                                  SmState* st, RedBuf rb) {
+    const Geom& g = LV == 0 ? o0.g : oc.g;
+    LoadPlain<T, T> ld{x};
+    double acc[1] = {0.0};
+    ST_NODE_LOOP_BEGIN(g)
+    T r;
+    if (ZERO) {
+        r = b[idx_];
+    } else {
+        if (is_free<SD>(g, i_, j_, k_, n_))
+            r = b[idx_] - op_row<SD, T, LV, TR>(o0, oc, i_, j_, k_, n_, ld);
+        else
+            r = b[idx_] - x[idx_];
+        u0[idx_] = r;
+    }
+    acc[0] += (double)r * (double)r;
+    ST_NODE_LOOP_END
+    __shared__ double out[1];
+    if (reduce_publish<1>(acc, 1, rb, out)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            const double beta = sqrt(out[0]);
+            st->beta = beta;
+            st->stop = !(beta > 0.0 && isfinite(beta));
+            st->s[0] = st->stop ? 0.0 : 1.0 / beta;
+            st->kdim = steps;
+            st->g[0] = beta;
+            for (int q = 0; q < kMaxSmooth; ++q) st->coef[q] = 0.0;
+        }
+    }
+}
+
+template <int SD, typename T, int LV, bool TR>
+__global__ void __launch_bounds__(256) k_sm_apply(OpL0<T> o0, OpLc<T> oc, const T* __restrict__ dinv,
+                                                  Basis<T> U, T* __restrict__ w, int j, SmState* st,
+                                                  RedBuf rb) {
+    if (st->stop || j >= st->kdim) return;
+    const Geom& g = LV == 0 ? o0.g : oc.g;
+    LoadScaled<T> ld{U.u[j], dinv};
+    double acc[kMaxSmooth] = {0.0};
+    ST_NODE_LOOP_BEGIN(g)
+    T v;
+    if (is_free<SD>(g, i_, j_, k_, n_))
+        v = op_row<SD, T, LV, TR>(o0, oc, i_, j_, k_, n_, ld);
+    else
+        v = ld(idx_);
+    w[idx_] = v;
+#pragma unroll
+    for (int q = 0; q < kMaxSmooth; ++q)
+        if (q <= j) acc[q] += (double)v * (double)U.u[q][idx_];
+    ST_NODE_LOOP_END
+    __shared__ double out[kMaxSmooth];
+    if (reduce_publish<kMaxSmooth>(acc, j + 1, rb, out)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            for (int q = 0; q <= j; ++q) st->H[q * kMaxSmooth + j] = st->s[q] * st->s[j] * out[q];
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sm_update(Geom g, Basis<T> U, const T* __restrict__ w, int j, int steps,
+                                                   SmState* st, RedBuf rb) {
+    if (st->stop || j >= st->kdim) return;
+    __shared__ T cf[kMaxSmooth];
+    __shared__ T sj;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    if (tid <= j) cf[tid] = (T)(st->H[tid * kMaxSmooth + j] * st->s[tid]);
+    if (tid == 0) sj = (T)st->s[j];
+    __syncthreads();
+    T* un = U.u[j + 1];
+    double acc[1] = {0.0};
+    ST_NODE_LOOP_BEGIN(g)
+    T v = sj * w[idx_];
+#pragma unroll
+    for (int q = 0; q < kMaxSmooth; ++q)
+        if (q <= j) v -= cf[q] * U.u[q][idx_];
+    un[idx_] = v;
+    acc[0] += (double)v * (double)v;
+    ST_NODE_LOOP_END
+    __shared__ double out[1];
+    if (reduce_publish<1>(acc, 1, rb, out)) {
+        if (tid == 0) {
+            const double h = sqrt(out[0]);
+            st->H[(j + 1) * kMaxSmooth + j] = h;
+            sm_givens_column(st, j);
+            const bool brk = !(h > 1e-13 * st->beta) || !isfinite(h);
+            if (brk) {
+                st->kdim = j + 1;
+            } else {
+                st->s[j + 1] = 1.0 / h;
+            }
+            if (brk || j + 1 == steps) sm_backsolve(st, j + 1);
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sm_finish(Geom g, T* __restrict__ x, const T* __restrict__ dinv,
+                                                   Basis<T> U, int zero_init, SmState* st) {
+    __shared__ T cf[kMaxSmooth];
+    __shared__ int kd;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    if (tid == 0) kd = st->stop ? 0 : st->kdim;
+    if (tid < kMaxSmooth) cf[tid] = st->stop ? T(0) : (T)st->coef[tid];
+    __syncthreads();
+    const int k = kd;
+    ST_NODE_LOOP_BEGIN(g)
+    T v = 0;
+    for (int q = 0; q < k; ++q) v += cf[q] * U.u[q][idx_];
+    v *= dinv[idx_];
+    x[idx_] = zero_init ? v : x[idx_] + v;
+    ST_NODE_LOOP_END
+}
+
+// ---------------------------------------------------------------- coarsest solve
+template <typename T>
+__global__ void k_coarse_gemv(const double* __restrict__ Ainv, int n, const T* __restrict__ b, T* __restrict__ x) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const double* row = Ainv + (long long)warp * n;
+    double a = 0;
+    for (int c = lane; c < n; c += 32) a += row[c] * (double)b[c];
+#pragma unroll
+    for (int off = 16; off; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+    if (lane == 0) x[warp] = (T)a;
+}
+
+template <typename T>
+__global__ void k_coarse_gemv_t(const double* __restrict__ Ainv, int n, const T* __restrict__ b, T* __restrict__ x) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    double a = 0;
+    for (int c = 0; c < n; ++c) a += Ainv[(long long)c * n + r] * (double)b[c];
+    x[r] = (T)a;
+}
+
+// ---------------------------------------------------------------- FGMRES (FP64)
+struct VPtrs {
+    double* v[kMaxRestart + 1];
+};
+
+template <typename TZ>
+struct ZPtrs {
+    TZ* z[kMaxRestart];
+};
+
+__device__ void fg_givens_column(FgState* fs, int j) {
+    double* H = fs->H;
+    for (int q = 0; q < j; ++q) {
+        const double c = fs->cs[q], s = fs->sn[q];
+        const double a = H[q * kMaxRestart + j], b = H[(q + 1) * kMaxRestart + j];
+        H[q * kMaxRestart + j] = c * a + s * b;
+        H[(q + 1) * kMaxRestart + j] = -s * a + c * b;
+    }
+    const double a = H[j * kMaxRestart + j], b = H[(j + 1) * kMaxRestart + j];
+    const double r = hypot(a, b);
+    const double c = r > 0 ? a / r : 1.0, s = r > 0 ? b / r : 0.0;
+    fs->cs[j] = c;
+    fs->sn[j] = s;
+    H[j * kMaxRestart + j] = r;
+    H[(j + 1) * kMaxRestart + j] = 0;
+    fs->g[j + 1] = -s * fs->g[j];
+    fs->g[j] = c * fs->g[j];
+    fs->res_est = fabs(fs->g[j + 1]);
+}
+
+static_assert(kRedQ >= kMaxRestart && kRedQ >= kMaxSmooth, "partial-sum stride too small");
+
+template <int SD, typename TZ, bool TR>
+__global__ void __launch_bounds__(256) k_fg_apply_dots(OpL0<double> op, const TZ* __restrict__ z,
+                                                       TZ* __restrict__ zstore, double* __restrict__ w, VPtrs V,
+                                                       int j, FgState* fs, RedBuf rb) {
+    const Geom& g = op.g;
+    LoadPlain<double, TZ> ld{z};
+    double dots[32] = {0.0};  // j + 1 <= kMaxRestart = 32 dots in one pass
+    ST_NODE_LOOP_BEGIN(g)
+    double v;
+    if (is_free<SD>(g, i_, j_, k_, n_))
+        v = row_l0<SD, double, TR>(op, i_, j_, k_, n_, ld);
+    else
+        v = (double)z[idx_];
+    w[idx_] = v;
+    zstore[idx_] = z[idx_];
+#pragma unroll
+    for (int q = 0; q < 32; ++q)
+        if (q <= j) dots[q] += v * V.v[q][idx_];
+    ST_NODE_LOOP_END
+    __shared__ double out[32];
+    if (reduce_publish<32>(dots, j + 1, rb, out)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0)
+            for (int q = 0; q <= j; ++q) fs->h1[q] = out[q];
+    }
+}
+
+// pass 0: w -= sum h1_q v_q, new dots -> h1 (first projection kept in H)
+// pass 1: w -= sum h1_q v_q, norm; H column completed, Givens applied.
+__global__ void __launch_bounds__(256) k_fg_update(Geom g, double* __restrict__ w, VPtrs V, int j, int pass,
+                                                   FgState* fs, RedBuf rb) {
+    __shared__ double cf[32];
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    if (tid <= j) cf[tid] = fs->h1[tid];
+    __syncthreads();
+    double dots[32] = {0.0};
+    ST_NODE_LOOP_BEGIN(g)
+    double v = w[idx_];
+#pragma unroll
+    for (int q = 0; q < 32; ++q)
+        if (q <= j) v -= cf[q] * V.v[q][idx_];
+    w[idx_] = v;
+    if (pass == 0) {
+#pragma unroll
+        for (int q = 0; q < 32; ++q)
+            if (q <= j) dots[q] += v * V.v[q][idx_];
+    } else {
+        dots[0] += v * v;
+    }
+    ST_NODE_LOOP_END
+    __shared__ double out[32];
+    if (reduce_publish<32>(dots, pass == 0 ? j + 1 : 1, rb, out)) {
+        if (tid == 0) {
+            if (pass == 0) {
+                for (int q = 0; q <= j; ++q) {
+                    fs->H[q * kMaxRestart + j] = cf[q];
+                    fs->h1[q] = out[q];
+                }
+            } else {
+                for (int q = 0; q <= j; ++q) fs->H[q * kMaxRestart + j] += cf[q];
+                const double h = sqrt(out[0]);
+                fs->H[(j + 1) * kMaxRestart + j] = h;
+                fs->nrm = h;
+                fg_givens_column(fs, j);
+                fs->breakdown = !(h > 0.0);
+                fs->bad = !isfinite(h) || !isfinite(fs->res_est);
+            }
+        }
+    }
+}
+
+template <typename TZ>
+__global__ void __launch_bounds__(256) k_fg_normalize(Geom g, const double* __restrict__ w,
+                                                      double* __restrict__ vn, TZ* __restrict__ bmg,
+                                                      const FgState* fs) {
+    const double h = fs->nrm;
+    const double inv = h > 0 ? 1.0 / h : 0.0;
+    ST_NODE_LOOP_BEGIN(g)
+    const double v = w[idx_] * inv;
+    vn[idx_] = v;
+    bmg[idx_] = (TZ)v;
+    ST_NODE_LOOP_END
+}
+
+__global__ void k_fg_backsolve(FgState* fs, int k) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int q = k - 1; q >= 0; --q) {
+        double a = fs->g[q];
+        for (int l = q + 1; l < k; ++l) a -= fs->H[q * kMaxRestart + l] * fs->h1[l];
+        const double d = fs->H[q * kMaxRestart + q];
+        fs->h1[q] = d != 0 ? a / d : 0.0;  // y stored in h1
+    }
+}
+
+template <typename TZ>
+__global__ void __launch_bounds__(256) k_fg_update_x(Geom g, double* __restrict__ x, ZPtrs<TZ> Z, int k,
+                                                     const FgState* fs) {
+    __shared__ double y[kMaxRestart];
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    if (tid < k) y[tid] = fs->h1[tid];
+    __syncthreads();
+    ST_NODE_LOOP_BEGIN(g)
+    double v = x[idx_];
+    for (int q = 0; q < k; ++q) v += y[q] * (double)Z.z[q][idx_];
+    x[idx_] = v;
+    ST_NODE_LOOP_END
+}
+
+template <int SD, bool TR>
+__global__ void __launch_bounds__(256) k_fg_residual(OpL0<double> op, const double* __restrict__ f,
+                                                     const double* __restrict__ x, double* __restrict__ r,
+                                                     FgState* fs, RedBuf rb) {
+    const Geom& g = op.g;
+    LoadPlain<double, double> ld{x};
+    double acc[1] = {0.0};
+    ST_NODE_LOOP_BEGIN(g)
+    double v;
+    if (is_free<SD>(g, i_, j_, k_, n_))
+        v = f[idx_] - row_l0<SD, double, TR>(op, i_, j_, k_, n_, ld);
+    else
+        v = f[idx_] - x[idx_];
+    r[idx_] = v;
+    acc[0] += v * v;
+    ST_NODE_LOOP_END
+    __shared__ double out[1];
+    if (reduce_publish<1>(acc, 1, rb, out)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            fs->beta = sqrt(out[0]);
+            fs->res_est = fs->beta;
+            fs->bad = !isfinite(fs->beta);
+        }
+    }
+}
+
+template <typename TZ>
+__global__ void __launch_bounds__(256) k_fg_start(Geom g, double* __restrict__ v0, TZ* __restrict__ bmg,
+                                                  FgState* fs) {
+    const double beta = fs->beta;
+    const double inv = beta > 0 ? 1.0 / beta : 0.0;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+        // g is read by later kernels only
+        fs->g[0] = beta;
+        for (int q = 1; q <= kMaxRestart; ++q) fs->g[q] = 0.0;
+        fs->breakdown = 0;
+    }
+    ST_NODE_LOOP_BEGIN(g)
+    const double v = v0[idx_] * inv;
+    v0[idx_] = v;
+    bmg[idx_] = (TZ)v;
+    ST_NODE_LOOP_END
+}
+
+__global__ void __launch_bounds__(256) k_dot64(Geom g, const double* __restrict__ a, const double* __restrict__ b,
+                                               double* out_d, RedBuf rb) {
+    double acc[1] = {0.0};
+    ST_NODE_LOOP_BEGIN(g)
+    acc[0] += a[idx_] * b[idx_];
+    ST_NODE_LOOP_END
+    __shared__ double out[1];
+    if (reduce_publish<1>(acc, 1, rb, out)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) *out_d = out[0];
+    }
+}
+
+template <int SD>
+__global__ void __launch_bounds__(256) k_mask_copy(Geom g, const double* __restrict__ src, double* __restrict__ dst) {
+    ST_NODE_LOOP_BEGIN(g)
+    dst[idx_] = is_free<SD>(g, i_, j_, k_, n_) ? src[idx_] : 0.0;
+    ST_NODE_LOOP_END
+}
+
+// ---------------------------------------------------------------- launch wrappers
+#define ST_SD_DISPATCH(sd, ...) \
+    do {                        \
+        if ((sd) == 2) {        \
+            constexpr int SD = 2; \
+            __VA_ARGS__;        \
+        } else {                \
+            constexpr int SD = 3; \
+            __VA_ARGS__;        \
+        }                       \
+    } while (0)
+
+template <typename T>
+static OpLc<T> dummy_lc(const Geom& g) {
+    OpLc<T> o{};
+    o.g = g;
+    return o;
+}
+template <typename T>
+static OpL0<T> dummy_l0(const Geom& g) {
+    OpL0<T> o{};
+    o.g = g;
+    return o;
+}
+
+template <typename T>
+void launch_apply_l0(int sd, const OpL0<T>& op, bool tr, const T* x, T* y, cudaStream_t s) {
+    note_launch(s);
+    const LaunchCfg c = node_cfg(op.g);
+    const OpLc<T> oc = dummy_lc<T>(op.g);
+    ST_SD_DISPATCH(sd, if (tr) k_apply<SD, T, 0, true><<<c.grid, c.block, 0, s>>>(op, oc, x, y);
+                   else k_apply<SD, T, 0, false><<<c.grid, c.block, 0, s>>>(op, oc, x, y));
+}
+template <typename T>
+void launch_apply_lc(int sd, const OpLc<T>& op, bool tr, const T* x, T* y, cudaStream_t s) {
+    note_launch(s);
+    const LaunchCfg c = node_cfg(op.g);
+    const OpL0<T> o0 = dummy_l0<T>(op.g);
+    ST_SD_DISPATCH(sd, if (tr) k_apply<SD, T, 1, true><<<c.grid, c.block, 0, s>>>(o0, op, x, y);
+                   else k_apply<SD, T, 1, false><<<c.grid, c.block, 0, s>>>(o0, op, x, y));
+}
+template <typename T>
+void launch_diag_l0(int sd, const OpL0<T>& op, T* d, bool invert, cudaStream_t s) {
+    note_launch(s);
+    const LaunchCfg c = node_cfg(op.g);
+    const OpLc<T> oc = dummy_lc<T>(op.g);
+    ST_SD_DISPATCH(sd, k_diag<SD, T, 0><<<c.grid, c.block, 0, s>>>(op, oc, d, invert ? 1 : 0));
+}
+template <typename T>
+void launch_diag_lc(int sd, const OpLc<T>& op, T* d, bool invert, cudaStream_t s) {
+    note_launch(s);
+    const LaunchCfg c = node_cfg(op.g);
+    const OpL0<T> o0 = dummy_l0<T>(op.g);
+    ST_SD_DISPATCH(sd, k_diag<SD, T, 1><<<c.grid, c.block, 0, s>>>(o0, op, d, invert ? 1 : 0));
+}
+template <typename T>
+void launch_residual(int sd, int lvl, const OpL0<T>& o0, const OpLc<T>& oc, bool tr, const T* b, const T* x, T* r,
+                     cudaStream_t s) {
+    note_launch(s);
+    const LaunchCfg c = node_cfg(lvl == 0 ? o0.g : oc.g);
+    if (lvl == 0) {
+        ST_SD_DISPATCH(sd, if (tr) k_residual<SD, T, 0, true><<<c.grid, c.block, 0, s>>>(o0, oc, b, x, r);
+                       else k_residual<SD, T, 0, false><<<c.grid, c.block, 0, s>>>(o0, oc, b, x, r));
+    } else {
+        ST_SD_DISPATCH(sd, if (tr) k_residual<SD, T, 1, true><<<c.grid, c.block, 0, s>>>(o0, oc, b, x, r);
+                       else k_residual<SD, T, 1, false><<<c.grid, c.block, 0, s>>>(o0, oc, b, x, r));
+    }
+}
+template <typename T>
+void launch_restrict(const Geom& gf, const Geom& gc, int kind, int sd, const T* rf, T* rc, cudaStream_t s) {
+    note_launch(s);
+    const LaunchCfg c = node_cfg(gc);
+    ST_SD_DISPATCH(sd, k_restrict<SD, T><<<c.grid, c.block, 0, s>>>(gf, gc, kind, rf, rc));
+}
+template <typename T>
+void launch_prolong(const Geom& gf, const Geom& gc, int kind, int sd, const T* xc, T* xf, cudaStream_t s) {
+    note_launch(s);
+    const LaunchCfg c = node_cfg(gf);
+    ST_SD_DISPATCH(sd, k_prolong<SD, T><<<c.grid, c.block, 0, s>>>(gf, gc, kind, xc, xf));
+}
+
+template <int SD, typename T, int LV, bool TR>
+static void smooth_impl(const OpL0<T>& o0, const OpLc<T>& oc, const T* b, T* x, const T* dinv, Basis<T> U, T* w,
+                        int steps, bool zero_init, SmState* st, RedBuf rb, cudaStream_t s) {
+    note_launch(s, 2 + 2 * steps);
+    const Geom& g = LV == 0 ? o0.g : oc.g;
+    const LaunchCfg c = node_cfg(g);
+    if (zero_init) {
+        U.u[0] = const_cast<T*>(b);
+        k_sm_start<SD, T, LV, TR, true><<<c.grid, c.block, 0, s>>>(o0, oc, b, x, nullptr, steps, st, rb);
+    } else {
+        k_sm_start<SD, T, LV, TR, false><<<c.grid, c.block, 0, s>>>(o0, oc, b, x, U.u[0], steps, st, rb);
+    }
+    for (int j = 0; j < steps; ++j) {
+        k_sm_apply<SD, T, LV, TR><<<c.grid, c.block, 0, s>>>(o0, oc, dinv, U, w, j, st, rb);
+        k_sm_update<T><<<c.grid, c.block, 0, s>>>(g, U, w, j, steps, st, rb);
+    }
+    k_sm_finish<T><<<c.grid, c.block, 0, s>>>(g, x, dinv, U, zero_init ? 1 : 0, st);
+}
+
+template <typename T>
+void launch_smooth(int sd, int lvl, const OpL0<T>& o0, const OpLc<T>& oc, bool tr, const T* b, T* x, const T* dinv,
+                   Basis<T> U, T* w, int steps, bool zero_init, SmState* st, RedBuf rb, cudaStream_t s) {
+    if (lvl == 0) {
+        ST_SD_DISPATCH(sd, if (tr) smooth_impl<SD, T, 0, true>(o0, oc, b, x, dinv, U, w, steps, zero_init, st, rb, s);
+                       else smooth_impl<SD, T, 0, false>(o0, oc, b, x, dinv, U, w, steps, zero_init, st, rb, s));
+    } else {
+        ST_SD_DISPATCH(sd, if (tr) smooth_impl<SD, T, 1, true>(o0, oc, b, x, dinv, U, w, steps, zero_init, st, rb, s);
+                       else smooth_impl<SD, T, 1, false>(o0, oc, b, x, dinv, U, w, steps, zero_init, st, rb, s));
+    }
+}
+
+template <typename T>
+void launch_coarse_solve(const double* Ainv, int n, bool tr, const T* b, T* x, cudaStream_t s) {
+    note_launch(s);
+    if (tr)
+        k_coarse_gemv_t<T><<<(n + 127) / 128, 128, 0, s>>>(Ainv, n, b, x);
+    else
+        k_coarse_gemv<T><<<(n * 32 + 255) / 256, 256, 0, s>>>(Ainv, n, b, x);
+}
+
+template <typename TZ>
+void launch_fg_apply_dots(int sd, const OpL0<double>& op, bool tr, const TZ* z, TZ* zstore, double* w,
+                          double* const* V, int j, FgState* fs, RedBuf rb, cudaStream_t s) {
+    note_launch(s);
+    VPtrs vp{};
+    for (int q = 0; q <= j && q <= kMaxRestart; ++q) vp.v[q] = V[q];
+    const LaunchCfg c = node_cfg(op.g);
+    ST_SD_DISPATCH(sd, if (tr) k_fg_apply_dots<SD, TZ, true><<<c.grid, c.block, 0, s>>>(op, z, zstore, w, vp, j, fs, rb);
+                   else k_fg_apply_dots<SD, TZ, false><<<c.grid, c.block, 0, s>>>(op, z, zstore, w, vp, j, fs, rb));
+}
+
+void launch_fg_update_dots(const Geom& g, double* w, double* const* V, int j, int pass, FgState* fs, RedBuf rb,
+                           cudaStream_t s) {
+    note_launch(s);
+    VPtrs vp{};
+    for (int q = 0; q <= j && q <= kMaxRestart; ++q) vp.v[q] = V[q];
+    const LaunchCfg c = node_cfg(g);
+    k_fg_update<<<c.grid, c.block, 0, s>>>(g, w, vp, j, pass, fs, rb);
+}
+
+template <typename TZ>
+void launch_fg_normalize(const Geom& g, const double* w, double* vnext, TZ* bmg, int j, FgState* fs, cudaStream_t s) {
+    note_launch(s);
+    (void)j;
+    const LaunchCfg c = node_cfg(g);
+    k_fg_normalize<TZ><<<c.grid, c.block, 0, s>>>(g, w, vnext, bmg, fs);
+}
+
+template <typename TZ>
+void launch_fg_update_x(const Geom& g, double* x, TZ* const* Z, int k, FgState* fs, cudaStream_t s) {
+    if (k > 0) note_launch(s, 2);
+    if (k <= 0) return;
+    k_fg_backsolve<<<1, 32, 0, s>>>(fs, k);
+    ZPtrs<TZ> zp{};
+    for (int q = 0; q < k; ++q) zp.z[q] = Z[q];
+    const LaunchCfg c = node_cfg(g);
+    k_fg_update_x<TZ><<<c.grid, c.block, 0, s>>>(g, x, zp, k, fs);
+}
+
+void launch_fg_residual(int sd, const OpL0<double>& op, bool tr, const double* f, const double* x, double* r,
+                        FgState* fs, RedBuf rb, cudaStream_t s) {
+    note_launch(s);
+    const LaunchCfg c = node_cfg(op.g);
+    ST_SD_DISPATCH(sd, if (tr) k_fg_residual<SD, true><<<c.grid, c.block, 0, s>>>(op, f, x, r, fs, rb);
+                   else k_fg_residual<SD, false><<<c.grid, c.block, 0, s>>>(op, f, x, r, fs, rb));
+}
+
+template <typename TZ>
+void launch_fg_start(const Geom& g, double* v0, TZ* bmg, FgState* fs, cudaStream_t s) {
+    note_launch(s);
+    const LaunchCfg c = node_cfg(g);
+    k_fg_start<TZ><<<c.grid, c.block, 0, s>>>(g, v0, bmg, fs);
+}
+
+void launch_dot64(const Geom& g, const double* a, const double* b, double* out, RedBuf rb, cudaStream_t s) {
+    note_launch(s);
+    const LaunchCfg c = node_cfg(g);
+    k_dot64<<<c.grid, c.block, 0, s>>>(g, a, b, out, rb);
+}
+
+void launch_mask_copy(int sd, const Geom& g, const double* src, double* dst, cudaStream_t s) {
+    note_launch(s);
+    const LaunchCfg c = node_cfg(g);
+    ST_SD_DISPATCH(sd, k_mask_copy<SD><<<c.grid, c.block, 0, s>>>(g, src, dst));
+}
+
+#define ST_INST_T(T)                                                                                                \
+    template void launch_apply_l0<T>(int, const OpL0<T>&, bool, const T*, T*, cudaStream_t);                        \
+    template void launch_apply_lc<T>(int, const OpLc<T>&, bool, const T*, T*, cudaStream_t);                        \
+    template void launch_diag_l0<T>(int, const OpL0<T>&, T*, bool, cudaStream_t);                                   \
+    template void launch_diag_lc<T>(int, const OpLc<T>&, T*, bool, cudaStream_t);                                   \
+    template void launch_residual<T>(int, int, const OpL0<T>&, const OpLc<T>&, bool, const T*, const T*, T*,        \
+                                     cudaStream_t);                                                                  \
+    template void launch_restrict<T>(const Geom&, const Geom&, int, int, const T*, T*, cudaStream_t);               \
+    template void launch_prolong<T>(const Geom&, const Geom&, int, int, const T*, T*, cudaStream_t);                \
+    template void launch_smooth<T>(int, int, const OpL0<T>&, const OpLc<T>&, bool, const T*, T*, const T*, Basis<T>, \
+                                   T*, int, bool, SmState*, RedBuf, cudaStream_t);                                  \
+    template void launch_coarse_solve<T>(const double*, int, bool, const T*, T*, cudaStream_t);                     \
+    template void launch_fg_apply_dots<T>(int, const OpL0<double>&, bool, const T*, T*, double*, double* const*,    \
+                                          int, FgState*, RedBuf, cudaStream_t);                                      \
+    template void launch_fg_normalize<T>(const Geom&, const double*, double*, T*, int, FgState*, cudaStream_t);     \
+    template void launch_fg_update_x<T>(const Geom&, double*, T* const*, int, FgState*, cudaStream_t);             \
+    template void launch_fg_start<T>(const Geom&, double*, T*, FgState*, cudaStream_t);
+
+ST_INST_T(float)
+ST_INST_T(double)
+
+}  // namespace st

@@ -1,0 +1,459 @@
+// Setup-phase kernels: design cast, Galerkin coarse operators J_{l+1} = P^T J_l P
+// (arXiv 2508.09589, Sec. 3.2) in element-block form, the dense inverse of the
+// coarsest operator, the source vector (Sec. 3.1.2), the p-norm objective and
+// its adjoint right-hand side (Sec. 3.3.1, 3.3.3) and the sensitivities (Sec. 3.3.3).
+#include <math.h>
+
+#include "st_device.cuh"
+
+namespace st {
+
+#define ST_SD_DISPATCH(sd, ...)   \
+    do {                          \
+        if ((sd) == 2) {          \
+            constexpr int SD = 2; \
+            __VA_ARGS__;          \
+        } else {                  \
+            constexpr int SD = 3; \
+            __VA_ARGS__;          \
+        }                         \
+    } while (0)
+
+__global__ void k_design_cast(const double* __restrict__ in, double* __restrict__ g64,
+                              __nv_bfloat16* __restrict__ g16, long long n) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        double v = in[q];
+        v = v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
+        if (!(v == v)) v = 0.0;
+        g64[q] = v;
+        g16[q] = __double2bfloat16(v);
+    }
+}
+
+__global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, long long n) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+        out[q] = (float)in[q];
+}
+
+// ---------------------------------------------------------------- element blocks
+// Masked element matrix of element (slab, spatial ex, ey, ez) in block form:
+// F[a_t * 2 + b_t][sym(a_s, b_s)], rows and columns of prescribed nodes zeroed.
+template <int SD>
+__device__ void l0_blocks(const OpL0<double>& op, int slab, int ex, int ey, int ez, double* F) {
+    constexpr int NS = 1 << SD, NSYM = NS * (NS + 1) / 2;
+    const Geom& g = op.g;
+    const long long se = ((long long)ez * g.ney + ey) * g.nex + ex;
+    double C, k;
+    coef_l0(op, op.tc ? se : (long long)slab * g.sp_elems + se, C, k);
+    bool fr[2 * NS];
+    for (int at = 0; at < 2; ++at)
+        for (int as = 0; as < NS; ++as)
+            fr[at * NS + as] = (slab + at > 0) &&
+                               !sp_dir<SD>(g, ex + (as & 1), ey + ((as >> 1) & 1), SD == 3 ? ez + ((as >> 2) & 1) : 0);
+    const double Dt[2][2] = {{0.0, 0.0}, {-1.0, 1.0}};
+    const double Mt[2][2] = {{2.0 * op.dt6, op.dt6}, {op.dt6, 2.0 * op.dt6}};
+    for (int at = 0; at < 2; ++at)
+        for (int bt = 0; bt < 2; ++bt)
+            for (int as = 0; as < NS; ++as)
+                for (int bs = as; bs < NS; ++bs) {
+                    const double v = C * Dt[at][bt] * op.mxd[as ^ bs] + k * Mt[at][bt] * op.kxd[as ^ bs];
+                    const bool m = fr[at * NS + as] && fr[bt * NS + bs];
+                    F[(at * 2 + bt) * NSYM + symidx<NS>(as, bs)] = m ? v : 0.0;
+                }
+}
+
+// Interpolation weight of coarse local node b (0|1) at fine position r (0, 1, 2) along a
+// halved axis: r = 0 -> (1, 0), r = 1 -> (1/2, 1/2), r = 2 -> (0, 1).
+__device__ __forceinline__ double q1(int r, int b) {
+    return r == 1 ? 0.5 : ((r == 0) == (b == 0) ? 1.0 : 0.0);
+}
+
+// One coarse element: A_E = M_E (sum_children Q_c^T A_c Q_c) M_E with Q_c = Q_t (x) Q_s.
+template <int SD, int LV>
+__global__ void k_build(OpL0<double> f0, OpLc<double> fc, Geom gc, int kind, int tc, double* __restrict__ out) {
+    constexpr int NS = 1 << SD, NSYM = NS * (NS + 1) / 2, NV = 4 * NSYM;
+    const Geom& gf = LV == 0 ? f0.g : fc.g;
+    const long long nstore = tc ? 2 * gc.sp_elems : (long long)gc.net * gc.sp_elems;
+    const long long E = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (E >= nstore) return;
+    const int N = (int)(E / gc.sp_elems);  // slab (space-time) or version (extruded)
+    const long long sec = E - (long long)N * gc.sp_elems;
+    double* G = out + E * NV;
+    for (int q = 0; q < NV; ++q) G[q] = 0.0;
+    if (tc && N == 1 && gc.net < 2) return;
+    const int Ex = (int)(sec % gc.nex), Ey = (int)((sec / gc.nex) % gc.ney), Ez = (int)(sec / ((long long)gc.nex * gc.ney));
+    const bool cs = kind != 1, ct = kind != 0;
+    const int nct = ct ? 2 : 1, ncs = cs ? NS : 1;
+    double F[NV];
+    double S[4][NS][NS];
+    for (int cst = 0; cst < nct; ++cst) {
+        const int fslab = ct ? 2 * N + cst : N;
+        for (int csp = 0; csp < ncs; ++csp) {
+            const int cx = csp & 1, cy = (csp >> 1) & 1, cz = (csp >> 2) & 1;
+            const int fx = cs ? 2 * Ex + cx : Ex, fy = cs ? 2 * Ey + cy : Ey;
+            const int fz = (SD == 3) ? (cs ? 2 * Ez + cz : Ez) : 0;
+            if constexpr (LV == 0) {
+                l0_blocks<SD>(f0, fslab, fx, fy, fz, F);
+            } else {
+                const long long sef = ((long long)fz * gf.ney + fy) * gf.nex + fx;
+                const double* A = fc.elem + elem_index(fc, fslab, sef) * NV;
+                for (int q = 0; q < NV; ++q) F[q] = A[q];
+            }
+            // spatial congruence S_ab = Q_s^T F_ab Q_s
+            for (int blk = 0; blk < 4; ++blk) {
+                for (int i = 0; i < NS; ++i)
+                    for (int j = 0; j < NS; ++j) {
+                        double acc = 0.0;
+                        if (cs) {
+                            for (int a = 0; a < NS; ++a) {
+                                const double qa = q1(cx + (a & 1), i & 1) * q1(cy + ((a >> 1) & 1), (i >> 1) & 1) *
+                                                  (SD == 3 ? q1(cz + ((a >> 2) & 1), (i >> 2) & 1) : 1.0);
+                                if (qa == 0.0) continue;
+                                for (int b = 0; b < NS; ++b) {
+                                    const double qb = q1(cx + (b & 1), j & 1) * q1(cy + ((b >> 1) & 1), (j >> 1) & 1) *
+                                                      (SD == 3 ? q1(cz + ((b >> 2) & 1), (j >> 2) & 1) : 1.0);
+                                    if (qb == 0.0) continue;
+                                    acc += qa * F[blk * NSYM + symidx<NS>(a, b)] * qb;
+                                }
+                            }
+                        } else {
+                            acc = F[blk * NSYM + symidx<NS>(i, j)];
+                        }
+                        S[blk][i][j] = acc;
+                    }
+            }
+            // temporal part: G_cd += sum_ab Qt[a][c] Qt[b][d] S_ab
+            for (int c = 0; c < 2; ++c)
+                for (int d = 0; d < 2; ++d) {
+                    double w[2][2];
+                    for (int a = 0; a < 2; ++a)
+                        for (int b = 0; b < 2; ++b)
+                            w[a][b] = ct ? q1(cst + a, c) * q1(cst + b, d) : ((a == c && b == d) ? 1.0 : 0.0);
+                    for (int i = 0; i < NS; ++i)
+                        for (int j = i; j < NS; ++j) {
+                            double acc = 0.0;
+                            for (int a = 0; a < 2; ++a)
+                                for (int b = 0; b < 2; ++b)
+                                    if (w[a][b] != 0.0) acc += w[a][b] * S[a * 2 + b][i][j];
+                            G[(c * 2 + d) * NSYM + symidx<NS>(i, j)] += acc;
+                        }
+                }
+        }
+    }
+    // coarse masks
+    bool fr[2 * NS];
+    for (int at = 0; at < 2; ++at)
+        for (int as = 0; as < NS; ++as)
+            fr[at * NS + as] = (N + at > 0) &&
+                               !sp_dir<SD>(gc, Ex + (as & 1), Ey + ((as >> 1) & 1), SD == 3 ? Ez + ((as >> 2) & 1) : 0);
+    for (int at = 0; at < 2; ++at)
+        for (int bt = 0; bt < 2; ++bt)
+            for (int as = 0; as < NS; ++as)
+                for (int bs = as; bs < NS; ++bs)
+                    if (!(fr[at * NS + as] && fr[bt * NS + bs])) G[(at * 2 + bt) * NSYM + symidx<NS>(as, bs)] = 0.0;
+}
+
+// ---------------------------------------------------------------- dense coarsest operator
+template <int SD, int LV>
+__global__ void k_dense_assemble(OpL0<double> o0, OpLc<double> oc, double* __restrict__ A) {
+    constexpr int NS = 1 << SD, NSYM = NS * (NS + 1) / 2, NV = 4 * NSYM;
+    const Geom& g = LV == 0 ? o0.g : oc.g;
+    const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long n = g.nnodes;
+    if (r >= n) return;
+    const int i = (int)(r % g.nx1);
+    const int j = (int)((r / g.nx1) % g.ny1);
+    const int k = (int)((r / ((long long)g.nx1 * g.ny1)) % g.nz1);
+    const int t = (int)(r / g.plane);
+    double* row = A + r * n;
+    if (!is_free<SD>(g, i, j, k, t)) {
+        row[r] = 1.0;
+        return;
+    }
+    double F[NV];
+    for (int o = 0; o < NS; ++o) {
+        const int ex = i - 1 + (o & 1), ey = j - 1 + ((o >> 1) & 1);
+        const int ez = (SD == 3) ? k - 1 + ((o >> 2) & 1) : 0;
+        if (ex < 0 || ex >= g.nex || ey < 0 || ey >= g.ney) continue;
+        if (SD == 3 && (ez < 0 || ez >= g.nez)) continue;
+        const int as = (~o) & (NS - 1);
+        const long long se = ((long long)ez * g.ney + ey) * g.nex + ex;
+        for (int sb = 0; sb < 2; ++sb) {
+            const int slab = t - 1 + sb;
+            if (slab < 0 || slab >= g.net) continue;
+            const int at = 1 - sb;
+            if constexpr (LV == 0) {
+                l0_blocks<SD>(o0, slab, ex, ey, ez, F);
+            } else {
+                const double* E = oc.elem + elem_index(oc, slab, se) * NV;
+                for (int q = 0; q < NV; ++q) F[q] = E[q];
+            }
+            for (int bt = 0; bt < 2; ++bt)
+                for (int bs = 0; bs < NS; ++bs) {
+                    const int ni = ex + (bs & 1), nj = ey + ((bs >> 1) & 1), nk = SD == 3 ? ez + ((bs >> 2) & 1) : 0;
+                    const long long col = (long long)(slab + bt) * g.plane + ((long long)nk * g.ny1 + nj) * g.nx1 + ni;
+                    row[col] += F[(at * 2 + bt) * NSYM + symidx<NS>(as, bs)];
+                }
+        }
+    }
+}
+
+// One Gauss-Jordan elimination step (no pivoting) from src into dst.  After n steps the
+// matrix holds its inverse.  The coarse operators have a positive definite symmetric
+// part (the free block) and identity rows at prescribed nodes, so no pivot vanishes.
+__global__ void k_gj_step(const double* __restrict__ src, double* __restrict__ dst, int n, int kp, int* err) {
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= (long long)n * n) return;
+    const int i = (int)(q / n), j = (int)(q % n);
+    double p = src[(long long)kp * n + kp];
+    if (!(fabs(p) > 1e-300) || !isfinite(p)) {
+        if (q == 0) *err = 1;
+        p = 1.0;
+    }
+    double v;
+    if (i == kp && j == kp)
+        v = 1.0 / p;
+    else if (i == kp)
+        v = src[(long long)kp * n + j] / p;
+    else if (j == kp)
+        v = -src[(long long)i * n + kp] / p;
+    else
+        v = src[q] - src[(long long)i * n + kp] * src[(long long)kp * n + j] / p;
+    dst[q] = v;
+}
+
+// ---------------------------------------------------------------- source (Sec. 3.1.2)
+// f_i = int N_i Q: spatially uniform Q, so the spatial integral of each adjacent element is
+// its volume / 2^SD; the time integral of N_i q(t) over each adjacent slab uses 2-point
+// Gauss (exact for uniform q).
+template <int SD>
+__global__ void k_rhs(Geom g, int kind, double q0, double a, double b, double f, double* __restrict__ out) {
+    ST_NODE_LOOP_BEGIN(g)
+    double v = 0.0;
+    if (is_free<SD>(g, i_, j_, k_, n_)) {
+        int nel = 0;
+        for (int o = 0; o < (1 << SD); ++o) {
+            const int ex = i_ - 1 + (o & 1), ey = j_ - 1 + ((o >> 1) & 1), ez = SD == 3 ? k_ - 1 + ((o >> 2) & 1) : 0;
+            if (ex < 0 || ex >= g.nex || ey < 0 || ey >= g.ney) continue;
+            if (SD == 3 && (ez < 0 || ez >= g.nez)) continue;
+            ++nel;
+        }
+        double vol = 1.0;
+        for (int d = 0; d < SD; ++d) vol *= 0.5 * g.h[d];
+        double tf = 0.0;
+        const double xi[2] = {0.5 - 0.5 / sqrt(3.0), 0.5 + 0.5 / sqrt(3.0)};
+        for (int sb = 0; sb < 2; ++sb) {
+            const int slab = n_ - 1 + sb;
+            if (slab < 0 || slab >= g.net) continue;
+            const int at = 1 - sb;
+            for (int gq = 0; gq < 2; ++gq) {
+                const double phi = at == 1 ? xi[gq] : 1.0 - xi[gq];
+                const double t = (slab + xi[gq]) * g.dt;
+                const double q = kind == ST_SRC_SIN_T ? q0 * (a + b * sin(2.0 * M_PI * f * t)) : q0;
+                tf += 0.5 * g.dt * phi * q;
+            }
+        }
+        v = nel * vol * tf;
+    }
+    out[idx_] = v;
+    ST_NODE_LOOP_END
+}
+
+// ---------------------------------------------------------------- p-norm objective (Sec. 3.3.1)
+template <int SD>
+__device__ __forceinline__ double elem_avg(const Geom& g, const double* s, int slab, int ex, int ey, int ez) {
+    constexpr int NS = 1 << SD;
+    double a = 0.0;
+    for (int at = 0; at < 2; ++at)
+        for (int bs = 0; bs < NS; ++bs) {
+            const int ni = ex + (bs & 1), nj = ey + ((bs >> 1) & 1), nk = SD == 3 ? ez + ((bs >> 2) & 1) : 0;
+            a += s[(long long)(slab + at) * g.plane + ((long long)nk * g.ny1 + nj) * g.nx1 + ni];
+        }
+    return a / (2 * NS);
+}
+
+template <int SD>
+__global__ void __launch_bounds__(256) k_pnorm_theta(Geom g, const double* __restrict__ s, int P, double* theta,
+                                                     RedBuf rb) {
+    // element loop: (ex, ey) from the thread grid, (slab, ez) from the plane loop
+    double acc[1] = {0.0};
+    const int ex = blockIdx.x * blockDim.x + threadIdx.x, ey = blockIdx.y * blockDim.y + threadIdx.y;
+    const long long planes = (long long)g.nez * g.net;
+    for (long long z = blockIdx.z; z < planes; z += gridDim.z) {
+        const int slab = (int)(z / g.nez), ez = (int)(z % g.nez);
+        if (ex < g.nex && ey < g.ney) {
+            const double T = elem_avg<SD>(g, s, slab, ex, ey, ez);
+            acc[0] += ipow(T, P);
+        }
+    }
+    __shared__ double out[1];
+    if (reduce_publish<1>(acc, 1, rb, out)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) *theta = out[0];
+    }
+}
+
+template <int SD>
+__global__ void __launch_bounds__(256) k_pnorm_rhs(Geom g, const double* __restrict__ s, int P,
+                                                   const double* theta, double* __restrict__ rhs, double* phi) {
+    constexpr int NS = 1 << SD;
+    const double th = *theta;
+    const double sc = pow(th, (1.0 - P) / (double)P) / (2 * NS);
+    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+        *phi = pow(th, 1.0 / P);
+    ST_NODE_LOOP_BEGIN(g)
+    double v = 0.0;
+    if (is_free<SD>(g, i_, j_, k_, n_)) {
+        for (int o = 0; o < NS; ++o) {
+            const int ex = i_ - 1 + (o & 1), ey = j_ - 1 + ((o >> 1) & 1), ez = SD == 3 ? k_ - 1 + ((o >> 2) & 1) : 0;
+            if (ex < 0 || ex >= g.nex || ey < 0 || ey >= g.ney) continue;
+            if (SD == 3 && (ez < 0 || ez >= g.nez)) continue;
+            for (int sb = 0; sb < 2; ++sb) {
+                const int slab = n_ - 1 + sb;
+                if (slab < 0 || slab >= g.net) continue;
+                v += sc * ipow(elem_avg<SD>(g, s, slab, ex, ey, ez), P - 1);
+            }
+        }
+    }
+    rhs[idx_] = v;
+    ST_NODE_LOOP_END
+}
+
+// ---------------------------------------------------------------- sensitivities (Sec. 3.3.3)
+// g_e = - Lambda_e^T (C'(gamma_e) (D_t (x) M_x) + k'(gamma_e) (M_t (x) K_x)) s_e; the time
+// diffusion k_ad = C dt / 2 scales with C, so it sits in the C' term.  Extruded designs
+// accumulate over the slabs of each spatial element in slab order.
+template <int SD>
+__global__ void k_sens(OpL0<double> op, const double* __restrict__ s, const double* __restrict__ lam,
+                       double* __restrict__ out) {
+    constexpr int NS = 1 << SD;
+    const Geom& g = op.g;
+    const long long nout = op.tc ? g.sp_elems : (long long)g.net * g.sp_elems;
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= nout) return;
+    const long long se = e % g.sp_elems;
+    const int ex = (int)(se % g.nex), ey = (int)((se / g.nex) % g.ney), ez = (int)(se / ((long long)g.nex * g.ney));
+    const int s0 = op.tc ? 0 : (int)(e / g.sp_elems), s1 = op.tc ? g.net : s0 + 1;
+    const double gm = op.g64[e];
+    const double dC = op.simp.p_c * op.simp.dC * ipow(gm, op.simp.p_c - 1);
+    const double dk = op.simp.p_k * op.simp.dk * ipow(gm, op.simp.p_k - 1);
+    const double Dt[2][2] = {{0.0, 0.0}, {-1.0, 1.0}};
+    const double Mt[2][2] = {{2.0 * op.dt6, op.dt6}, {op.dt6, 2.0 * op.dt6}};
+    long long sidx[NS];
+    bool fs[NS];
+    for (int bs = 0; bs < NS; ++bs) {
+        const int ni = ex + (bs & 1), nj = ey + ((bs >> 1) & 1), nk = SD == 3 ? ez + ((bs >> 2) & 1) : 0;
+        sidx[bs] = ((long long)nk * g.ny1 + nj) * g.nx1 + ni;
+        fs[bs] = !sp_dir<SD>(g, ni, nj, nk);
+    }
+    double total = 0.0;
+    for (int slab = s0; slab < s1; ++slab) {
+        double sv[2][NS], lv[2][NS];
+        for (int at = 0; at < 2; ++at)
+            for (int bs = 0; bs < NS; ++bs) {
+                const bool fr = fs[bs] && (slab + at > 0);
+                const long long q = (long long)(slab + at) * g.plane + sidx[bs];
+                sv[at][bs] = fr ? s[q] : 0.0;
+                lv[at][bs] = fr ? lam[q] : 0.0;
+            }
+        double acc = 0.0;
+        for (int at = 0; at < 2; ++at)
+            for (int as = 0; as < NS; ++as) {
+                double r = 0.0;
+                for (int bt = 0; bt < 2; ++bt)
+                    for (int bs = 0; bs < NS; ++bs)
+                        r += (dC * Dt[at][bt] * op.mxd[as ^ bs] + dk * Mt[at][bt] * op.kxd[as ^ bs]) * sv[bt][bs];
+                acc += lv[at][as] * r;
+            }
+        total -= acc;
+    }
+    out[e] = total;
+}
+
+// ---------------------------------------------------------------- wrappers
+void launch_design_cast(const double* in, double* g64, __nv_bfloat16* g16, long long n, cudaStream_t s) {
+    note_launch(s);
+    const int blocks = (int)((n + 255) / 256 < 65536 ? (n + 255) / 256 : 65536);
+    k_design_cast<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(in, g64, g16, n);
+}
+
+void launch_to_float(const double* in, float* out, long long n, cudaStream_t s) {
+    note_launch(s);
+    const int blocks = (int)((n + 255) / 256 < 65536 ? (n + 255) / 256 : 65536);
+    k_to_float<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(in, out, n);
+}
+
+void launch_build_from_l0(int sd, const OpL0<double>& f0, const Geom& gc, int kind, int tc, double* elem_c,
+                          cudaStream_t s) {
+    note_launch(s);
+    const long long nstore = tc ? 2 * gc.sp_elems : (long long)gc.net * gc.sp_elems;
+    const int blocks = (int)((nstore + 127) / 128);
+    OpLc<double> dummy{};
+    ST_SD_DISPATCH(sd, k_build<SD, 0><<<blocks, 128, 0, s>>>(f0, dummy, gc, kind, tc, elem_c));
+}
+
+void launch_build_from_lc(int sd, const OpLc<double>& fc, const Geom& gc, int kind, double* elem_c, cudaStream_t s) {
+    note_launch(s);
+    const long long nstore = fc.tc ? 2 * gc.sp_elems : (long long)gc.net * gc.sp_elems;
+    const int blocks = (int)((nstore + 127) / 128);
+    OpL0<double> dummy{};
+    ST_SD_DISPATCH(sd, k_build<SD, 1><<<blocks, 128, 0, s>>>(dummy, fc, gc, kind, fc.tc, elem_c));
+}
+
+void launch_dense_assemble(int sd, int lvl, const OpL0<double>& o0, const OpLc<double>& oc, double* A,
+                           cudaStream_t s) {
+    note_launch(s);
+    const Geom& g = lvl == 0 ? o0.g : oc.g;
+    cudaMemsetAsync(A, 0, sizeof(double) * g.nnodes * g.nnodes, s);
+    const int blocks = (int)((g.nnodes + 127) / 128);
+    if (lvl == 0) {
+        ST_SD_DISPATCH(sd, k_dense_assemble<SD, 0><<<blocks, 128, 0, s>>>(o0, oc, A));
+    } else {
+        ST_SD_DISPATCH(sd, k_dense_assemble<SD, 1><<<blocks, 128, 0, s>>>(o0, oc, A));
+    }
+}
+
+void launch_gauss_jordan(double* A, double* B, int n, int* err, cudaStream_t s) {
+    note_launch(s, n);
+    const long long nn = (long long)n * n;
+    const int blocks = (int)((nn + 255) / 256);
+    double* src = A;
+    double* dst = B;
+    for (int kp = 0; kp < n; ++kp) {
+        k_gj_step<<<blocks, 256, 0, s>>>(src, dst, n, kp, err);
+        double* t = src;
+        src = dst;
+        dst = t;
+    }
+    if (src != A) cudaMemcpyAsync(A, src, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s);
+}
+
+void launch_rhs(int sd, const Geom& g, int kind, double q0, double a, double b, double f, double* out,
+                cudaStream_t s) {
+    note_launch(s);
+    const LaunchCfg c = node_cfg(g);
+    ST_SD_DISPATCH(sd, k_rhs<SD><<<c.grid, c.block, 0, s>>>(g, kind, q0, a, b, f, out));
+}
+
+void launch_pnorm(int sd, const Geom& g, const double* s, int P, double* rhs, double* phi, RedBuf rb,
+                  double* scratch, cudaStream_t st) {
+    note_launch(st, 2);
+    dim3 block(32, 8, 1);
+    const int gx = (g.nex + 31) / 32, gy = (g.ney + 7) / 8;
+    long long gz = (long long)kMaxBlocks / ((long long)gx * gy);
+    const long long planes = (long long)g.nez * g.net;
+    if (gz < 1) gz = 1;
+    if (gz > planes) gz = planes;
+    dim3 grid(gx, gy, (unsigned)gz);
+    ST_SD_DISPATCH(sd, k_pnorm_theta<SD><<<grid, block, 0, st>>>(g, s, P, scratch, rb));
+    const LaunchCfg c = node_cfg(g);
+    ST_SD_DISPATCH(sd, k_pnorm_rhs<SD><<<c.grid, c.block, 0, st>>>(g, s, P, scratch, rhs, phi));
+}
+
+void launch_sens(int sd, const OpL0<double>& op, const double* s, const double* lam, double* out, cudaStream_t st) {
+    note_launch(st);
+    const long long nout = op.tc ? op.g.sp_elems : (long long)op.g.net * op.g.sp_elems;
+    const int blocks = (int)((nout + 127) / 128);
+    ST_SD_DISPATCH(sd, k_sens<SD><<<blocks, 128, 0, st>>>(op, s, lam, out));
+}
+
+}  // namespace st

@@ -1,0 +1,299 @@
+// Request server: continuous batching of forward + adjoint + sensitivity requests on
+// one GPU.  Requests wait in a FIFO queue; a slot takes the head request as soon as a
+// slot is free and its device-memory footprint fits the budget, so requests that arrive
+// while others run are admitted as slots and memory free up and their work overlaps
+// on the device (one CUDA stream per slot).  Meshes (hierarchy and Krylov buffers) are
+// kept in an idle pool keyed by their description and reused by later requests of the
+// same shape; idle meshes are released when the budget needs the room.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <list>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/st.h"
+
+namespace {
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+std::string desc_key(const st_mesh_desc& d) {
+    return std::string(reinterpret_cast<const char*>(&d), sizeof(d));
+}
+
+struct Job {
+    uint64_t ticket = 0;
+    st_request req{};
+    std::vector<double> gamma;
+    std::vector<double> grad;
+    st_result res{};
+    long long footprint = 0;
+    double t_submit = 0, t_admit = 0;
+    bool done = false;
+};
+
+struct Pooled {
+    st_mesh* mesh;
+    long long bytes;
+};
+
+}  // namespace
+
+struct st_server {
+    st_server_desc desc{};
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<std::shared_ptr<Job>> queue;
+    std::map<uint64_t, std::shared_ptr<Job>> jobs;
+    std::multimap<std::string, Pooled> idle;
+    std::list<std::string> idle_lru;  // keys, most recent at the back
+    long long in_use = 0, idle_bytes = 0;
+    uint64_t next_ticket = 1;
+    bool stopping = false;
+    std::vector<std::thread> workers;
+
+    // Release idle meshes (least recently used first) until `need` more bytes fit.
+    void evict_for(long long need) {
+        while (in_use + idle_bytes + need > desc.hbm_budget && !idle_lru.empty()) {
+            const std::string key = idle_lru.front();
+            idle_lru.pop_front();
+            auto it = idle.find(key);
+            if (it == idle.end()) continue;
+            idle_bytes -= it->second.bytes;
+            st_destroy_mesh(it->second.mesh);
+            idle.erase(it);
+        }
+    }
+
+    void worker(int slot) {
+        cudaSetDevice(desc.device);
+        cudaStream_t stream = nullptr;
+        cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
+        (void)slot;
+        for (;;) {
+            std::shared_ptr<Job> job;
+            st_mesh* mesh = nullptr;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                for (;;) {
+                    if (stopping && queue.empty()) break;
+                    if (!queue.empty()) {
+                        auto& head = queue.front();
+                        const std::string key = desc_key(head->req.mesh);
+                        auto it = idle.find(key);
+                        if (it != idle.end()) {  // reuse an idle mesh of this shape
+                            mesh = it->second.mesh;
+                            idle_bytes -= it->second.bytes;
+                            in_use += head->footprint;
+                            idle.erase(it);
+                            for (auto l = idle_lru.begin(); l != idle_lru.end(); ++l)
+                                if (*l == key) {
+                                    idle_lru.erase(l);
+                                    break;
+                                }
+                            job = head;
+                            queue.pop_front();
+                            break;
+                        }
+                        evict_for(head->footprint);
+                        if (in_use + idle_bytes + head->footprint <= desc.hbm_budget) {
+                            in_use += head->footprint;
+                            job = head;
+                            queue.pop_front();
+                            break;
+                        }
+                    }
+                    cv_work.wait(lk);
+                }
+            }
+            if (!job) break;
+            job->t_admit = now_s();
+            run(job.get(), mesh, stream);
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                in_use -= job->footprint;
+                job->done = true;
+            }
+            cv_work.notify_all();
+            cv_done.notify_all();
+        }
+        if (stream) cudaStreamDestroy(stream);
+    }
+
+    void run(Job* job, st_mesh* mesh, cudaStream_t stream) {
+        st_result& r = job->res;
+        memset(&r, 0, sizeof(r));
+        r.footprint = job->footprint;
+        st_status s = ST_OK;
+        if (!mesh) s = st_create_mesh(&job->req.mesh, &mesh);
+        if (s == ST_OK) s = st_set_stream(mesh, stream);
+        if (s == ST_OK) s = st_set_design(mesh, job->gamma.data(), job->req.layout, job->gamma.size(), ST_MEM_HOST);
+        if (s == ST_OK) {
+            s = st_solve_forward(mesh, &job->req.source, &job->req.options, &r.forward);
+            if (s == ST_ERR_NOT_CONVERGED) s = ST_OK;
+        }
+        if (s == ST_OK) {
+            s = st_solve_adjoint(mesh, &job->req.objective, &job->req.options, &r.phi, &r.adjoint);
+            if (s == ST_ERR_NOT_CONVERGED) s = ST_OK;
+        }
+        if (s == ST_OK && job->req.want_gradient) {
+            job->grad.resize(job->gamma.size());
+            s = st_sensitivities(mesh, job->grad.data(), job->grad.size(), ST_MEM_HOST);
+        }
+        if (s == ST_OK && !(r.forward.converged && r.adjoint.converged)) s = ST_ERR_NOT_CONVERGED;
+        r.status = s;
+        const double t = now_s();
+        r.latency_s = t - job->t_submit;
+        r.queue_s = job->t_admit - job->t_submit;
+        if (mesh) {
+            st_set_stream(mesh, nullptr);
+            st_mesh_info info{};
+            st_mesh_info_get(mesh, &info);
+            std::lock_guard<std::mutex> lk(mu);
+            const std::string key = desc_key(job->req.mesh);
+            if (!stopping && info.device_bytes <= desc.hbm_budget) {
+                idle.insert({key, Pooled{mesh, info.device_bytes}});
+                idle_lru.push_back(key);
+                idle_bytes += info.device_bytes;
+            } else {
+                st_destroy_mesh(mesh);
+            }
+        }
+    }
+};
+
+extern "C" {
+
+long long st_footprint_bytes(const st_mesh_desc* d, int precision, int restart) {
+    if (!d) return -1;
+    // Hierarchy sizes by the same halving rule the mesh uses, with the worst-case
+    // (space-time) element storage; see st_create_mesh for the rule itself.
+    const int sd = d->ndim_space;
+    long long n[3] = {d->n[0], d->n[1], sd == 3 ? d->n[2] : 1};
+    long long nt = d->n_t;
+    const int NS = 1 << sd, NV = 4 * NS * (NS + 1) / 2;
+    const double Deff = sqrt(d->mat.k_con * d->mat.k_ins / (d->mat.C_con * d->mat.C_ins));
+    double h[3] = {d->ext[0] / d->n[0], d->ext[1] / d->n[1], sd == 3 ? d->ext[2] / d->n[2] : 1.0};
+    double dt = d->tau / d->n_t;
+    const int tsz = precision == ST_PREC_FP64 ? 8 : 4;
+    long long bytes = 0, N0 = 0, ne0 = 0, nc = 0;
+    for (int l = 0; l < 40; ++l) {
+        long long N = nt + 1, ne = nt;
+        for (int q = 0; q < sd; ++q) {
+            N *= n[q] + 1;
+            ne *= n[q];
+        }
+        if (l == 0) {
+            N0 = N;
+            ne0 = ne;
+        } else {
+            bytes += ne * NV * 12;  // FP64 + FP32 element blocks
+        }
+        bytes += N * (long long)tsz * 16;  // b, x, r, dinv, w and 11 basis vectors
+        nc = N;
+        bool can_s = true;
+        for (int q = 0; q < sd; ++q) can_s = can_s && n[q] % 2 == 0 && n[q] >= 4;
+        const bool can_t = nt % 2 == 0 && nt >= 2;
+        if (N <= d->coarse_dof_cap || (d->max_levels > 0 && l + 1 >= d->max_levels)) break;
+        int kind;
+        if (d->coarsening == ST_COARSEN_FULL) {
+            kind = (can_s && can_t) ? 2 : -1;
+        } else {
+            double hmin = h[0];
+            for (int q = 1; q < sd; ++q) hmin = hmin < h[q] ? hmin : h[q];
+            kind = Deff * dt / (hmin * hmin) < d->lambda_crit ? 1 : 0;
+            if (kind == 1 && !can_t) kind = can_s ? 0 : -1;
+            else if (kind == 0 && !can_s) kind = can_t ? 1 : -1;
+        }
+        if (kind < 0) break;
+        if (kind != 1)
+            for (int q = 0; q < sd; ++q) {
+                n[q] /= 2;
+                h[q] *= 2;
+            }
+        if (kind != 0) {
+            nt /= 2;
+            dt *= 2;
+        }
+    }
+    bytes += N0 * 8LL * (5 + restart + 1) + N0 * (long long)tsz * restart;  // FP64 vectors, V, Z
+    bytes += ne0 * 26LL;                                                     // design copies, sensitivities
+    bytes += 2 * nc * nc * 8 + (4 << 20);
+    return bytes;
+}
+
+st_status st_server_create(const st_server_desc* d, st_server** out) {
+    if (!d || !out || d->max_inflight < 1 || d->hbm_budget <= 0) return ST_ERR_ARG;
+    st_server* s = new st_server();
+    s->desc = *d;
+    for (int q = 0; q < d->max_inflight; ++q) s->workers.emplace_back([s, q] { s->worker(q); });
+    *out = s;
+    return ST_OK;
+}
+
+st_status st_server_destroy(st_server* s) {
+    if (!s) return ST_ERR_ARG;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stopping = true;
+    }
+    s->cv_work.notify_all();
+    for (auto& t : s->workers) t.join();
+    for (auto& kv : s->idle) st_destroy_mesh(kv.second.mesh);
+    delete s;
+    return ST_OK;
+}
+
+st_status st_submit(st_server* s, const st_request* r, uint64_t* ticket) {
+    if (!s || !r || !ticket || !r->gamma) return ST_ERR_ARG;
+    auto job = std::make_shared<Job>();
+    job->req = *r;
+    job->gamma.assign(r->gamma, r->gamma + r->count);
+    job->req.gamma = nullptr;
+    job->footprint = st_footprint_bytes(&r->mesh, r->options.precision, r->options.restart > 0 ? r->options.restart : 30);
+    if (job->footprint <= 0 || job->footprint > s->desc.hbm_budget) return ST_ERR_BUSY;
+    job->t_submit = now_s();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stopping) return ST_ERR_STATE;
+        job->ticket = s->next_ticket++;
+        s->jobs[job->ticket] = job;
+        s->queue.push_back(job);
+        *ticket = job->ticket;
+    }
+    s->cv_work.notify_all();
+    return ST_OK;
+}
+
+st_status st_poll(st_server* s, uint64_t ticket, st_result* out, double* grad, size_t count, int* done) {
+    if (!s || !done) return ST_ERR_ARG;
+    std::shared_ptr<Job> job;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->jobs.find(ticket);
+        if (it == s->jobs.end()) return ST_ERR_NOT_FOUND;
+        job = it->second;
+        *done = job->done ? 1 : 0;
+        if (!job->done) return ST_OK;
+        if (grad && !job->grad.empty() && count != job->grad.size()) return ST_ERR_ARG;
+        s->jobs.erase(it);
+    }
+    if (out) *out = job->res;
+    if (grad && !job->grad.empty()) {
+        memcpy(grad, job->grad.data(), count * sizeof(double));
+    }
+    return ST_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,1018 @@
+// Host side of the space-time solver: mesh and hierarchy (Algorithm 1), design set-up
+// (Galerkin coarse operators, Jacobi diagonals, coarsest inverse), the FP64 flexible
+// GMRES with the multigrid V-cycle preconditioner (arXiv 2508.09589, Sec. 3.2), the
+// adjoint solve and sensitivities (Sec. 3.3.3), and the C ABI declared in include/st.h.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <string>
+#include <vector>
+
+#include "st_internal.h"
+#include "st_mesh.h"
+
+namespace st {
+
+thread_local std::string g_last_error;
+
+st_status fail(st_status code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(e_ == cudaErrorMemoryAllocation ? ST_ERR_OOM : ST_ERR_CUDA,               \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                      \
+    } while (0)
+
+#define CKS(call)                      \
+    do {                               \
+        st_status s_ = (call);         \
+        if (s_ != ST_OK) return s_;    \
+    } while (0)
+
+static double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// ---------------------------------------------------------------- device memory
+st_status Mesh::alloc(void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(ST_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+    }
+    allocs.push_back(*p);
+    alloc_sizes.push_back(bytes);
+    bytes_held += (long long)bytes;
+    return ST_OK;
+}
+
+void Mesh::release(void* p) {
+    if (!p) return;
+    for (size_t q = 0; q < allocs.size(); ++q)
+        if (allocs[q] == p) {
+            cudaFree(p);
+            bytes_held -= (long long)alloc_sizes[q];
+            allocs.erase(allocs.begin() + q);
+            alloc_sizes.erase(alloc_sizes.begin() + q);
+            return;
+        }
+}
+
+Mesh::~Mesh() {
+    if (device >= 0) cudaSetDevice(device);
+    if (stream) cudaStreamSynchronize(stream);
+    drop_graphs();
+    for (void* p : allocs) cudaFree(p);
+    if (h_fg) cudaFreeHost(h_fg);
+    if (own_stream && own) cudaStreamDestroy(own);
+}
+
+void Mesh::drop_graphs() {
+    for (int q = 0; q < 4; ++q) {
+        if (gexec[q]) cudaGraphExecDestroy(gexec[q]);
+        gexec[q] = nullptr;
+    }
+}
+
+// ---------------------------------------------------------------- geometry
+static void patch_range(int n, double w, int& lo, int& hi) {
+    lo = n + 1;
+    hi = -1;
+    for (int j = 0; j <= n; ++j)
+        if (fabs(2.0 * j - n) <= w * n + 1e-9) {
+            lo = std::min(lo, j);
+            hi = std::max(hi, j);
+        }
+}
+
+static Geom make_geom(const st_mesh_desc& d, const int n[3], int nt, const double h[3], double dt) {
+    Geom g{};
+    const int sd = d.ndim_space;
+    g.nex = n[0];
+    g.ney = n[1];
+    g.nez = sd == 3 ? n[2] : 1;
+    g.net = nt;
+    g.nx1 = g.nex + 1;
+    g.ny1 = g.ney + 1;
+    g.nz1 = sd == 3 ? g.nez + 1 : 1;
+    g.nt1 = nt + 1;
+    g.plane = (long long)g.nx1 * g.ny1 * g.nz1;
+    g.nnodes = g.plane * g.nt1;
+    g.sp_elems = (long long)g.nex * g.ney * g.nez;
+    for (int q = 0; q < 3; ++q) g.h[q] = h[q];
+    g.dt = dt;
+    g.bc = d.bc;
+    g.face = d.bc == ST_BC_PATCH_BOTTOM ? 1 : 0;
+    for (int q = 0; q < 3; ++q) {
+        g.plo[q] = 0;
+        g.phi[q] = -1;
+    }
+    for (int q = 0; q < sd; ++q) patch_range(n[q], d.bc_width, g.plo[q], g.phi[q]);
+    return g;
+}
+
+// Algorithm 1: lambda = D_eff dt / dx^2 (dx: smallest spatial size); coarsen time when
+// lambda < lambda_crit, else space; fall back to the other axis when the chosen one cannot
+// be halved; stop at max_levels or once a level has at most coarse_dof_cap nodes.
+static st_status build_levels(const st_mesh_desc& d, std::vector<LevelH>& lv) {
+    const int sd = d.ndim_space;
+    const double Deff = sqrt(d.mat.k_con * d.mat.k_ins / (d.mat.C_con * d.mat.C_ins));
+    int n[3] = {d.n[0], d.n[1], sd == 3 ? d.n[2] : 1};
+    int nt = d.n_t;
+    double h[3] = {d.ext[0] / d.n[0], d.ext[1] / d.n[1], sd == 3 ? d.ext[2] / d.n[2] : 1.0};
+    double dt = d.tau / d.n_t;
+    lv.clear();
+    for (;;) {
+        LevelH L;
+        L.g = make_geom(d, n, nt, h, dt);
+        const bool done = (d.max_levels > 0 && (int)lv.size() + 1 >= d.max_levels) ||
+                          L.g.nnodes <= d.coarse_dof_cap || (int)lv.size() + 1 >= kMaxLevels;
+        bool can_s = true;
+        for (int q = 0; q < sd; ++q) can_s = can_s && n[q] % 2 == 0 && n[q] >= 4;
+        const bool can_t = nt % 2 == 0 && nt >= 2;
+        int kind = -1;
+        if (d.coarsening == ST_COARSEN_FULL) {
+            kind = (can_s && can_t) ? 2 : -1;
+        } else {
+            double hmin = h[0];
+            for (int q = 1; q < sd; ++q) hmin = std::min(hmin, h[q]);
+            const double lam = Deff * dt / (hmin * hmin);
+            kind = lam < d.lambda_crit ? 1 : 0;
+            if (kind == 1 && !can_t) kind = can_s ? 0 : -1;
+            else if (kind == 0 && !can_s) kind = can_t ? 1 : -1;
+        }
+        if (done || kind < 0) {
+            L.to_next = -1;
+            lv.push_back(L);
+            break;
+        }
+        L.to_next = kind;
+        lv.push_back(L);
+        if (kind == 0 || kind == 2)
+            for (int q = 0; q < sd; ++q) {
+                n[q] /= 2;
+                h[q] *= 2;
+            }
+        if (kind == 1 || kind == 2) {
+            nt /= 2;
+            dt *= 2;
+        }
+    }
+    return ST_OK;
+}
+
+static st_status build_hierarchy(Mesh* m) {
+    CKS(build_levels(m->desc, m->lv));
+    const long long nc = m->lv.back().g.nnodes;
+    if (nc > kMaxCoarse)
+        return fail(ST_ERR_ARG, "coarsest level has " + std::to_string(nc) + " nodes (> " +
+                                    std::to_string(kMaxCoarse) +
+                                    "): the element counts cannot be halved far enough; use counts with more factors of 2");
+    return ST_OK;
+}
+
+template <typename T>
+OpL0<T> Mesh::op0() const {
+    OpL0<T> o{};
+    o.g = lv[0].g;
+    o.g64 = g64;
+    o.g16 = g16;
+    o.tc = layout == ST_DESIGN_EXTRUDED ? 1 : 0;
+    o.simp.C_ins = desc.mat.C_ins;
+    o.simp.dC = desc.mat.C_con - desc.mat.C_ins;
+    o.simp.k_ins = desc.mat.k_ins;
+    o.simp.dk = desc.mat.k_con - desc.mat.k_ins;
+    o.simp.p_c = desc.mat.p_c;
+    o.simp.p_k = desc.mat.p_k;
+    const int NS = 1 << sd;
+    for (int mb = 0; mb < 8; ++mb) {
+        double mx = 1.0, kx = 0.0;
+        if (mb < NS) {
+            for (int dd = 0; dd < sd; ++dd) mx *= ((mb >> dd) & 1) ? o.g.h[dd] / 6.0 : o.g.h[dd] / 3.0;
+            for (int dd = 0; dd < sd; ++dd) {
+                double t = ((mb >> dd) & 1) ? -1.0 / o.g.h[dd] : 1.0 / o.g.h[dd];
+                for (int e = 0; e < sd; ++e)
+                    if (e != dd) t *= ((mb >> e) & 1) ? o.g.h[e] / 6.0 : o.g.h[e] / 3.0;
+                kx += t;
+            }
+        } else {
+            mx = 0.0;
+        }
+        o.mxd[mb] = (T)mx;
+        o.kxd[mb] = (T)kx;
+    }
+    o.dt6 = (T)(o.g.dt / 6.0);
+    return o;
+}
+
+template <>
+OpLc<double> Mesh::opc<double>(int l) const {
+    OpLc<double> o{};
+    o.g = lv[l].g;
+    o.elem = l > 0 ? lv[l].e64 : nullptr;
+    o.tc = layout == ST_DESIGN_EXTRUDED ? 1 : 0;
+    return o;
+}
+
+template <>
+OpLc<float> Mesh::opc<float>(int l) const {
+    OpLc<float> o{};
+    o.g = lv[l].g;
+    o.elem = l > 0 ? lv[l].e32 : nullptr;
+    o.tc = layout == ST_DESIGN_EXTRUDED ? 1 : 0;
+    return o;
+}
+
+// ---------------------------------------------------------------- creation
+st_status validate_desc(const st_mesh_desc* d) {
+    if (!d) return fail(ST_ERR_ARG, "null argument");
+    const int sd = d->ndim_space;
+    if (sd != 2 && sd != 3) return fail(ST_ERR_ARG, "ndim_space must be 2 or 3");
+    for (int q = 0; q < sd; ++q)
+        if (d->n[q] < 1 || d->ext[q] <= 0) return fail(ST_ERR_ARG, "spatial element counts and extents must be positive");
+    if (d->n_t < 1 || d->tau <= 0) return fail(ST_ERR_ARG, "n_t and tau must be positive");
+    if (d->mat.p_c < 1 || d->mat.p_k < 1 || d->mat.p_c > 16 || d->mat.p_k > 16)
+        return fail(ST_ERR_ARG, "SIMP powers must be integers in [1, 16]");
+    if (!(d->mat.C_ins > 0 && d->mat.C_con > 0 && d->mat.k_ins > 0 && d->mat.k_con > 0))
+        return fail(ST_ERR_ARG, "material constants must be positive");
+    if (d->bc < 0 || d->bc > 3) return fail(ST_ERR_ARG, "unknown boundary-condition kind");
+    if (d->coarse_dof_cap < 1 || d->coarse_dof_cap > kMaxCoarse)
+        return fail(ST_ERR_ARG, "coarse_dof_cap must be in [1, " + std::to_string(kMaxCoarse) + "]");
+    long long nn = d->n_t + 1;
+    for (int q = 0; q < sd; ++q) nn *= d->n[q] + 1;
+    if (nn > (1LL << 31) - 1) return fail(ST_ERR_ARG, "more than 2^31 - 1 nodes");
+    // one time plane's (x, y) node tiles must fit the partial-sum buffer of the reducing kernels
+    const long long tiles = (long long)((d->n[0] + 1 + 31) / 32) * ((d->n[1] + 1 + 7) / 8);
+    if (tiles > kMaxBlocks) return fail(ST_ERR_ARG, "x-y plane too large (more than 4096 32x8 node tiles)");
+    return ST_OK;
+}
+
+st_status plan_hierarchy(const st_mesh_desc* d, st_level_info* out, int max_out, int* n_levels) {
+    CKS(validate_desc(d));
+    std::vector<LevelH> lv;
+    CKS(build_levels(*d, lv));
+    if (n_levels) *n_levels = (int)lv.size();
+    for (int l = 0; l < (int)lv.size() && l < max_out && out; ++l) {
+        const Geom& g = lv[l].g;
+        st_level_info& li = out[l];
+        li.n[0] = g.nex;
+        li.n[1] = g.ney;
+        li.n[2] = d->ndim_space == 3 ? g.nez : 0;
+        li.n_t = g.net;
+        li.n_nodes = g.nnodes;
+        li.to_next = lv[l].to_next;
+        for (int q = 0; q < 3; ++q) li.h[q] = g.h[q];
+        li.dt = g.dt;
+    }
+    return ST_OK;
+}
+
+st_status create_mesh(const st_mesh_desc* d, Mesh** out) {
+    if (!d || !out) return fail(ST_ERR_ARG, "null argument");
+    *out = nullptr;
+    CKS(validate_desc(d));
+    const int sd = d->ndim_space;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(ST_ERR_CUDA, "no CUDA device available");
+    }
+    if (d->device < 0 || d->device >= ndev) return fail(ST_ERR_ARG, "device ordinal out of range");
+    Mesh* m = new Mesh();
+    m->desc = *d;
+    m->sd = sd;
+    m->device = d->device;
+    cudaSetDevice(m->device);
+    st_status st = build_hierarchy(m);
+    if (st != ST_OK) {
+        delete m;
+        return st;
+    }
+    if (cudaStreamCreateWithFlags(&m->own, cudaStreamNonBlocking) != cudaSuccess) {
+        delete m;
+        return fail(ST_ERR_CUDA, "stream creation failed");
+    }
+    m->own_stream = true;
+    m->stream = m->own;
+    const long long N = m->lv[0].g.nnodes;
+    st = ST_OK;
+    auto A = [&](void** p, size_t b) {
+        if (st == ST_OK) st = m->alloc(p, b);
+    };
+    A((void**)&m->f, N * sizeof(double));
+    A((void**)&m->s, N * sizeof(double));
+    A((void**)&m->lam, N * sizeof(double));
+    A((void**)&m->adjrhs, N * sizeof(double));
+    A((void**)&m->fg_w, N * sizeof(double));
+    A((void**)&m->d_fg, sizeof(FgState));
+    A((void**)&m->d_sm, sizeof(SmState));
+    A((void**)&m->rb.part, sizeof(double) * kMaxBlocks * kRedQ);
+    A((void**)&m->rb.counter, sizeof(unsigned) * 4);
+    A((void**)&m->d_scalar, sizeof(double) * 8);
+    A((void**)&m->d_err, sizeof(int) * 4);
+    const long long nc = m->lv.back().g.nnodes;
+    A((void**)&m->Ainv, nc * nc * sizeof(double));
+    A((void**)&m->Awork, nc * nc * sizeof(double));
+    if (st == ST_OK && cudaMallocHost((void**)&m->h_fg, sizeof(FgState)) != cudaSuccess) {
+        cudaGetLastError();
+        st = fail(ST_ERR_OOM, "pinned host allocation failed");
+    }
+    if (st != ST_OK) {
+        delete m;
+        return st;
+    }
+    cudaMemsetAsync(m->rb.counter, 0, sizeof(unsigned) * 4, m->stream);
+    cudaMemsetAsync(m->s, 0, N * sizeof(double), m->stream);
+    cudaMemsetAsync(m->lam, 0, N * sizeof(double), m->stream);
+    cudaMemsetAsync(m->f, 0, N * sizeof(double), m->stream);
+    cudaMemsetAsync(m->d_err, 0, sizeof(int) * 4, m->stream);
+    if (cudaStreamSynchronize(m->stream) != cudaSuccess) {
+        delete m;
+        return fail(ST_ERR_CUDA, "initialisation failed");
+    }
+    *out = m;
+    return ST_OK;
+}
+
+// ---------------------------------------------------------------- design set-up
+st_status Mesh::ensure_level_storage() {
+    const int tc = layout == ST_DESIGN_EXTRUDED ? 1 : 0;
+    if (storage_tc == tc) return ST_OK;
+    drop_graphs();
+    for (size_t l = 1; l < lv.size(); ++l) {
+        release(lv[l].e64);
+        release(lv[l].e32);
+        lv[l].e64 = nullptr;
+        lv[l].e32 = nullptr;
+    }
+    for (size_t l = 1; l < lv.size(); ++l) {
+        const Geom& g = lv[l].g;
+        lv[l].nstore = tc ? 2 * g.sp_elems : (long long)g.net * g.sp_elems;
+        CKS(alloc((void**)&lv[l].e64, lv[l].nstore * nvals(sd) * sizeof(double)));
+        CKS(alloc((void**)&lv[l].e32, lv[l].nstore * nvals(sd) * sizeof(float)));
+    }
+    storage_tc = tc;
+    return ST_OK;
+}
+
+st_status set_design(Mesh* m, const double* gamma, int layout, size_t count, int mem) {
+    if (!gamma) return fail(ST_ERR_ARG, "null design");
+    if (layout != ST_DESIGN_EXTRUDED && layout != ST_DESIGN_SPACETIME) return fail(ST_ERR_ARG, "unknown layout");
+    const Geom& g0 = m->lv[0].g;
+    const long long want = layout == ST_DESIGN_EXTRUDED ? g0.sp_elems : g0.sp_elems * g0.net;
+    if ((long long)count != want)
+        return fail(ST_ERR_ARG, "design count " + std::to_string(count) + " != " + std::to_string(want));
+    cudaSetDevice(m->device);
+    if (m->design_count != want) {
+        m->drop_graphs();
+        m->release(m->g64);
+        m->release(m->g16);
+        m->release(m->gin);
+        m->release(m->gsens);
+        m->g64 = nullptr;
+        m->g16 = nullptr;
+        CKS(m->alloc((void**)&m->g64, want * sizeof(double)));
+        CKS(m->alloc((void**)&m->g16, want * sizeof(__nv_bfloat16)));
+        CKS(m->alloc((void**)&m->gin, want * sizeof(double)));
+        CKS(m->alloc((void**)&m->gsens, want * sizeof(double)));
+        m->design_count = want;
+    }
+    m->layout = layout;
+    CKS(m->ensure_level_storage());
+    cudaStream_t s = m->stream;
+    CK(cudaMemcpyAsync(m->gin, gamma, want * sizeof(double),
+                       mem == ST_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    launch_design_cast(m->gin, m->g64, m->g16, want, s);
+    // Galerkin coarse operators, level by level, in FP64; FP32 copies for the mixed V-cycle.
+    const int L = (int)m->lv.size();
+    for (int l = 1; l < L; ++l) {
+        const int kind = m->lv[l - 1].to_next;
+        if (l == 1)
+            launch_build_from_l0(m->sd, m->op0<double>(), m->lv[1].g, kind, m->storage_tc, m->lv[1].e64, s);
+        else
+            launch_build_from_lc(m->sd, m->opc<double>(l - 1), m->lv[l].g, kind, m->lv[l].e64, s);
+        launch_to_float(m->lv[l].e64, m->lv[l].e32, m->lv[l].nstore * nvals(m->sd), s);
+    }
+    // coarsest operator, dense, and its inverse
+    const int nc = (int)m->lv[L - 1].g.nnodes;
+    launch_dense_assemble(m->sd, L - 1, m->op0<double>(), m->opc<double>(L - 1), m->Ainv, s);
+    CK(cudaMemsetAsync(m->d_err, 0, sizeof(int), s));
+    launch_gauss_jordan(m->Ainv, m->Awork, nc, m->d_err, s);
+    CK(cudaGetLastError());
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, m->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (herr) return fail(ST_ERR_NUMERIC, "zero pivot in the coarsest-level inverse");
+    m->design_version++;
+    m->have_design = true;
+    m->have_state = false;
+    m->have_adjoint = false;
+    return ST_OK;
+}
+
+// ---------------------------------------------------------------- multigrid workspace
+template <typename T>
+MGWork<T>& Mesh::work() {
+    if constexpr (sizeof(T) == 4)
+        return w32;
+    else
+        return w64;
+}
+
+template <typename T>
+st_status Mesh::ensure_mg(int steps) {
+    MGWork<T>& W = work<T>();
+    const int L = (int)lv.size();
+    if (!W.ready) {
+        W.b.assign(L, nullptr);
+        W.x.assign(L, nullptr);
+        W.r.assign(L, nullptr);
+        W.w.assign(L, nullptr);
+        W.dinv.assign(L, nullptr);
+        W.U.assign(L, Basis<T>{});
+        for (int l = 0; l < L; ++l) {
+            const long long N = lv[l].g.nnodes;
+            CKS(alloc((void**)&W.b[l], N * sizeof(T)));
+            CKS(alloc((void**)&W.x[l], N * sizeof(T)));
+            CKS(alloc((void**)&W.r[l], N * sizeof(T)));
+            CKS(alloc((void**)&W.dinv[l], N * sizeof(T)));
+            if (l < L - 1) {
+                CKS(alloc((void**)&W.w[l], N * sizeof(T)));
+            }
+        }
+        W.nbasis = 0;
+        W.ready = true;
+        W.dinv_version = -1;
+    }
+    if (steps + 1 > W.nbasis) {
+        drop_graphs();
+        for (int l = 0; l < L - 1; ++l) {
+            const long long N = lv[l].g.nnodes;
+            for (int q = W.nbasis; q <= steps; ++q) CKS(alloc((void**)&W.U[l].u[q], N * sizeof(T)));
+        }
+        W.nbasis = steps + 1;
+    }
+    if (W.dinv_version != design_version) {
+        for (int l = 0; l < L; ++l) {
+            if (l == 0)
+                launch_diag_l0<T>(sd, op0<T>(), W.dinv[0], true, stream);
+            else
+                launch_diag_lc<T>(sd, opc<T>(l), W.dinv[l], true, stream);
+        }
+        W.dinv_version = design_version;
+    }
+    return ST_OK;
+}
+
+template <typename T>
+void Mesh::smooth(int l, bool tr, bool zero_init, int steps) {
+    MGWork<T>& W = work<T>();
+    launch_smooth<T>(sd, l, op0<T>(), opc<T>(l), tr, W.b[l], W.x[l], W.dinv[l], W.U[l], W.w[l], steps, zero_init, d_sm,
+                     rb, stream);
+}
+
+// One V-cycle on level l: pre-smoothing from zero, residual, restriction, coarse
+// correction, prolongation, post-smoothing (classical V-cycle, Sec. 3.2).
+template <typename T>
+void Mesh::vcycle_rec(int l, bool tr, int steps) {
+    MGWork<T>& W = work<T>();
+    const int L = (int)lv.size();
+    if (l == L - 1) {
+        launch_coarse_solve<T>(Ainv, (int)lv[l].g.nnodes, tr, W.b[l], W.x[l], stream);
+        return;
+    }
+    smooth<T>(l, tr, true, steps);
+    launch_residual<T>(sd, l, op0<T>(), opc<T>(l), tr, W.b[l], W.x[l], W.r[l], stream);
+    launch_restrict<T>(lv[l].g, lv[l + 1].g, lv[l].to_next, sd, W.r[l], W.b[l + 1], stream);
+    vcycle_rec<T>(l + 1, tr, steps);
+    launch_prolong<T>(lv[l].g, lv[l + 1].g, lv[l].to_next, sd, W.x[l + 1], W.x[l], stream);
+    smooth<T>(l, tr, false, steps);
+}
+
+template <typename T>
+st_status Mesh::vcycle(bool tr, int steps, bool graphs) {
+    const int slot = (sizeof(T) == 4 ? 0 : 2) + (tr ? 1 : 0);
+    if (!graphs) {
+        vcycle_rec<T>(0, tr, steps);
+        return ST_OK;
+    }
+    if (!gexec[slot] || gsteps[slot] != steps) {
+        if (gexec[slot]) cudaGraphExecDestroy(gexec[slot]);
+        gexec[slot] = nullptr;
+        cudaGraph_t graph;
+        CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+        vcycle_rec<T>(0, tr, steps);
+        CK(cudaStreamEndCapture(stream, &graph));
+        long long graph_kernel_count = 0;
+        {
+            size_t nn = 0;
+            cudaGraphGetNodes(graph, nullptr, &nn);
+            std::vector<cudaGraphNode_t> nodes(nn);
+            if (nn) cudaGraphGetNodes(graph, nodes.data(), &nn);
+            for (size_t q = 0; q < nn; ++q) {
+                cudaGraphNodeType t;
+                if (cudaGraphNodeGetType(nodes[q], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+                    ++graph_kernel_count;
+            }
+        }
+        cudaError_t e = cudaGraphInstantiate(&gexec[slot], graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            gexec[slot] = nullptr;
+            return fail(ST_ERR_CUDA, std::string("graph instantiation failed: ") + cudaGetErrorString(e));
+        }
+        gsteps[slot] = steps;
+        gversion[slot] = design_version;
+        gkernels[slot] = graph_kernel_count;
+    }
+    CK(cudaGraphLaunch(gexec[slot], stream));
+    note_graph_launch(gkernels[slot]);
+    return ST_OK;
+}
+
+// ---------------------------------------------------------------- FGMRES (FP64, right preconditioned)
+template <typename T>
+st_status Mesh::fgmres(bool tr, const double* rhs, double* x, const st_options& o, st_stats* stats) {
+    const Geom& g = lv[0].g;
+    const int m = o.restart;
+    CKS(ensure_mg<T>(o.smooth_steps));
+    MGWork<T>& W = work<T>();
+    std::vector<T*>& Z = sizeof(T) == 4 ? (std::vector<T*>&)Z32 : (std::vector<T*>&)Z64;
+    const long long N = g.nnodes;
+    while ((int)V.size() < m + 1) {
+        double* p = nullptr;
+        CKS(alloc((void**)&p, N * sizeof(double)));
+        V.push_back(p);
+    }
+    while ((int)Z.size() < m) {
+        T* p = nullptr;
+        CKS(alloc((void**)&p, N * sizeof(T)));
+        Z.push_back(p);
+    }
+    const OpL0<double> A64 = op0<double>();
+    cudaStream_t s = stream;
+    // ||f||
+    launch_dot64(g, rhs, rhs, d_scalar, rb, s);
+    double nf2 = 0;
+    CK(cudaMemcpyAsync(&nf2, d_scalar, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double nf = sqrt(nf2);
+    stats->norm_f = nf;
+    stats->outer_its = 0;
+    stats->restarts = 0;
+    stats->converged = 0;
+    if (!(nf > 0)) {
+        CK(cudaMemsetAsync(x, 0, N * sizeof(double), s));
+        CK(cudaStreamSynchronize(s));
+        stats->converged = 1;
+        stats->rel_res = 0;
+        stats->rel_res_est = 0;
+        return ST_OK;
+    }
+    const double tol = o.rtol * nf;
+    int its = 0;
+    auto read_fg = [&]() -> st_status {
+        CK(cudaMemcpyAsync(h_fg, d_fg, sizeof(FgState), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        return ST_OK;
+    };
+    launch_fg_residual(sd, A64, tr, rhs, x, V[0], d_fg, rb, s);
+    CKS(read_fg());
+    double beta = h_fg->beta;
+    st_status result = ST_OK;
+    for (;;) {
+        if (!(beta == beta) || h_fg->bad) {
+            result = fail(ST_ERR_NUMERIC, "NaN/Inf in the residual");
+            break;
+        }
+        if (beta <= tol) {
+            stats->converged = 1;
+            break;
+        }
+        if (its >= o.max_it) {
+            result = fail(ST_ERR_NOT_CONVERGED, "rtol not reached within max_it outer iterations");
+            break;
+        }
+        launch_fg_start<T>(g, V[0], W.b[0], d_fg, s);
+        int k = 0;
+        for (int j = 0; j < m; ++j) {
+            CKS(vcycle<T>(tr, o.smooth_steps, o.use_graphs != 0));
+            launch_fg_apply_dots<T>(sd, A64, tr, W.x[0], Z[j], fg_w, V.data(), j, d_fg, rb, s);
+            launch_fg_update_dots(g, fg_w, V.data(), j, 0, d_fg, rb, s);
+            launch_fg_update_dots(g, fg_w, V.data(), j, 1, d_fg, rb, s);
+            ++its;
+            k = j + 1;
+            CKS(read_fg());
+            if (h_fg->bad) break;
+            if (h_fg->res_est <= tol || h_fg->breakdown || its >= o.max_it) break;
+            launch_fg_normalize<T>(g, fg_w, V[j + 1], W.b[0], j, d_fg, s);
+        }
+        stats->rel_res_est = h_fg->res_est / nf;
+        if (h_fg->bad) {
+            result = fail(ST_ERR_NUMERIC, "NaN/Inf in the Arnoldi process");
+            break;
+        }
+        launch_fg_update_x<T>(g, x, Z.data(), k, d_fg, s);
+        launch_fg_residual(sd, A64, tr, rhs, x, V[0], d_fg, rb, s);
+        CKS(read_fg());
+        beta = h_fg->beta;
+        stats->restarts++;
+    }
+    if (stats->restarts > 0) stats->restarts--;
+    stats->outer_its = its;
+    stats->rel_res = beta / nf;
+    CK(cudaGetLastError());
+    return result;
+}
+
+st_status solve(Mesh* m, bool adjoint, const st_options* op, st_stats* stats) {
+    st_options o;
+    st_options_default(&o);
+    if (op) o = *op;
+    if (o.restart < 1 || o.restart > kMaxRestart) return fail(ST_ERR_ARG, "restart must be in [1, 32]");
+    if (o.smooth_steps < 1 || o.smooth_steps > kMaxSmooth) return fail(ST_ERR_ARG, "smooth_steps must be in [1, 16]");
+    if (!(o.rtol > 0) || o.max_it < 1) return fail(ST_ERR_ARG, "rtol and max_it must be positive");
+    if (o.precision != ST_PREC_MIXED && o.precision != ST_PREC_FP64) return fail(ST_ERR_ARG, "unknown precision");
+    st_stats local{};
+    st_stats* S = stats ? stats : &local;
+    *S = st_stats{};
+    const double t0 = now_s();
+    double* x = adjoint ? m->lam : m->s;
+    const double* rhs = adjoint ? m->adjrhs : m->f;
+    if (!o.warm_start) CK(cudaMemsetAsync(x, 0, m->lv[0].g.nnodes * sizeof(double), m->stream));
+    st_status r = o.precision == ST_PREC_MIXED ? m->fgmres<float>(adjoint, rhs, x, o, S)
+                                               : m->fgmres<double>(adjoint, rhs, x, o, S);
+    cudaStreamSynchronize(m->stream);
+    S->seconds = now_s() - t0;
+    return r;
+}
+
+}  // namespace st
+
+// ================================================================= C ABI
+using st::fail;
+using st::Mesh;
+
+struct st_mesh : public st::Mesh {};
+
+static Mesh* M(st_mesh* m) { return static_cast<Mesh*>(m); }
+
+static st_status finish_sync(Mesh* mm) {
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(mm->stream);
+    if (e != cudaSuccess) return fail(ST_ERR_CUDA, cudaGetErrorString(e));
+    return ST_OK;
+}
+
+template <typename T>
+static st_status smooth_entry(Mesh* mm, int level, int transpose, const void* b, void* x, int steps, int zero_init) {
+    CKS(mm->ensure_mg<T>(steps));
+    st::MGWork<T>& W = mm->work<T>();
+    const long long N = mm->lv[level].g.nnodes;
+    CK(cudaMemcpyAsync(W.b[level], b, N * sizeof(T), cudaMemcpyDeviceToDevice, mm->stream));
+    CK(cudaMemcpyAsync(W.x[level], x, N * sizeof(T), cudaMemcpyDeviceToDevice, mm->stream));
+    if (level == (int)mm->lv.size() - 1 && W.w[level] == nullptr)
+        CKS(mm->alloc((void**)&W.w[level], N * sizeof(T)));
+    if (W.U[level].u[0] == nullptr)
+        for (int q = 0; q < W.nbasis; ++q) CKS(mm->alloc((void**)&W.U[level].u[q], N * sizeof(T)));
+    mm->smooth<T>(level, transpose != 0, zero_init != 0, steps);
+    CK(cudaMemcpyAsync(x, W.x[level], N * sizeof(T), cudaMemcpyDeviceToDevice, mm->stream));
+    return finish_sync(mm);
+}
+
+template <typename T>
+static st_status vcycle_entry(Mesh* mm, int transpose, const void* b, void* x) {
+    st_options o;
+    st_options_default(&o);
+    CKS(mm->ensure_mg<T>(o.smooth_steps));
+    st::MGWork<T>& W = mm->work<T>();
+    const long long N = mm->lv[0].g.nnodes;
+    CK(cudaMemcpyAsync(W.b[0], b, N * sizeof(T), cudaMemcpyDeviceToDevice, mm->stream));
+    CKS(mm->vcycle<T>(transpose != 0, o.smooth_steps, false));
+    CK(cudaMemcpyAsync(x, W.x[0], N * sizeof(T), cudaMemcpyDeviceToDevice, mm->stream));
+    return finish_sync(mm);
+}
+
+extern "C" {
+
+const char* st_version(void) { return "st-gb300 0.1 (sm_103a)"; }
+
+const char* st_last_error(void) { return st::g_last_error.c_str(); }
+
+void st_mesh_desc_default(st_mesh_desc* d) {
+    if (!d) return;
+    memset(d, 0, sizeof(*d));
+    d->ndim_space = 2;
+    d->n[0] = d->n[1] = d->n[2] = 32;
+    d->n_t = 32;
+    d->ext[0] = d->ext[1] = d->ext[2] = 1.0;
+    d->tau = 1.0;
+    d->mat.C_ins = 0.5;
+    d->mat.C_con = 1.0;
+    d->mat.k_ins = 0.03;
+    d->mat.k_con = 3.0;
+    d->mat.p_c = 2;
+    d->mat.p_k = 3;
+    d->bc = ST_BC_PATCH_LEFT;
+    d->bc_width = 0.1;
+    d->lambda_crit = 0.5;
+    d->coarse_dof_cap = 2000;
+    d->max_levels = 0;
+    d->coarsening = ST_COARSEN_SEMI;
+    d->device = 0;
+}
+
+void st_options_default(st_options* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->rtol = 1e-8;
+    o->max_it = 200;
+    o->restart = 30;
+    o->precision = ST_PREC_MIXED;
+    o->warm_start = 0;
+    o->smooth_steps = 10;
+    o->use_graphs = 1;
+}
+
+st_status st_plan_hierarchy(const st_mesh_desc* d, st_level_info* out, int max_out, int* n_levels) {
+    return st::plan_hierarchy(d, out, max_out, n_levels);
+}
+
+long long st_kernel_launches(void) { return st::kernel_launches(); }
+
+st_status st_create_mesh(const st_mesh_desc* d, st_mesh** out) {
+    Mesh* m = nullptr;
+    st_status s = st::create_mesh(d, &m);
+    if (out) *out = static_cast<st_mesh*>(m);
+    return s;
+}
+
+st_status st_destroy_mesh(st_mesh* m) {
+    if (!m) return fail(ST_ERR_ARG, "null mesh");
+    delete M(m);
+    return ST_OK;
+}
+
+st_status st_mesh_info_get(const st_mesh* m, st_mesh_info* info) {
+    if (!m || !info) return fail(ST_ERR_ARG, "null argument");
+    const Mesh* mm = static_cast<const Mesh*>(m);
+    info->n_levels = (int)mm->lv.size();
+    info->n_nodes = mm->lv[0].g.nnodes;
+    info->n_elem = mm->lv[0].g.sp_elems * mm->lv[0].g.net;
+    info->device_bytes = mm->bytes_held;
+    return ST_OK;
+}
+
+st_status st_level_info_get(const st_mesh* m, int level, st_level_info* info) {
+    if (!m || !info) return fail(ST_ERR_ARG, "null argument");
+    const Mesh* mm = static_cast<const Mesh*>(m);
+    if (level < 0 || level >= (int)mm->lv.size()) return fail(ST_ERR_ARG, "level out of range");
+    const st::Geom& g = mm->lv[level].g;
+    info->n[0] = g.nex;
+    info->n[1] = g.ney;
+    info->n[2] = mm->sd == 3 ? g.nez : 0;
+    info->n_t = g.net;
+    info->n_nodes = g.nnodes;
+    info->to_next = mm->lv[level].to_next;
+    for (int q = 0; q < 3; ++q) info->h[q] = g.h[q];
+    info->dt = g.dt;
+    return ST_OK;
+}
+
+st_status st_set_stream(st_mesh* m, void* stream) {
+    if (!m) return fail(ST_ERR_ARG, "null mesh");
+    Mesh* mm = M(m);
+    cudaStreamSynchronize(mm->stream);
+    mm->stream = stream ? (cudaStream_t)stream : mm->own;
+    return ST_OK;
+}
+
+st_status st_synchronize(st_mesh* m) {
+    if (!m) return fail(ST_ERR_ARG, "null mesh");
+    cudaError_t e = cudaStreamSynchronize(M(m)->stream);
+    if (e != cudaSuccess) return fail(ST_ERR_CUDA, cudaGetErrorString(e));
+    return ST_OK;
+}
+
+st_status st_set_design(st_mesh* m, const double* gamma, int layout, size_t count, int mem) {
+    if (!m) return fail(ST_ERR_ARG, "null mesh");
+    cudaSetDevice(M(m)->device);
+    return st::set_design(M(m), gamma, layout, count, mem);
+}
+
+st_status st_solve_forward(st_mesh* m, const st_source* q, const st_options* o, st_stats* stats) {
+    if (!m || !q) return fail(ST_ERR_ARG, "null argument");
+    Mesh* mm = M(m);
+    if (!mm->have_design) return fail(ST_ERR_STATE, "st_set_design must precede st_solve_forward");
+    if (q->kind != ST_SRC_UNIFORM && q->kind != ST_SRC_SIN_T) return fail(ST_ERR_ARG, "unknown source kind");
+    cudaSetDevice(mm->device);
+    st::launch_rhs(mm->sd, mm->lv[0].g, q->kind, q->q0, q->a, q->b, q->f, mm->f, mm->stream);
+    st_status r = st::solve(mm, false, o, stats);
+    mm->have_state = (r == ST_OK || r == ST_ERR_NOT_CONVERGED);
+    mm->have_adjoint = false;
+    return r;
+}
+
+st_status st_solve_adjoint(st_mesh* m, const st_objective* obj, const st_options* o, double* phi_out,
+                           st_stats* stats) {
+    if (!m || !obj) return fail(ST_ERR_ARG, "null argument");
+    Mesh* mm = M(m);
+    if (!mm->have_state) return fail(ST_ERR_STATE, "st_solve_forward must precede st_solve_adjoint");
+    cudaSetDevice(mm->device);
+    const st::Geom& g = mm->lv[0].g;
+    double phi = 0;
+    if (obj->kind == ST_OBJ_COMPLIANCE) {
+        st::launch_dot64(g, mm->f, mm->s, mm->d_scalar, mm->rb, mm->stream);
+        cudaMemcpyAsync(mm->adjrhs, mm->f, g.nnodes * sizeof(double), cudaMemcpyDeviceToDevice, mm->stream);
+        cudaMemcpyAsync(&phi, mm->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, mm->stream);
+    } else if (obj->kind == ST_OBJ_PNORM) {
+        if (obj->P < 1 || obj->P > 64) return fail(ST_ERR_ARG, "p-norm exponent must be in [1, 64]");
+        st::launch_pnorm(mm->sd, g, mm->s, obj->P, mm->adjrhs, mm->d_scalar + 1, mm->rb, mm->d_scalar + 2, mm->stream);
+        cudaMemcpyAsync(&phi, mm->d_scalar + 1, sizeof(double), cudaMemcpyDeviceToHost, mm->stream);
+    } else {
+        return fail(ST_ERR_ARG, "unknown objective kind");
+    }
+    cudaError_t e = cudaStreamSynchronize(mm->stream);
+    if (e != cudaSuccess) return fail(ST_ERR_CUDA, cudaGetErrorString(e));
+    if (phi_out) *phi_out = phi;
+    st_status r = st::solve(mm, true, o, stats);
+    mm->have_adjoint = (r == ST_OK || r == ST_ERR_NOT_CONVERGED);
+    return r;
+}
+
+st_status st_sensitivities(st_mesh* m, double* out, size_t count, int mem) {
+    if (!m || !out) return fail(ST_ERR_ARG, "null argument");
+    Mesh* mm = M(m);
+    if (!mm->have_adjoint) return fail(ST_ERR_STATE, "st_solve_adjoint must precede st_sensitivities");
+    if ((long long)count != mm->design_count) return fail(ST_ERR_ARG, "count must equal the design size");
+    cudaSetDevice(mm->device);
+    st::launch_sens(mm->sd, mm->op0<double>(), mm->s, mm->lam, mm->gsens, mm->stream);
+    cudaError_t e = cudaMemcpyAsync(out, mm->gsens, count * sizeof(double),
+                                    mem == ST_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                    mm->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(mm->stream);
+    if (e != cudaSuccess) return fail(ST_ERR_CUDA, cudaGetErrorString(e));
+    return ST_OK;
+}
+
+st_status st_get_state(st_mesh* m, int which, double* out, size_t count, int mem) {
+    if (!m || !out) return fail(ST_ERR_ARG, "null argument");
+    Mesh* mm = M(m);
+    if ((long long)count != mm->lv[0].g.nnodes) return fail(ST_ERR_ARG, "count must equal the node count");
+    const double* src = which == ST_STATE_T ? mm->s : which == ST_STATE_LAMBDA ? mm->lam
+                      : which == ST_STATE_RHS ? mm->f : which == ST_STATE_ADJ_RHS ? mm->adjrhs : nullptr;
+    if (!src) return fail(ST_ERR_ARG, "unknown state kind");
+    cudaSetDevice(mm->device);
+    cudaError_t e = cudaMemcpyAsync(out, src, count * sizeof(double),
+                                    mem == ST_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                    mm->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(mm->stream);
+    if (e != cudaSuccess) return fail(ST_ERR_CUDA, cudaGetErrorString(e));
+    return ST_OK;
+}
+
+st_status st_set_state(st_mesh* m, const double* s, size_t count, int mem) {
+    if (!m || !s) return fail(ST_ERR_ARG, "null argument");
+    Mesh* mm = M(m);
+    if ((long long)count != mm->lv[0].g.nnodes) return fail(ST_ERR_ARG, "count must equal the node count");
+    cudaSetDevice(mm->device);
+    cudaError_t e = cudaMemcpyAsync(mm->s, s, count * sizeof(double),
+                                    mem == ST_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                    mm->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(mm->stream);
+    if (e != cudaSuccess) return fail(ST_ERR_CUDA, cudaGetErrorString(e));
+    return ST_OK;
+}
+
+// ---- component entry points
+static st_status comp_check(Mesh* mm, int level, int precision) {
+    if (!mm->have_design) return fail(ST_ERR_STATE, "st_set_design must come first");
+    if (level < 0 || level >= (int)mm->lv.size()) return fail(ST_ERR_ARG, "level out of range");
+    if (precision != ST_PREC_MIXED && precision != ST_PREC_FP64) return fail(ST_ERR_ARG, "unknown precision");
+    cudaSetDevice(mm->device);
+    return ST_OK;
+}
+
+static st_status finish(Mesh* mm) {
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(mm->stream);
+    if (e != cudaSuccess) return fail(ST_ERR_CUDA, cudaGetErrorString(e));
+    return ST_OK;
+}
+
+st_status st_op_apply(st_mesh* m, int level, int precision, int transpose, const void* x, void* y) {
+    if (!m || !x || !y) return fail(ST_ERR_ARG, "null argument");
+    Mesh* mm = M(m);
+    CKS(comp_check(mm, level, precision));
+    if (precision == ST_PREC_MIXED) {
+        if (level == 0)
+            st::launch_apply_l0<float>(mm->sd, mm->op0<float>(), transpose, (const float*)x, (float*)y, mm->stream);
+        else
+            st::launch_apply_lc<float>(mm->sd, mm->opc<float>(level), transpose, (const float*)x, (float*)y, mm->stream);
+    } else {
+        if (level == 0)
+            st::launch_apply_l0<double>(mm->sd, mm->op0<double>(), transpose, (const double*)x, (double*)y, mm->stream);
+        else
+            st::launch_apply_lc<double>(mm->sd, mm->opc<double>(level), transpose, (const double*)x, (double*)y,
+                                        mm->stream);
+    }
+    return finish(mm);
+}
+
+st_status st_op_diag(st_mesh* m, int level, int precision, void* d) {
+    if (!m || !d) return fail(ST_ERR_ARG, "null argument");
+    Mesh* mm = M(m);
+    CKS(comp_check(mm, level, precision));
+    if (precision == ST_PREC_MIXED) {
+        if (level == 0)
+            st::launch_diag_l0<float>(mm->sd, mm->op0<float>(), (float*)d, false, mm->stream);
+        else
+            st::launch_diag_lc<float>(mm->sd, mm->opc<float>(level), (float*)d, false, mm->stream);
+    } else {
+        if (level == 0)
+            st::launch_diag_l0<double>(mm->sd, mm->op0<double>(), (double*)d, false, mm->stream);
+        else
+            st::launch_diag_lc<double>(mm->sd, mm->opc<double>(level), (double*)d, false, mm->stream);
+    }
+    return finish(mm);
+}
+
+st_status st_restrict(st_mesh* m, int level, int precision, const void* rf, void* rc) {
+    if (!m || !rf || !rc) return fail(ST_ERR_ARG, "null argument");
+    Mesh* mm = M(m);
+    CKS(comp_check(mm, level, precision));
+    if (level + 1 >= (int)mm->lv.size()) return fail(ST_ERR_ARG, "no coarser level");
+    const st::LevelH& F = mm->lv[level];
+    const st::LevelH& C = mm->lv[level + 1];
+    if (precision == ST_PREC_MIXED)
+        st::launch_restrict<float>(F.g, C.g, F.to_next, mm->sd, (const float*)rf, (float*)rc, mm->stream);
+    else
+        st::launch_restrict<double>(F.g, C.g, F.to_next, mm->sd, (const double*)rf, (double*)rc, mm->stream);
+    return finish(mm);
+}
+
+st_status st_prolong(st_mesh* m, int level, int precision, const void* xc, void* xf) {
+    if (!m || !xc || !xf) return fail(ST_ERR_ARG, "null argument");
+    Mesh* mm = M(m);
+    CKS(comp_check(mm, level, precision));
+    if (level + 1 >= (int)mm->lv.size()) return fail(ST_ERR_ARG, "no coarser level");
+    const st::LevelH& F = mm->lv[level];
+    const st::LevelH& C = mm->lv[level + 1];
+    if (precision == ST_PREC_MIXED)
+        st::launch_prolong<float>(F.g, C.g, F.to_next, mm->sd, (const float*)xc, (float*)xf, mm->stream);
+    else
+        st::launch_prolong<double>(F.g, C.g, F.to_next, mm->sd, (const double*)xc, (double*)xf, mm->stream);
+    return finish(mm);
+}
+
+st_status st_smooth(st_mesh* m, int level, int precision, int transpose, const void* b, void* x, int steps,
+                    int zero_init) {
+    if (!m || !b || !x) return fail(ST_ERR_ARG, "null argument");
+    Mesh* mm = M(m);
+    CKS(comp_check(mm, level, precision));
+    if (steps < 1 || steps > st::kMaxSmooth) return fail(ST_ERR_ARG, "steps must be in [1, 16]");
+    if (precision == ST_PREC_MIXED) return smooth_entry<float>(mm, level, transpose, b, x, steps, zero_init);
+    return smooth_entry<double>(mm, level, transpose, b, x, steps, zero_init);
+}
+
+st_status st_vcycle(st_mesh* m, int precision, int transpose, const void* b, void* x) {
+    if (!m || !b || !x) return fail(ST_ERR_ARG, "null argument");
+    Mesh* mm = M(m);
+    CKS(comp_check(mm, 0, precision));
+    if (precision == ST_PREC_MIXED) return vcycle_entry<float>(mm, transpose, b, x);
+    return vcycle_entry<double>(mm, transpose, b, x);
+}
+
+st_status st_level_elements(st_mesh* m, int level, double* out, size_t count) {
+    if (!m || !out) return fail(ST_ERR_ARG, "null argument");
+    Mesh* mm = M(m);
+    CKS(comp_check(mm, level, ST_PREC_FP64));
+    if (level < 1) return fail(ST_ERR_ARG, "level 0 is matrix free");
+    const long long want = mm->lv[level].nstore * st::nvals(mm->sd);
+    if ((long long)count != want) return fail(ST_ERR_ARG, "count must be " + std::to_string(want));
+    CK(cudaMemcpyAsync(out, mm->lv[level].e64, want * sizeof(double), cudaMemcpyDeviceToHost, mm->stream));
+    return finish(mm);
+}
+
+st_status st_coarse_inverse(st_mesh* m, double* out, size_t count) {
+    if (!m || !out) return fail(ST_ERR_ARG, "null argument");
+    Mesh* mm = M(m);
+    CKS(comp_check(mm, 0, ST_PREC_FP64));
+    const long long n = mm->lv.back().g.nnodes;
+    if ((long long)count != n * n) return fail(ST_ERR_ARG, "count must be n*n of the coarsest level");
+    CK(cudaMemcpyAsync(out, mm->Ainv, n * n * sizeof(double), cudaMemcpyDeviceToHost, mm->stream));
+    return finish(mm);
+}
+
+}  // extern "C"

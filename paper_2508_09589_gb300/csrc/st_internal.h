@@ -1,0 +1,192 @@
+// Internal declarations shared by the CUDA translation units of the space-time solver.
+//
+// Geometry, operator descriptors and launch wrappers.  Device code lives in
+// k_ops.cu (operator applies, transfers, smoother, Krylov kernels) and
+// k_setup.cu (design cast, Galerkin coarse operators, coarsest inverse,
+// source, objective, sensitivities); host orchestration in solver.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/st.h"
+
+namespace st {
+
+constexpr int kMaxLevels = 40;
+constexpr int kMaxSmooth = 16;     // Jacobi-GMRES steps per smoothing call
+constexpr int kMaxRestart = 32;    // FGMRES restart length
+constexpr int kMaxBlocks = 4096;   // blocks of a reducing kernel (partial-sum buffer size)
+constexpr int kMaxCoarse = 4096;   // largest coarsest level (dense inverse)
+constexpr int kRedQ = 32;          // partial sums per block (>= kMaxRestart, kMaxSmooth)
+
+// Node/element geometry of one level.  Spatial axes are x, y, z (z unused in 2D);
+// nodes are ordered ((n * nz1 + k) * ny1 + j) * nx1 + i.
+struct Geom {
+    int nx1, ny1, nz1, nt1;        // node counts per axis (nz1 = 1 in 2D)
+    int nex, ney, nez, net;        // element counts (nez = 1 in 2D)
+    long long plane;               // nodes per time plane
+    long long nnodes;
+    long long sp_elems;            // spatial elements per time slab
+    double h[3];                   // spatial element sizes
+    double dt;
+    int bc;                        // ST_BC_*
+    int face;                      // patch face axis (0: x = 0, 1: y = 0)
+    int plo[3], phi[3];            // patch node range per spatial axis (inclusive)
+};
+
+// Modified SIMP parameters (C = C_ins + dC g^p_c, k = k_ins + dk g^p_k).
+struct Simp {
+    double C_ins, dC, k_ins, dk;
+    int p_c, p_k;
+};
+
+// Level-0 (fine) operator: matrix free from the design.  Element matrix
+// J_e = C_e (D_t (x) M_x) + k_e (M_t (x) K_x); M_x and K_x entries depend only on
+// which local bits differ, so they are tabulated by (a ^ b).
+template <typename T>
+struct OpL0 {
+    Geom g;
+    const double* g64;             // FP64 design (used when T = double)
+    const __nv_bfloat16* g16;      // BF16 design (used when T = float)
+    int tc;                        // 1: extruded design (per spatial element)
+    Simp simp;
+    T mxd[8], kxd[8];              // M_x, K_x by (a ^ b) over spatial bits
+    T dt6;                         // dt / 6 (time mass scale)
+};
+
+// Coarse operator (levels >= 1): element matrices in block form, 4 symmetric
+// spatial blocks (a_t, b_t) packed as upper triangles; extruded designs keep two
+// versions per spatial element (first slab, other slabs).
+template <typename T>
+struct OpLc {
+    Geom g;
+    const T* elem;
+    int tc;
+};
+
+// Per-call smoother state (device).
+struct SmState {
+    double H[(kMaxSmooth + 1) * kMaxSmooth];   // Hessenberg matrix, row-major
+    double R[(kMaxSmooth + 1) * kMaxSmooth];   // after Givens rotations
+    double s[kMaxSmooth + 1];                  // basis scales 1 / ||u_j||
+    double cs[kMaxSmooth], sn[kMaxSmooth], g[kMaxSmooth + 1];
+    double coef[kMaxSmooth];                   // y_j s_j of the final update
+    double beta;
+    int kdim;
+    int stop;
+};
+
+// FGMRES state (device).
+struct FgState {
+    double H[(kMaxRestart + 1) * kMaxRestart];
+    double h1[kMaxRestart + 1];
+    double cs[kMaxRestart], sn[kMaxRestart], g[kMaxRestart + 1];
+    double beta;
+    double res_est;
+    double nrm;                    // scratch scalar result
+    int breakdown;
+    int bad;                       // NaN/Inf seen
+};
+
+struct RedBuf {
+    double* part;                  // [kMaxBlocks][kRedQ]
+    unsigned* counter;
+};
+
+template <typename T>
+struct Basis {
+    T* u[kMaxSmooth + 1];
+};
+
+struct LaunchCfg {
+    dim3 grid, block;
+};
+
+LaunchCfg node_cfg(const Geom& g);
+
+// Kernel-launch accounting (st_kernel_launches): n launches queued on s; launches
+// recorded into a graph under capture are counted when the graph is replayed.
+void note_launch(cudaStream_t s, long long n = 1);
+void note_graph_launch(long long kernels);
+
+// ---------------------------------------------------------------- launch wrappers
+// All take the spatial dimension sd (2|3) and dispatch to templates.
+// Operator applies: y = A x (transpose: A^T x).
+template <typename T>
+void launch_apply_l0(int sd, const OpL0<T>& op, bool tr, const T* x, T* y, cudaStream_t s);
+template <typename T>
+void launch_apply_lc(int sd, const OpLc<T>& op, bool tr, const T* x, T* y, cudaStream_t s);
+template <typename T>
+void launch_diag_l0(int sd, const OpL0<T>& op, T* dinv, bool invert, cudaStream_t s);
+template <typename T>
+void launch_diag_lc(int sd, const OpLc<T>& op, T* dinv, bool invert, cudaStream_t s);
+// r = b - A x
+template <typename T>
+void launch_residual(int sd, int lvl, const OpL0<T>& o0, const OpLc<T>& oc, bool tr, const T* b,
+                     const T* x, T* r, cudaStream_t s);
+// transfers between level (fine geometry gf) and level+1 (gc); kind 0 space, 1 time, 2 full
+template <typename T>
+void launch_restrict(const Geom& gf, const Geom& gc, int kind, int sd, const T* rf, T* rc, cudaStream_t s);
+template <typename T>
+void launch_prolong(const Geom& gf, const Geom& gc, int kind, int sd, const T* xc, T* xf, cudaStream_t s);
+
+// Jacobi-GMRES smoother on one level.
+template <typename T>
+void launch_smooth(int sd, int lvl, const OpL0<T>& o0, const OpLc<T>& oc, bool tr, const T* b, T* x,
+                   const T* dinv, Basis<T> U, T* w, int steps, bool zero_init, SmState* st, RedBuf rb,
+                   cudaStream_t s);
+
+// Coarsest solve x = Ainv b (or Ainv^T b).
+template <typename T>
+void launch_coarse_solve(const double* Ainv, int n, bool tr, const T* b, T* x, cudaStream_t s);
+
+// ---- FGMRES (FP64 outer) kernels; TZ is the multigrid vector type
+template <typename TZ>
+void launch_fg_apply_dots(int sd, const OpL0<double>& op, bool tr, const TZ* z, TZ* zstore,
+                          double* w, double* const* V, int j, FgState* fs, RedBuf rb, cudaStream_t s);
+void launch_fg_update_dots(const Geom& g, double* w, double* const* V, int j, int pass, FgState* fs,
+                           RedBuf rb, cudaStream_t s);
+template <typename TZ>
+void launch_fg_normalize(const Geom& g, const double* w, double* vnext, TZ* bmg, int j, FgState* fs,
+                         cudaStream_t s);
+template <typename TZ>
+void launch_fg_update_x(const Geom& g, double* x, TZ* const* Z, int k, FgState* fs, cudaStream_t s);
+void launch_fg_residual(int sd, const OpL0<double>& op, bool tr, const double* f, const double* x,
+                        double* r, FgState* fs, RedBuf rb, cudaStream_t s);
+template <typename TZ>
+void launch_fg_start(const Geom& g, double* v0, TZ* bmg, FgState* fs, cudaStream_t s);
+void launch_dot64(const Geom& g, const double* a, const double* b, double* out, RedBuf rb, cudaStream_t s);
+void launch_mask_copy(int sd, const Geom& g, const double* src, double* dst, cudaStream_t s);
+
+// ---- setup kernels
+void launch_design_cast(const double* in, double* g64, __nv_bfloat16* g16, long long n, cudaStream_t s);
+void launch_build_from_l0(int sd, const OpL0<double>& f0, const Geom& gc, int kind, int tc, double* elem_c,
+                          cudaStream_t s);
+void launch_build_from_lc(int sd, const OpLc<double>& fc, const Geom& gc, int kind, double* elem_c,
+                          cudaStream_t s);
+void launch_to_float(const double* in, float* out, long long n, cudaStream_t s);
+void launch_dense_assemble(int sd, int lvl, const OpL0<double>& o0, const OpLc<double>& oc, double* A,
+                           cudaStream_t s);
+void launch_gauss_jordan(double* A, double* B, int n, int* err, cudaStream_t s);  // result in A
+void launch_rhs(int sd, const Geom& g, int kind, double q0, double a, double b, double f, double* out,
+                cudaStream_t s);
+void launch_pnorm(int sd, const Geom& g, const double* s, int P, double* rhs, double* phi, RedBuf rb,
+                  double* scratch, cudaStream_t st);
+void launch_sens(int sd, const OpL0<double>& op, const double* s, const double* lam, double* out,
+                 cudaStream_t st);
+
+// element storage sizes
+inline int nsp(int sd) { return 1 << sd; }
+inline int nsym(int sd) { return nsp(sd) * (nsp(sd) + 1) / 2; }
+inline int nvals(int sd) { return 4 * nsym(sd); }
+
+}  // namespace st
+
+#define ST_CUDA_LAUNCH_CHECK() \
+    do {                       \
+    } while (0)

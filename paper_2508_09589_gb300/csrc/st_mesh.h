@@ -1,0 +1,109 @@
+// Mesh object behind the st_mesh handle: hierarchy, design, device buffers and the
+// per-precision multigrid workspaces.
+#pragma once
+
+#include <vector>
+
+#include "st_internal.h"
+
+namespace st {
+
+st_status fail(st_status code, const std::string& msg);
+long long kernel_launches();
+extern thread_local std::string g_last_error;
+
+struct LevelH {
+    Geom g;
+    int to_next = -1;          // 0 space, 1 time, 2 both, -1 coarsest
+    long long nstore = 0;      // stored element matrices (levels >= 1)
+    double* e64 = nullptr;     // FP64 element blocks
+    float* e32 = nullptr;      // FP32 copy for the mixed V-cycle
+};
+
+template <typename T>
+struct MGWork {
+    bool ready = false;
+    int nbasis = 0;
+    long long dinv_version = -1;
+    std::vector<T*> b, x, r, w, dinv;
+    std::vector<Basis<T>> U;
+};
+
+struct Mesh {
+    st_mesh_desc desc{};
+    int sd = 2;
+    int device = -1;
+    cudaStream_t stream = nullptr;
+    cudaStream_t own = nullptr;
+    bool own_stream = false;
+    std::vector<LevelH> lv;
+
+    // design
+    int layout = ST_DESIGN_EXTRUDED;
+    int storage_tc = -1;
+    long long design_count = 0;
+    long long design_version = 0;
+    double* gin = nullptr;
+    double* g64 = nullptr;
+    __nv_bfloat16* g16 = nullptr;
+    double* gsens = nullptr;
+    bool have_design = false, have_state = false, have_adjoint = false;
+
+    // coarsest inverse
+    double* Ainv = nullptr;
+    double* Awork = nullptr;
+    int* d_err = nullptr;
+
+    // FP64 vectors
+    double* f = nullptr;
+    double* s = nullptr;
+    double* lam = nullptr;
+    double* adjrhs = nullptr;
+    double* fg_w = nullptr;
+    std::vector<double*> V;
+    std::vector<float*> Z32;
+    std::vector<double*> Z64;
+
+    MGWork<float> w32;
+    MGWork<double> w64;
+
+    SmState* d_sm = nullptr;
+    FgState* d_fg = nullptr;
+    FgState* h_fg = nullptr;
+    RedBuf rb{};
+    double* d_scalar = nullptr;
+
+    cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
+    int gsteps[4] = {0, 0, 0, 0};
+    long long gversion[4] = {-1, -1, -1, -1};
+    long long gkernels[4] = {0, 0, 0, 0};
+
+    std::vector<void*> allocs;
+    std::vector<size_t> alloc_sizes;
+    long long bytes_held = 0;
+
+    ~Mesh();
+    st_status alloc(void** p, size_t bytes);
+    void release(void* p);
+    void drop_graphs();
+    st_status ensure_level_storage();
+
+    template <typename T>
+    OpL0<T> op0() const;
+    template <typename T>
+    OpLc<T> opc(int l) const;
+    template <typename T>
+    MGWork<T>& work();
+    template <typename T>
+    st_status ensure_mg(int steps);
+    template <typename T>
+    void smooth(int l, bool tr, bool zero_init, int steps);
+    template <typename T>
+    void vcycle_rec(int l, bool tr, int steps);
+    template <typename T>
+    st_status vcycle(bool tr, int steps, bool graphs);
+    template <typename T>
+    st_status fgmres(bool tr, const double* rhs, double* x, const st_options& o, st_stats* stats);
+};
+
+}  // namespace st

@@ -1,0 +1,48 @@
+"""Shared helpers of the GPU tests: building the native library, seeded cases, BF16 rounding."""
+import math
+import os
+
+import numpy as np
+
+from oracle import st_oracle as O
+
+
+def ensure_built():
+    from paper_2508_09589_gb300 import _lib
+    if not os.path.exists(_lib.LIB_PATH):
+        from paper_2508_09589_gb300 import build
+        build.build()
+    return _lib.lib()
+
+
+def bf16_round(x: np.ndarray) -> np.ndarray:
+    """Round float64 values to the nearest BF16 value (ties to even), exactly in float64:
+    x = m 2^e with m in [0.5, 1); BF16 keeps 8 significant bits."""
+    x = np.asarray(x, dtype=np.float64)
+    m, e = np.frexp(x)
+    return np.ldexp(np.rint(m * 256.0) / 256.0, e)
+
+
+def mat_dict(mat: O.Material) -> dict:
+    return dict(C_ins=mat.C_ins, C_con=mat.C_con, k_ins=mat.k_ins, k_con=mat.k_con, p_c=mat.p_c, p_k=mat.p_k)
+
+
+def gpu_mesh(om: O.Mesh, **kw):
+    from paper_2508_09589_gb300 import Mesh
+    return Mesh(om.ns, om.nt, ext=om.ext, tau=om.tau, material=mat_dict(om.mat), bc=om.bc,
+                bc_width=om.bc_width, **kw)
+
+
+def oracle_levels(om: O.Mesh, gm_levels):
+    """Oracle Level objects matching the hierarchy the library built."""
+    out = []
+    for L in gm_levels:
+        h = tuple(e / n for e, n in zip(om.ext, L["ns"]))
+        out.append(O.Level(tuple(L["ns"]), L["nt"], h, om.tau / L["nt"], L["to_next"]))
+    return out
+
+
+def rel_err(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))

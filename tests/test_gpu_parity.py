@@ -1,0 +1,269 @@
+"""GPU parity: every kernel family through the C ABI against the FP64 CPU oracle.
+
+Sizes are chosen so the oracle finishes in seconds while the meshes span several
+32x8 thread tiles with ragged edges (node counts not multiples of the tile), both
+spatial dimensions (2+1D and 3+1D), both design layouts and every boundary kind.
+Tolerances: FP64 paths 1e-12 (operators) / 1e-10 (solves at rtol 1e-13); FP32 paths
+use the BF16-rounded design in the oracle and compare at 1e-4 of the largest entry
+(operators) or 2e-3 (ten FP32 GMRES steps).
+"""
+import numpy as np
+import pytest
+
+from oracle import st_oracle as O
+from tests.gpu_common import bf16_round, ensure_built, gpu_mesh, rel_err
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+MATS = {
+    "paper": O.Material(),
+    "unitcap": O.Material(C_ins=1.0, C_con=1.0, k_ins=1e-3, k_con=1.0, p_c=1, p_k=3),
+    "capvar": O.Material(C_ins=0.5, C_con=1.0, k_ins=1e-3, k_con=1.0, p_c=1, p_k=3),
+}
+
+# (ns, nt, material, bc, bc_width, space-time design?)
+CASES = [
+    ((40, 24), 20, "paper", "patch_left", 0.3, True),
+    ((36, 20), 16, "unitcap", "patch_bottom", 0.25, False),
+    ((16, 16), 24, "paper", "all_walls", 0.1, False),
+    ((6, 4, 8), 6, "capvar", "patch_left", 0.5, False),
+    ((4, 6, 4), 5, "paper", "none", 0.1, True),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    ensure_built()
+    assert torch.cuda.is_available()
+
+
+def _case(i, seed=0):
+    ns, nt, mat, bc, w, st = CASES[i]
+    om = O.Mesh(ns, nt, mat=MATS[mat], bc=bc, bc_width=w)
+    rng = np.random.default_rng(100 + i + seed)
+    g = rng.random(om.elem_shape if st else tuple(reversed(ns)))
+    return om, g
+
+
+def _dev(a, dtype=torch.float64):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+@pytest.mark.parametrize("i", range(len(CASES)))
+@pytest.mark.parametrize("transpose", [False, True])
+def test_fine_operator_fp64_and_fp32(i, transpose):
+    om, g = _case(i)
+    gm = gpu_mesh(om, coarse_dof_cap=400)
+    gm.set_design(g)
+    A = O.assemble(om, g)
+    A = A.T.tocsr() if transpose else A
+    x = np.random.default_rng(1).standard_normal(om.n_nodes)
+    y = torch.empty(om.n_nodes, dtype=torch.float64, device="cuda")
+    gm.apply(0, _dev(x), y, "fp64", transpose)
+    assert rel_err(y.cpu().numpy(), A @ x) < 1e-13
+    # FP32 operator with the BF16 design
+    A16 = O.assemble(om, bf16_round(g))
+    A16 = A16.T.tocsr() if transpose else A16
+    y32 = torch.empty(om.n_nodes, dtype=torch.float32, device="cuda")
+    gm.apply(0, _dev(x, torch.float32), y32, "mixed", transpose)
+    assert rel_err(y32.cpu().numpy(), A16 @ x.astype(np.float32).astype(np.float64)) < 1e-4
+    d = torch.empty(om.n_nodes, dtype=torch.float64, device="cuda")
+    gm.diag(0, d, "fp64")
+    assert rel_err(d.cpu().numpy(), A.diagonal()) < 1e-14
+
+
+@pytest.mark.parametrize("i", range(len(CASES)))
+def test_hierarchy_galerkin_transfers(i):
+    """Every level: the coarse operator apply (both orientations), its diagonal, and the
+    masked restriction / prolongation against P^T A P + (I - D_c) built by sparse products."""
+    om, g = _case(i)
+    gm = gpu_mesh(om, coarse_dof_cap=300)
+    gm.set_design(g)
+    glev = gm.levels()
+    olev = O.hierarchy(om, coarse_cap=300)
+    assert [(tuple(L.ns), L.nt, L.to_next) for L in olev] == [(L["ns"], L["nt"], L["to_next"]) for L in glev]
+    mg = O.build_mg(om, g, olev)
+    rng = np.random.default_rng(2)
+    for l in range(len(mg)):
+        N = mg[l].A.shape[0]
+        x = rng.standard_normal(N)
+        for tr in (False, True):
+            A = mg[l].A.T.tocsr() if tr else mg[l].A
+            y = torch.empty(N, dtype=torch.float64, device="cuda")
+            gm.apply(l, _dev(x), y, "fp64", tr)
+            assert rel_err(y.cpu().numpy(), A @ x) < 1e-12, (l, tr)
+            if l > 0:
+                y32 = torch.empty(N, dtype=torch.float32, device="cuda")
+                gm.apply(l, _dev(x, torch.float32), y32, "mixed", tr)
+                assert rel_err(y32.cpu().numpy(), A @ x) < 1e-4, (l, tr)
+        d = torch.empty(N, dtype=torch.float64, device="cuda")
+        gm.diag(l, d, "fp64")
+        assert rel_err(d.cpu().numpy(), mg[l].A.diagonal()) < 1e-12
+        if l + 1 < len(mg):
+            Pt = mg[l].Pt
+            rc = torch.empty(Pt.shape[1], dtype=torch.float64, device="cuda")
+            gm.restrict(l, _dev(x), rc, "fp64")
+            assert rel_err(rc.cpu().numpy(), Pt.T @ x) < 1e-14
+            xc = rng.standard_normal(Pt.shape[1])
+            xf0 = rng.standard_normal(N)
+            xf = _dev(xf0)
+            gm.prolong(l, _dev(xc), xf, "fp64")
+            assert rel_err(xf.cpu().numpy(), xf0 + Pt @ xc) < 1e-14
+    Ainv = gm.coarse_inverse()
+    Ac = mg[-1].A.toarray()
+    assert np.abs(Ainv @ Ac - np.eye(Ac.shape[0])).max() < 1e-9
+
+
+@pytest.mark.parametrize("i", [0, 1, 3])
+@pytest.mark.parametrize("zero_init", [True, False])
+def test_smoother_matches_oracle_gmres(i, zero_init):
+    om, g = _case(i)
+    gm = gpu_mesh(om, coarse_dof_cap=300)
+    gm.set_design(g)
+    olev = O.hierarchy(om, coarse_cap=300)
+    mg = O.build_mg(om, g, olev)
+    rng = np.random.default_rng(3)
+    for l in (0, 1):
+        A = mg[l].A
+        b = rng.standard_normal(A.shape[0])
+        b[mg[l].mask] = 0
+        x0 = np.zeros_like(b) if zero_init else 0.1 * rng.standard_normal(A.shape[0]) * (~mg[l].mask)
+        for tr in (False, True):
+            At = A.T.tocsr() if tr else A
+            ref = O.gmres_jacobi(At, b, x0, 10)
+            x = _dev(x0)
+            gm.smooth(l, _dev(b), x, 10, zero_init, "fp64", tr)
+            assert rel_err(x.cpu().numpy(), ref) < 1e-9, (l, tr)
+            x32 = _dev(x0, torch.float32)
+            gm.smooth(l, _dev(b, torch.float32), x32, 10, zero_init, "mixed", tr)
+            ref32 = ref if l > 0 else O.gmres_jacobi(
+                (O.assemble(om, bf16_round(g)).T.tocsr() if tr else O.assemble(om, bf16_round(g))), b, x0, 10)
+            assert rel_err(x32.cpu().numpy(), ref32) < 2e-3, (l, tr)
+
+
+def test_smoother_zero_rhs_leaves_zero():
+    om, g = _case(1)
+    gm = gpu_mesh(om, coarse_dof_cap=300)
+    gm.set_design(g)
+    b = torch.zeros(om.n_nodes, dtype=torch.float64, device="cuda")
+    x = torch.zeros_like(b)
+    gm.smooth(0, b, x, 10, True, "fp64")
+    assert torch.count_nonzero(x).item() == 0
+
+
+@pytest.mark.parametrize("i", [0, 1, 3])
+def test_vcycle_matches_oracle(i):
+    om, g = _case(i)
+    gm = gpu_mesh(om, coarse_dof_cap=300)
+    gm.set_design(g)
+    mg = O.build_mg(om, g, O.hierarchy(om, coarse_cap=300))
+    b = np.random.default_rng(4).standard_normal(om.n_nodes)
+    b[mg[0].mask] = 0
+    for tr in (False, True):
+        ref = O.vcycle(mg, b, transpose=tr)
+        x = torch.empty(om.n_nodes, dtype=torch.float64, device="cuda")
+        gm.vcycle(_dev(b), x, "fp64", tr)
+        assert rel_err(x.cpu().numpy(), ref) < 1e-8, tr
+
+
+def _src_kw(kind):
+    return dict(kind=kind, q0=1.0, a=1.0, b=0.5, f=4.0)
+
+
+@pytest.mark.parametrize("i", range(len(CASES)))
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_forward_adjoint_sensitivities(i, precision):
+    om, g = _case(i)
+    src = "sin_t" if i % 2 == 0 else "uniform"
+    sol = O.forward(om, g, src, 1.0)
+    dm = O.dirichlet_mask(om)
+    lam = O.adjoint(sol.A, sol.f, dm, sol.lu)
+    sens = O.sensitivities(om, g, sol.s, lam, extruded=g.size == int(np.prod(om.ns)))
+    gm = gpu_mesh(om, coarse_dof_cap=300)
+    gm.set_design(g)
+    st = gm.solve_forward(rtol=1e-13, precision=precision, max_it=400, **_src_kw(src))
+    assert st["converged"] and st["rel_res"] <= 1e-13
+    np.testing.assert_allclose(gm.state("rhs"), sol.f, rtol=0, atol=1e-15 * np.abs(sol.f).max())
+    s = gm.state("T")
+    assert rel_err(s, sol.s) < 1e-10
+    phi, sta = gm.solve_adjoint("compliance", rtol=1e-13, precision=precision, max_it=400)
+    assert sta["converged"]
+    np.testing.assert_allclose(phi, O.compliance(sol.f, sol.s), rtol=1e-11)
+    assert rel_err(gm.state("lambda"), lam) < 1e-10
+    gs = gm.sensitivities()
+    assert rel_err(gs, sens.reshape(-1)) < 1e-9
+
+
+def test_pnorm_objective_and_adjoint():
+    om, g = _case(0)
+    sol = O.forward(om, g, "uniform", 1.0)
+    dm = O.dirichlet_mask(om)
+    phi_ref, dphi = O.pnorm(om, sol.s, 20)
+    lam = O.adjoint(sol.A, dphi, dm, sol.lu)
+    gm = gpu_mesh(om, coarse_dof_cap=300)
+    gm.set_design(g)
+    gm.solve_forward(rtol=1e-13, precision="fp64", max_it=400)
+    phi, st = gm.solve_adjoint("pnorm", P=20, rtol=1e-13, precision="fp64", max_it=400)
+    np.testing.assert_allclose(phi, phi_ref, rtol=1e-11)
+    np.testing.assert_allclose(gm.state("adj_rhs"), np.where(dm, 0, dphi), rtol=1e-11, atol=1e-14 * np.abs(dphi).max())
+    assert rel_err(gm.state("lambda"), lam) < 1e-10
+
+
+def test_mixed_to_1e8_meets_1e6_and_fp64_meets_1e10():
+    """Target tolerances at the 1e-8 outer residual: the mixed path's temperature error
+    against the FP64 oracle is reported and must be below 1e-6 (relative, max norm)."""
+    om, g = _case(1)
+    sol = O.forward(om, g, "uniform", 1.0)
+    gm = gpu_mesh(om, coarse_dof_cap=300)
+    gm.set_design(g)
+    st = gm.solve_forward(rtol=1e-8, precision="mixed")
+    assert st["converged"] and st["rel_res"] <= 1e-8
+    assert rel_err(gm.state("T"), sol.s) < 1e-6
+    st = gm.solve_forward(rtol=1e-13, precision="fp64", max_it=400)
+    assert rel_err(gm.state("T"), sol.s) < 1e-10
+
+
+def test_c0_workload_compliance():
+    """32x32x32 (33^3 DOFs), uniform design 0.5, unit capacity, FP64: compliance and state."""
+    import workloads as W
+    w = W.C0
+    om = O.Mesh(w.ns, w.nt, mat=O.Material(**w.material), bc=w.bc, bc_width=w.bc_width)
+    g = W.make_design(w)
+    sol = O.forward(om, g, "uniform", w.source_q0)
+    gm = gpu_mesh(om)
+    gm.set_design(g)
+    assert [L["ns"] + (L["nt"],) for L in gm.levels()] == [(32, 32, 32), (16, 16, 32), (16, 16, 16), (8, 8, 16)]
+    st = gm.solve_forward(rtol=1e-13, precision="fp64", max_it=400)
+    assert rel_err(gm.state("T"), sol.s) < 1e-10
+    phi, _ = gm.solve_adjoint("compliance", rtol=1e-13, precision="fp64", max_it=400)
+    np.testing.assert_allclose(phi, O.compliance(sol.f, sol.s), rtol=1e-11)
+
+
+def test_warm_start_and_errors():
+    from paper_2508_09589_gb300 import STError
+    om, g = _case(1)
+    gm = gpu_mesh(om, coarse_dof_cap=300)
+    with pytest.raises(STError):
+        gm.solve_forward()  # no design yet
+    gm.set_design(g)
+    with pytest.raises(STError):
+        gm.set_design(np.zeros(7))  # wrong size
+    st1 = gm.solve_forward(rtol=1e-10)
+    st2 = gm.solve_forward(rtol=1e-10, warm_start=True)
+    assert st2["outer_its"] <= 1
+    st3 = gm.solve_forward(rtol=1e-14, max_it=1, allow_not_converged=True)
+    assert st3["status"] == -3 and not st3["converged"]
+    assert st1["converged"]
+
+
+def test_graphs_and_eager_identical():
+    om, g = _case(0)
+    gm = gpu_mesh(om, coarse_dof_cap=300)
+    gm.set_design(g)
+    gm.solve_forward(rtol=1e-9, use_graphs=False)
+    a = gm.state("T")
+    gm.solve_forward(rtol=1e-9, use_graphs=True)
+    b = gm.state("T")
+    np.testing.assert_array_equal(a, b)

@@ -534,3 +534,16 @@ def test_sin_source_moments_match_closed_form():
     np.testing.assert_allclose(t @ f, 0.5 - 1.0 / (16.0 * math.pi), rtol=1e-10)
     f2 = O.assemble_source(m, O.source_fn("sin_t", 1.0), nq=2, constrained=False)
     np.testing.assert_allclose(t @ f2, 0.5 - 1.0 / (16.0 * math.pi), rtol=1e-5)
+
+
+def test_apply_rows_matches_assembled_operator():
+    """Row-by-row evaluation (used for sampled checks on large meshes) equals the assembled
+    constrained operator, for space-time and extruded designs in 2+1D and 3+1D."""
+    rng = np.random.default_rng(12)
+    for ns, nt, st in (((5, 4), 6, True), ((5, 4), 3, False), ((3, 2, 2), 3, False)):
+        m = O.Mesh(ns, nt, mat=O.Material(), bc="patch_bottom", bc_width=0.6)
+        g = rng.random(m.elem_shape if st else tuple(reversed(ns)))
+        A = O.assemble(m, g)
+        x = rng.random(m.n_nodes)
+        rows = np.arange(m.n_nodes)
+        np.testing.assert_allclose(O.apply_rows(m, g, x, rows), A @ x, rtol=1e-13, atol=1e-15)
