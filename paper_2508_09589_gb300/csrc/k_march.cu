@@ -1,0 +1,77 @@
+// 27-point stencils of levels whose coefficients do not change along time (every level of
+// an extruded design, Sec. 3.4.1) in 2 spatial dimensions.  Row (n, p) of a level operator
+// is the sum over the adjacent elements of the masked element-matrix rows: Galerkin blocks
+// T_ab on coarse levels (Sec. 3.2), C_e (D_t (x) M_x) + k_e (M_t (x) K_x) on level 0 (Sec.
+// 3.1).  Gathered per spatial node p and plane class they form the stencil applied by the
+// time-marching kernels (march2d).
+#include <math.h>
+
+#include "st_device.cuh"
+
+namespace st {
+
+// class c: 0 first free plane (n = 1 < n_t), 1 interior, 2 last (n = n_t >= 2), 3 n_t == 1.
+// The slab below plane n is the first slab (version 0) iff n == 1; the slab above is interior.
+template <int LV>
+__global__ void k_stencil_build(OpL0<double> o0, OpLc<double> oc, double* __restrict__ out64,
+                                float* __restrict__ out32, unsigned char* __restrict__ dir) {
+    constexpr int NS = 4, NSYM = 10, NV = 40;
+    const Geom& g = LV == 0 ? o0.g : oc.g;
+    const long long P = (long long)g.nx1 * g.ny1;
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const int i = (int)(p % g.nx1), j = (int)(p / g.nx1);
+    dir[p] = sp_dir<2>(g, i, j, 0) ? 1 : 0;
+    double F[NV];
+    for (int tr = 0; tr < 2; ++tr)
+        for (int c = 0; c < 4; ++c) {
+            double s[27];
+            for (int q = 0; q < 27; ++q) s[q] = 0.0;
+            const bool has_above = (c == 0 || c == 1);
+            const int slab_below = (c == 0 || c == 3) ? 0 : 1;  // representative slab of its version
+            for (int o = 0; o < NS; ++o) {
+                const int ex = i - 1 + (o & 1), ey = j - 1 + ((o >> 1) & 1);
+                if (ex < 0 || ex >= g.nex || ey < 0 || ey >= g.ney) continue;
+                const int as = (~o) & (NS - 1);
+                const long long se = (long long)ey * g.nex + ex;
+                for (int sb = 0; sb < 2; ++sb) {
+                    if (sb == 1 && !has_above) continue;
+                    const int at = 1 - sb;
+                    const int slab = sb == 0 ? slab_below : 1;
+                    if constexpr (LV == 0) {
+                        l0_blocks<2>(o0, slab, ex, ey, 0, F);
+                    } else {
+                        const double* A = oc.elem + elem_index(oc, slab, se) * NV;
+                        for (int q = 0; q < NV; ++q) F[q] = A[q];
+                    }
+                    for (int bt = 0; bt < 2; ++bt) {
+                        const int blk = tr ? (bt * 2 + at) : (at * 2 + bt);
+                        const int dt = sb + bt;  // plane offset index: 0 (n-1), 1 (n), 2 (n+1)
+                        for (int bs = 0; bs < NS; ++bs) {
+                            const int di = ex + (bs & 1) - i + 1, dj = ey + ((bs >> 1) & 1) - j + 1;
+                            s[dt * 9 + dj * 3 + di] += F[blk * NSYM + symidx<NS>(as, bs)];
+                        }
+                    }
+                }
+            }
+            for (int q = 0; q < 27; ++q) {
+                const long long o = (long long)((tr * 4 + c) * 27 + q) * P + p;
+                out64[o] = s[q];
+                out32[o] = (float)s[q];
+            }
+        }
+}
+
+void launch_stencil_build(int lvl, const OpL0<double>& o0, const OpLc<double>& oc, double* st64, float* st32,
+                          unsigned char* dir, cudaStream_t s) {
+    note_launch(s);
+    const Geom& g = lvl == 0 ? o0.g : oc.g;
+    const long long P = (long long)g.nx1 * g.ny1;
+    const int blocks = (int)((P + 127) / 128);
+    if (lvl == 0)
+        k_stencil_build<0><<<blocks, 128, 0, s>>>(o0, oc, st64, st32, dir);
+    else
+        k_stencil_build<1><<<blocks, 128, 0, s>>>(o0, oc, st64, st32, dir);
+}
+
+}  // namespace st

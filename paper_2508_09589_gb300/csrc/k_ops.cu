@@ -200,6 +200,7 @@ __global__ void __launch_bounds__(256) k_sm_start(OpL0<T> o0, OpLc<T> oc, const 
     const Geom& g = LV == 0 ? o0.g : oc.g;
     LoadPlain<T, T> ld{x};
     double acc[1] = {0.0};
+    T accT = T(0);
     ST_NODE_LOOP_BEGIN(g)
     T r;
     if (ZERO) {
@@ -211,19 +212,12 @@ __global__ void __launch_bounds__(256) k_sm_start(OpL0<T> o0, OpLc<T> oc, const 
             r = b[idx_] - x[idx_];
         u0[idx_] = r;
     }
-    acc[0] += (double)r * (double)r;
+    accT += r * r;
     ST_NODE_LOOP_END
+    acc[0] = (double)accT;
     __shared__ double out[1];
     if (reduce_publish<1>(acc, 1, rb, out)) {
-        if (threadIdx.x == 0 && threadIdx.y == 0) {
-            const double beta = sqrt(out[0]);
-            st->beta = beta;
-            st->stop = !(beta > 0.0 && isfinite(beta));
-            st->s[0] = st->stop ? 0.0 : 1.0 / beta;
-            st->kdim = steps;
-            st->g[0] = beta;
-            for (int q = 0; q < kMaxSmooth; ++q) st->coef[q] = 0.0;
-        }
+        if (threadIdx.x == 0 && threadIdx.y == 0) sm_start_finish(st, out[0], steps);
     }
 }
 
@@ -234,7 +228,9 @@ __global__ void __launch_bounds__(256) k_sm_apply(OpL0<T> o0, OpLc<T> oc, const 
     if (st->stop || j >= st->kdim) return;
     const Geom& g = LV == 0 ? o0.g : oc.g;
     LoadScaled<T> ld{U.u[j], dinv};
-    double acc[kMaxSmooth] = {0.0};
+    T accT[kMaxSmooth];
+#pragma unroll
+    for (int q = 0; q < kMaxSmooth; ++q) accT[q] = T(0);
     ST_NODE_LOOP_BEGIN(g)
     T v;
     if (is_free<SD>(g, i_, j_, k_, n_))
@@ -244,13 +240,14 @@ __global__ void __launch_bounds__(256) k_sm_apply(OpL0<T> o0, OpLc<T> oc, const 
     w[idx_] = v;
 #pragma unroll
     for (int q = 0; q < kMaxSmooth; ++q)
-        if (q <= j) acc[q] += (double)v * (double)U.u[q][idx_];
+        if (q <= j) accT[q] += v * U.u[q][idx_];
     ST_NODE_LOOP_END
+    double acc[kMaxSmooth];
+#pragma unroll
+    for (int q = 0; q < kMaxSmooth; ++q) acc[q] = (double)accT[q];
     __shared__ double out[kMaxSmooth];
     if (reduce_publish<kMaxSmooth>(acc, j + 1, rb, out)) {
-        if (threadIdx.x == 0 && threadIdx.y == 0) {
-            for (int q = 0; q <= j; ++q) st->H[q * kMaxSmooth + j] = st->s[q] * st->s[j] * out[q];
-        }
+        if (threadIdx.x == 0 && threadIdx.y == 0) sm_apply_finish(st, out, j);
     }
 }
 
@@ -266,14 +263,16 @@ __global__ void __launch_bounds__(256) k_sm_update(Geom g, Basis<T> U, const T* 
     __syncthreads();
     T* un = U.u[j + 1];
     double acc[1] = {0.0};
+    T accT = T(0);
     ST_NODE_LOOP_BEGIN(g)
     T v = sj * w[idx_];
 #pragma unroll
     for (int q = 0; q < kMaxSmooth; ++q)
         if (q <= j) v -= cf[q] * U.u[q][idx_];
     un[idx_] = v;
-    acc[0] += (double)v * (double)v;
+    accT += v * v;
     ST_NODE_LOOP_END
+    acc[0] = (double)accT;
     __shared__ double out[1];
     if (reduce_publish<1>(acc, 1, rb, out)) {
         if (tid == 0) {
@@ -384,8 +383,7 @@ __global__ void __launch_bounds__(256) k_fg_apply_dots(OpL0<double> op, const TZ
     ST_NODE_LOOP_END
     __shared__ double out[32];
     if (reduce_publish<32>(dots, j + 1, rb, out)) {
-        if (threadIdx.x == 0 && threadIdx.y == 0)
-            for (int q = 0; q <= j; ++q) fs->h1[q] = out[q];
+        if (threadIdx.x == 0 && threadIdx.y == 0) fg_apply_finish(fs, out, j);
     }
 }
 
@@ -488,11 +486,7 @@ __global__ void __launch_bounds__(256) k_fg_residual(OpL0<double> op, const doub
     ST_NODE_LOOP_END
     __shared__ double out[1];
     if (reduce_publish<1>(acc, 1, rb, out)) {
-        if (threadIdx.x == 0 && threadIdx.y == 0) {
-            fs->beta = sqrt(out[0]);
-            fs->res_est = fs->beta;
-            fs->bad = !isfinite(fs->beta);
-        }
+        if (threadIdx.x == 0 && threadIdx.y == 0) fg_residual_finish(fs, out[0]);
     }
 }
 
@@ -533,6 +527,157 @@ __global__ void __launch_bounds__(256) k_mask_copy(Geom g, const double* __restr
     ST_NODE_LOOP_END
 }
 
+
+// ---------------------------------------------------------------- time-marching variants
+// Used when the level carries 27-point stencils (extruded design, 2 spatial dimensions).
+template <typename T>
+__global__ void __launch_bounds__(256) km_apply(Geom g, const T* __restrict__ coef, const unsigned char* __restrict__ dir,
+                                                int chunk, const T* __restrict__ x, T* __restrict__ y) {
+    LoadPlain<T, T> ld{x};
+    march2d<T>(g, coef, dir, ld, chunk, [&](long long q, T v) { y[q] = v; });
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) km_residual(Geom g, const T* __restrict__ coef,
+                                                   const unsigned char* __restrict__ dir, int chunk,
+                                                   const T* __restrict__ b, const T* __restrict__ x,
+                                                   T* __restrict__ r) {
+    LoadPlain<T, T> ld{x};
+    march2d<T>(g, coef, dir, ld, chunk, [&](long long q, T v) { r[q] = b[q] - v; });
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) km_sm_start(Geom g, const T* __restrict__ coef,
+                                                   const unsigned char* __restrict__ dir, int chunk,
+                                                   const T* __restrict__ b, const T* __restrict__ x,
+                                                   T* __restrict__ u0, int steps, SmState* st, RedBuf rb) {
+    LoadPlain<T, T> ld{x};
+    T accT = T(0);
+    march2d<T>(g, coef, dir, ld, chunk, [&](long long q, T v) {
+        const T r = b[q] - v;
+        u0[q] = r;
+        accT += r * r;
+    });
+    double acc[1] = {(double)accT};
+    __shared__ double out[1];
+    if (reduce_publish<1>(acc, 1, rb, out)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) sm_start_finish(st, out[0], steps);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) km_sm_apply(Geom g, const T* __restrict__ coef,
+                                                   const unsigned char* __restrict__ dir, int chunk,
+                                                   const T* __restrict__ dinv, Basis<T> U, T* __restrict__ w, int j,
+                                                   SmState* st, RedBuf rb) {
+    if (st->stop || j >= st->kdim) return;
+    LoadScaled<T> ld{U.u[j], dinv};
+    T accT[kMaxSmooth];
+#pragma unroll
+    for (int q = 0; q < kMaxSmooth; ++q) accT[q] = T(0);
+    march2d<T>(g, coef, dir, ld, chunk, [&](long long q, T v) {
+        w[q] = v;
+#pragma unroll
+        for (int s = 0; s < kMaxSmooth; ++s)
+            if (s <= j) accT[s] += v * U.u[s][q];
+    });
+    double acc[kMaxSmooth];
+#pragma unroll
+    for (int q = 0; q < kMaxSmooth; ++q) acc[q] = (double)accT[q];
+    __shared__ double out[kMaxSmooth];
+    if (reduce_publish<kMaxSmooth>(acc, j + 1, rb, out)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) sm_apply_finish(st, out, j);
+    }
+}
+
+template <typename TZ>
+__global__ void __launch_bounds__(256) km_fg_apply_dots(Geom g, const double* __restrict__ coef,
+                                                        const unsigned char* __restrict__ dir, int chunk,
+                                                        const TZ* __restrict__ z, TZ* __restrict__ zstore,
+                                                        double* __restrict__ w, VPtrs V, int j, FgState* fs,
+                                                        RedBuf rb) {
+    LoadPlain<double, TZ> ld{z};
+    double dots[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) dots[q] = 0.0;
+    march2d<double>(g, coef, dir, ld, chunk, [&](long long q, double v) {
+        w[q] = v;
+        zstore[q] = z[q];
+#pragma unroll
+        for (int s = 0; s < 32; ++s)
+            if (s <= j) dots[s] += v * V.v[s][q];
+    });
+    __shared__ double out[32];
+    if (reduce_publish<32>(dots, j + 1, rb, out)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) fg_apply_finish(fs, out, j);
+    }
+}
+
+__global__ void __launch_bounds__(256) km_fg_residual(Geom g, const double* __restrict__ coef,
+                                                      const unsigned char* __restrict__ dir, int chunk,
+                                                      const double* __restrict__ f, const double* __restrict__ x,
+                                                      double* __restrict__ r, FgState* fs, RedBuf rb) {
+    LoadPlain<double, double> ld{x};
+    double acc[1] = {0.0};
+    march2d<double>(g, coef, dir, ld, chunk, [&](long long q, double v) {
+        const double rr = f[q] - v;
+        r[q] = rr;
+        acc[0] += rr * rr;
+    });
+    __shared__ double out[1];
+    if (reduce_publish<1>(acc, 1, rb, out)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) fg_residual_finish(fs, out[0]);
+    }
+}
+
+
+// Smoother step apply only (dots in a streaming kernel): w = A (D^{-1} u_j).
+template <typename T>
+__global__ void __launch_bounds__(256) km_sm_applyw(Geom g, const T* __restrict__ coef,
+                                                    const unsigned char* __restrict__ dir, int chunk,
+                                                    const T* __restrict__ dinv, const T* __restrict__ uj,
+                                                    T* __restrict__ w, int j, const SmState* st) {
+    if (st->stop || j >= st->kdim) return;
+    LoadScaled<T> ld{uj, dinv};
+    march2d<T>(g, coef, dir, ld, chunk, [&](long long q, T v) { w[q] = v; });
+}
+
+template <int SD, typename T, int LV, bool TR>
+__global__ void __launch_bounds__(256) k_sm_applyw(OpL0<T> o0, OpLc<T> oc, const T* __restrict__ dinv,
+                                                   const T* __restrict__ uj, T* __restrict__ w, int j,
+                                                   const SmState* st) {
+    if (st->stop || j >= st->kdim) return;
+    const Geom& g = LV == 0 ? o0.g : oc.g;
+    LoadScaled<T> ld{uj, dinv};
+    ST_NODE_LOOP_BEGIN(g)
+    w[idx_] = is_free<SD>(g, i_, j_, k_, n_) ? op_row<SD, T, LV, TR>(o0, oc, i_, j_, k_, n_, ld) : ld(idx_);
+    ST_NODE_LOOP_END
+}
+
+// FGMRES: w = A z (FP64) and the copy of z into the basis Z_j.
+template <typename TZ>
+__global__ void __launch_bounds__(256) km_fg_apply(Geom g, const double* __restrict__ coef,
+                                                   const unsigned char* __restrict__ dir, int chunk,
+                                                   const TZ* __restrict__ z, TZ* __restrict__ zstore,
+                                                   double* __restrict__ w) {
+    LoadPlain<double, TZ> ld{z};
+    march2d<double>(g, coef, dir, ld, chunk, [&](long long q, double v) {
+        w[q] = v;
+        zstore[q] = z[q];
+    });
+}
+
+template <int SD, typename TZ, bool TR>
+__global__ void __launch_bounds__(256) k_fg_apply(OpL0<double> op, const TZ* __restrict__ z, TZ* __restrict__ zstore,
+                                                  double* __restrict__ w) {
+    const Geom& g = op.g;
+    LoadPlain<double, TZ> ld{z};
+    ST_NODE_LOOP_BEGIN(g)
+    w[idx_] = is_free<SD>(g, i_, j_, k_, n_) ? row_l0<SD, double, TR>(op, i_, j_, k_, n_, ld) : (double)z[idx_];
+    zstore[idx_] = z[idx_];
+    ST_NODE_LOOP_END
+}
+
 // ---------------------------------------------------------------- launch wrappers
 #define ST_SD_DISPATCH(sd, ...) \
     do {                        \
@@ -561,6 +706,12 @@ static OpL0<T> dummy_l0(const Geom& g) {
 template <typename T>
 void launch_apply_l0(int sd, const OpL0<T>& op, bool tr, const T* x, T* y, cudaStream_t s) {
     note_launch(s);
+    if (sd == 2 && op.st_dir) {
+        dim3 grid, block;
+        const MarchGrid mg = march_grid(op.g, grid, block);
+        km_apply<T><<<grid, block, 0, s>>>(op.g, op.st_coef[tr ? 1 : 0], op.st_dir, mg.chunk, x, y);
+        return;
+    }
     const LaunchCfg c = node_cfg(op.g);
     const OpLc<T> oc = dummy_lc<T>(op.g);
     ST_SD_DISPATCH(sd, if (tr) k_apply<SD, T, 0, true><<<c.grid, c.block, 0, s>>>(op, oc, x, y);
@@ -569,6 +720,12 @@ void launch_apply_l0(int sd, const OpL0<T>& op, bool tr, const T* x, T* y, cudaS
 template <typename T>
 void launch_apply_lc(int sd, const OpLc<T>& op, bool tr, const T* x, T* y, cudaStream_t s) {
     note_launch(s);
+    if (sd == 2 && op.st_dir) {
+        dim3 grid, block;
+        const MarchGrid mg = march_grid(op.g, grid, block);
+        km_apply<T><<<grid, block, 0, s>>>(op.g, op.st_coef[tr ? 1 : 0], op.st_dir, mg.chunk, x, y);
+        return;
+    }
     const LaunchCfg c = node_cfg(op.g);
     const OpL0<T> o0 = dummy_l0<T>(op.g);
     ST_SD_DISPATCH(sd, if (tr) k_apply<SD, T, 1, true><<<c.grid, c.block, 0, s>>>(o0, op, x, y);
@@ -592,6 +749,17 @@ template <typename T>
 void launch_residual(int sd, int lvl, const OpL0<T>& o0, const OpLc<T>& oc, bool tr, const T* b, const T* x, T* r,
                      cudaStream_t s) {
     note_launch(s);
+    {
+        const Geom& g = lvl == 0 ? o0.g : oc.g;
+        const unsigned char* dir = lvl == 0 ? o0.st_dir : oc.st_dir;
+        if (sd == 2 && dir) {
+            const T* coef = lvl == 0 ? o0.st_coef[tr ? 1 : 0] : oc.st_coef[tr ? 1 : 0];
+            dim3 grid, block;
+            const MarchGrid mg = march_grid(g, grid, block);
+            km_residual<T><<<grid, block, 0, s>>>(g, coef, dir, mg.chunk, b, x, r);
+            return;
+        }
+    }
     const LaunchCfg c = node_cfg(lvl == 0 ? o0.g : oc.g);
     if (lvl == 0) {
         ST_SD_DISPATCH(sd, if (tr) k_residual<SD, T, 0, true><<<c.grid, c.block, 0, s>>>(o0, oc, b, x, r);
@@ -614,23 +782,51 @@ void launch_prolong(const Geom& gf, const Geom& gc, int kind, int sd, const T* x
     ST_SD_DISPATCH(sd, k_prolong<SD, T><<<c.grid, c.block, 0, s>>>(gf, gc, kind, xc, xf));
 }
 
+// Below this many nodes a level's Arnoldi step is latency bound: the fused stencil + dots
+// kernel (one launch fewer) is used; above it the apply, dots and update run as separate
+// bandwidth-efficient kernels.
+constexpr long long kSplitNodes = 200000;
+
 template <int SD, typename T, int LV, bool TR>
 static void smooth_impl(const OpL0<T>& o0, const OpLc<T>& oc, const T* b, T* x, const T* dinv, Basis<T> U, T* w,
                         int steps, bool zero_init, SmState* st, RedBuf rb, cudaStream_t s) {
-    note_launch(s, 2 + 2 * steps);
     const Geom& g = LV == 0 ? o0.g : oc.g;
+    const long long N = g.nnodes;
     const LaunchCfg c = node_cfg(g);
+    const unsigned char* dir = LV == 0 ? o0.st_dir : oc.st_dir;
+    const bool march = SD == 2 && dir != nullptr;
+    const T* coef = march ? (LV == 0 ? o0.st_coef[TR ? 1 : 0] : oc.st_coef[TR ? 1 : 0]) : nullptr;
+    dim3 mgrid, mblock;
+    const MarchGrid mg = march_grid(g, mgrid, mblock);
+    if (zero_init) U.u[0] = const_cast<T*>(b);
+    Ptrs<T> P{};
+    for (int q = 0; q <= steps; ++q) P.p[q] = U.u[q];
+    const bool split = N >= kSplitNodes;
     if (zero_init) {
-        U.u[0] = const_cast<T*>(b);
-        k_sm_start<SD, T, LV, TR, true><<<c.grid, c.block, 0, s>>>(o0, oc, b, x, nullptr, steps, st, rb);
+        launch_sm_norm<T>(N, b, steps, st, rb, s);
     } else {
-        k_sm_start<SD, T, LV, TR, false><<<c.grid, c.block, 0, s>>>(o0, oc, b, x, U.u[0], steps, st, rb);
+        note_launch(s);
+        if (march)
+            km_sm_start<T><<<mgrid, mblock, 0, s>>>(g, coef, dir, mg.chunk, b, x, U.u[0], steps, st, rb);
+        else
+            k_sm_start<SD, T, LV, TR, false><<<c.grid, c.block, 0, s>>>(o0, oc, b, x, U.u[0], steps, st, rb);
     }
     for (int j = 0; j < steps; ++j) {
-        k_sm_apply<SD, T, LV, TR><<<c.grid, c.block, 0, s>>>(o0, oc, dinv, U, w, j, st, rb);
-        k_sm_update<T><<<c.grid, c.block, 0, s>>>(g, U, w, j, steps, st, rb);
+        note_launch(s);
+        if (split) {
+            if (march)
+                km_sm_applyw<T><<<mgrid, mblock, 0, s>>>(g, coef, dir, mg.chunk, dinv, U.u[j], w, j, st);
+            else
+                k_sm_applyw<SD, T, LV, TR><<<c.grid, c.block, 0, s>>>(o0, oc, dinv, U.u[j], w, j, st);
+            launch_dots<T>(N, w, P, j + 1, j, 0, st, rb, s);
+        } else if (march) {
+            km_sm_apply<T><<<mgrid, mblock, 0, s>>>(g, coef, dir, mg.chunk, dinv, U, w, j, st, rb);
+        } else {
+            k_sm_apply<SD, T, LV, TR><<<c.grid, c.block, 0, s>>>(o0, oc, dinv, U, w, j, st, rb);
+        }
+        launch_update<T>(N, w, U.u[j + 1], P, j, steps, 0, st, rb, s);
     }
-    k_sm_finish<T><<<c.grid, c.block, 0, s>>>(g, x, dinv, U, zero_init ? 1 : 0, st);
+    launch_sm_combine<T>(N, x, dinv, P, steps, zero_init, st, s);
 }
 
 template <typename T>
@@ -658,20 +854,25 @@ template <typename TZ>
 void launch_fg_apply_dots(int sd, const OpL0<double>& op, bool tr, const TZ* z, TZ* zstore, double* w,
                           double* const* V, int j, FgState* fs, RedBuf rb, cudaStream_t s) {
     note_launch(s);
-    VPtrs vp{};
-    for (int q = 0; q <= j && q <= kMaxRestart; ++q) vp.v[q] = V[q];
-    const LaunchCfg c = node_cfg(op.g);
-    ST_SD_DISPATCH(sd, if (tr) k_fg_apply_dots<SD, TZ, true><<<c.grid, c.block, 0, s>>>(op, z, zstore, w, vp, j, fs, rb);
-                   else k_fg_apply_dots<SD, TZ, false><<<c.grid, c.block, 0, s>>>(op, z, zstore, w, vp, j, fs, rb));
+    if (sd == 2 && op.st_dir) {
+        dim3 grid, block;
+        const MarchGrid mg = march_grid(op.g, grid, block);
+        km_fg_apply<TZ><<<grid, block, 0, s>>>(op.g, op.st_coef[tr ? 1 : 0], op.st_dir, mg.chunk, z, zstore, w);
+    } else {
+        const LaunchCfg c = node_cfg(op.g);
+        ST_SD_DISPATCH(sd, if (tr) k_fg_apply<SD, TZ, true><<<c.grid, c.block, 0, s>>>(op, z, zstore, w);
+                       else k_fg_apply<SD, TZ, false><<<c.grid, c.block, 0, s>>>(op, z, zstore, w));
+    }
+    Ptrs<double> P{};
+    for (int q = 0; q <= j; ++q) P.p[q] = V[q];
+    launch_dots<double>(op.g.nnodes, w, P, j + 1, j, 1, fs, rb, s);
 }
 
 void launch_fg_update_dots(const Geom& g, double* w, double* const* V, int j, int pass, FgState* fs, RedBuf rb,
                            cudaStream_t s) {
-    note_launch(s);
-    VPtrs vp{};
-    for (int q = 0; q <= j && q <= kMaxRestart; ++q) vp.v[q] = V[q];
-    const LaunchCfg c = node_cfg(g);
-    k_fg_update<<<c.grid, c.block, 0, s>>>(g, w, vp, j, pass, fs, rb);
+    Ptrs<double> P{};
+    for (int q = 0; q <= j; ++q) P.p[q] = V[q];
+    launch_update<double>(g.nnodes, w, w, P, j, 0, pass == 0 ? 1 : 2, fs, rb, s);
 }
 
 template <typename TZ>
@@ -684,18 +885,23 @@ void launch_fg_normalize(const Geom& g, const double* w, double* vnext, TZ* bmg,
 
 template <typename TZ>
 void launch_fg_update_x(const Geom& g, double* x, TZ* const* Z, int k, FgState* fs, cudaStream_t s) {
-    if (k > 0) note_launch(s, 2);
     if (k <= 0) return;
+    note_launch(s);
     k_fg_backsolve<<<1, 32, 0, s>>>(fs, k);
-    ZPtrs<TZ> zp{};
-    for (int q = 0; q < k; ++q) zp.z[q] = Z[q];
-    const LaunchCfg c = node_cfg(g);
-    k_fg_update_x<TZ><<<c.grid, c.block, 0, s>>>(g, x, zp, k, fs);
+    Ptrs<TZ> P{};
+    for (int q = 0; q < k; ++q) P.p[q] = Z[q];
+    launch_fg_combine<TZ>(g.nnodes, x, P, k, fs, s);
 }
 
 void launch_fg_residual(int sd, const OpL0<double>& op, bool tr, const double* f, const double* x, double* r,
                         FgState* fs, RedBuf rb, cudaStream_t s) {
     note_launch(s);
+    if (sd == 2 && op.st_dir) {
+        dim3 grid, block;
+        const MarchGrid mg = march_grid(op.g, grid, block);
+        km_fg_residual<<<grid, block, 0, s>>>(op.g, op.st_coef[tr ? 1 : 0], op.st_dir, mg.chunk, f, x, r, fs, rb);
+        return;
+    }
     const LaunchCfg c = node_cfg(op.g);
     ST_SD_DISPATCH(sd, if (tr) k_fg_residual<SD, true><<<c.grid, c.block, 0, s>>>(op, f, x, r, fs, rb);
                    else k_fg_residual<SD, false><<<c.grid, c.block, 0, s>>>(op, f, x, r, fs, rb));

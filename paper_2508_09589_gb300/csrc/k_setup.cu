@@ -35,39 +35,6 @@ __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ ou
         out[q] = (float)in[q];
 }
 
-// ---------------------------------------------------------------- element blocks
-// Masked element matrix of element (slab, spatial ex, ey, ez) in block form:
-// F[a_t * 2 + b_t][sym(a_s, b_s)], rows and columns of prescribed nodes zeroed.
-template <int SD>
-__device__ void l0_blocks(const OpL0<double>& op, int slab, int ex, int ey, int ez, double* F) {
-    constexpr int NS = 1 << SD, NSYM = NS * (NS + 1) / 2;
-    const Geom& g = op.g;
-    const long long se = ((long long)ez * g.ney + ey) * g.nex + ex;
-    double C, k;
-    coef_l0(op, op.tc ? se : (long long)slab * g.sp_elems + se, C, k);
-    bool fr[2 * NS];
-    for (int at = 0; at < 2; ++at)
-        for (int as = 0; as < NS; ++as)
-            fr[at * NS + as] = (slab + at > 0) &&
-                               !sp_dir<SD>(g, ex + (as & 1), ey + ((as >> 1) & 1), SD == 3 ? ez + ((as >> 2) & 1) : 0);
-    const double Dt[2][2] = {{0.0, 0.0}, {-1.0, 1.0}};
-    const double Mt[2][2] = {{2.0 * op.dt6, op.dt6}, {op.dt6, 2.0 * op.dt6}};
-    for (int at = 0; at < 2; ++at)
-        for (int bt = 0; bt < 2; ++bt)
-            for (int as = 0; as < NS; ++as)
-                for (int bs = as; bs < NS; ++bs) {
-                    const double v = C * Dt[at][bt] * op.mxd[as ^ bs] + k * Mt[at][bt] * op.kxd[as ^ bs];
-                    const bool m = fr[at * NS + as] && fr[bt * NS + bs];
-                    F[(at * 2 + bt) * NSYM + symidx<NS>(as, bs)] = m ? v : 0.0;
-                }
-}
-
-// Interpolation weight of coarse local node b (0|1) at fine position r (0, 1, 2) along a
-// halved axis: r = 0 -> (1, 0), r = 1 -> (1/2, 1/2), r = 2 -> (0, 1).
-__device__ __forceinline__ double q1(int r, int b) {
-    return r == 1 ? 0.5 : ((r == 0) == (b == 0) ? 1.0 : 0.0);
-}
-
 // One coarse element: A_E = M_E (sum_children Q_c^T A_c Q_c) M_E with Q_c = Q_t (x) Q_s.
 template <int SD, int LV>
 __global__ void k_build(OpL0<double> f0, OpLc<double> fc, Geom gc, int kind, int tc, double* __restrict__ out) {
@@ -201,25 +168,35 @@ __global__ void k_dense_assemble(OpL0<double> o0, OpLc<double> oc, double* __res
 // One Gauss-Jordan elimination step (no pivoting) from src into dst.  After n steps the
 // matrix holds its inverse.  The coarse operators have a positive definite symmetric
 // part (the free block) and identity rows at prescribed nodes, so no pivot vanishes.
-__global__ void k_gj_step(const double* __restrict__ src, double* __restrict__ dst, int n, int kp, int* err) {
+// pinv[kp] holds 1 / pivot of this step; the thread that writes the next pivot stores its
+// reciprocal, so each step needs one division in total.
+__global__ void k_gj_first(const double* __restrict__ A, double* __restrict__ pinv, int* err) {
+    const double p = A[0];
+    if (!(fabs(p) > 1e-300) || !isfinite(p)) *err = 1;
+    pinv[0] = (fabs(p) > 1e-300 && isfinite(p)) ? 1.0 / p : 1.0;
+}
+
+__global__ void k_gj_step(const double* __restrict__ src, double* __restrict__ dst, int n, int kp,
+                          double* __restrict__ pinv, int* err) {
     const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (q >= (long long)n * n) return;
     const int i = (int)(q / n), j = (int)(q % n);
-    double p = src[(long long)kp * n + kp];
-    if (!(fabs(p) > 1e-300) || !isfinite(p)) {
-        if (q == 0) *err = 1;
-        p = 1.0;
-    }
+    const double ip = pinv[kp];
     double v;
     if (i == kp && j == kp)
-        v = 1.0 / p;
+        v = ip;
     else if (i == kp)
-        v = src[(long long)kp * n + j] / p;
+        v = src[(long long)kp * n + j] * ip;
     else if (j == kp)
-        v = -src[(long long)i * n + kp] / p;
+        v = -src[(long long)i * n + kp] * ip;
     else
-        v = src[q] - src[(long long)i * n + kp] * src[(long long)kp * n + j] / p;
+        v = src[q] - src[(long long)i * n + kp] * (src[(long long)kp * n + j] * ip);
     dst[q] = v;
+    if (i == kp + 1 && j == kp + 1) {
+        const bool ok = fabs(v) > 1e-300 && isfinite(v);
+        if (!ok) *err = 1;
+        pinv[kp + 1] = ok ? 1.0 / v : 1.0;
+    }
 }
 
 // ---------------------------------------------------------------- source (Sec. 3.1.2)
@@ -412,14 +389,15 @@ void launch_dense_assemble(int sd, int lvl, const OpL0<double>& o0, const OpLc<d
     }
 }
 
-void launch_gauss_jordan(double* A, double* B, int n, int* err, cudaStream_t s) {
-    note_launch(s, n);
+void launch_gauss_jordan(double* A, double* B, double* pinv, int n, int* err, cudaStream_t s) {
+    note_launch(s, n + 1);
     const long long nn = (long long)n * n;
     const int blocks = (int)((nn + 255) / 256);
     double* src = A;
     double* dst = B;
+    k_gj_first<<<1, 1, 0, s>>>(A, pinv, err);
     for (int kp = 0; kp < n; ++kp) {
-        k_gj_step<<<blocks, 256, 0, s>>>(src, dst, n, kp, err);
+        k_gj_step<<<blocks, 256, 0, s>>>(src, dst, n, kp, pinv, err);
         double* t = src;
         src = dst;
         dst = t;

@@ -213,6 +213,17 @@ OpL0<T> Mesh::op0() const {
         o.kxd[mb] = (T)kx;
     }
     o.dt6 = (T)(o.g.dt / 6.0);
+    if (lv[0].sdir) {
+        const long long half = 4LL * 27 * lv[0].g.plane;
+        const T* base;
+        if constexpr (sizeof(T) == 4)
+            base = lv[0].st32;
+        else
+            base = lv[0].st64;
+        o.st_coef[0] = base;
+        o.st_coef[1] = base + half;
+        o.st_dir = lv[0].sdir;
+    }
     return o;
 }
 
@@ -222,6 +233,11 @@ OpLc<double> Mesh::opc<double>(int l) const {
     o.g = lv[l].g;
     o.elem = l > 0 ? lv[l].e64 : nullptr;
     o.tc = layout == ST_DESIGN_EXTRUDED ? 1 : 0;
+    if (l > 0 && lv[l].sdir) {
+        o.st_coef[0] = lv[l].st64;
+        o.st_coef[1] = lv[l].st64 + 4LL * 27 * lv[l].g.plane;
+        o.st_dir = lv[l].sdir;
+    }
     return o;
 }
 
@@ -231,6 +247,11 @@ OpLc<float> Mesh::opc<float>(int l) const {
     o.g = lv[l].g;
     o.elem = l > 0 ? lv[l].e32 : nullptr;
     o.tc = layout == ST_DESIGN_EXTRUDED ? 1 : 0;
+    if (l > 0 && lv[l].sdir) {
+        o.st_coef[0] = lv[l].st32;
+        o.st_coef[1] = lv[l].st32 + 4LL * 27 * lv[l].g.plane;
+        o.st_dir = lv[l].sdir;
+    }
     return o;
 }
 
@@ -324,6 +345,7 @@ st_status create_mesh(const st_mesh_desc* d, Mesh** out) {
     const long long nc = m->lv.back().g.nnodes;
     A((void**)&m->Ainv, nc * nc * sizeof(double));
     A((void**)&m->Awork, nc * nc * sizeof(double));
+    A((void**)&m->pinv, (nc + 1) * sizeof(double));
     if (st == ST_OK && cudaMallocHost((void**)&m->h_fg, sizeof(FgState)) != cudaSuccess) {
         cudaGetLastError();
         st = fail(ST_ERR_OOM, "pinned host allocation failed");
@@ -350,17 +372,31 @@ st_status Mesh::ensure_level_storage() {
     const int tc = layout == ST_DESIGN_EXTRUDED ? 1 : 0;
     if (storage_tc == tc) return ST_OK;
     drop_graphs();
-    for (size_t l = 1; l < lv.size(); ++l) {
+    for (size_t l = 0; l < lv.size(); ++l) {
         release(lv[l].e64);
         release(lv[l].e32);
+        release(lv[l].st64);
+        release(lv[l].st32);
+        release(lv[l].sdir);
         lv[l].e64 = nullptr;
         lv[l].e32 = nullptr;
+        lv[l].st64 = nullptr;
+        lv[l].st32 = nullptr;
+        lv[l].sdir = nullptr;
     }
     for (size_t l = 1; l < lv.size(); ++l) {
         const Geom& g = lv[l].g;
         lv[l].nstore = tc ? 2 * g.sp_elems : (long long)g.net * g.sp_elems;
         CKS(alloc((void**)&lv[l].e64, lv[l].nstore * nvals(sd) * sizeof(double)));
         CKS(alloc((void**)&lv[l].e32, lv[l].nstore * nvals(sd) * sizeof(float)));
+    }
+    if (tc && sd == 2) {
+        for (size_t l = 0; l < lv.size(); ++l) {
+            const long long P = lv[l].g.plane;
+            CKS(alloc((void**)&lv[l].st64, 8LL * 27 * P * sizeof(double)));
+            CKS(alloc((void**)&lv[l].st32, 8LL * 27 * P * sizeof(float)));
+            CKS(alloc((void**)&lv[l].sdir, P));
+        }
     }
     storage_tc = tc;
     return ST_OK;
@@ -404,11 +440,19 @@ st_status set_design(Mesh* m, const double* gamma, int layout, size_t count, int
             launch_build_from_lc(m->sd, m->opc<double>(l - 1), m->lv[l].g, kind, m->lv[l].e64, s);
         launch_to_float(m->lv[l].e64, m->lv[l].e32, m->lv[l].nstore * nvals(m->sd), s);
     }
+    // 27-point stencils of every level (extruded designs, 2 spatial dimensions)
+    if (m->lv[0].sdir) {
+        for (int l = 0; l < L; ++l) {
+            OpL0<double> o0 = m->op0<double>();
+            OpLc<double> oc = m->opc<double>(l);
+            launch_stencil_build(l, o0, oc, m->lv[l].st64, m->lv[l].st32, m->lv[l].sdir, s);
+        }
+    }
     // coarsest operator, dense, and its inverse
     const int nc = (int)m->lv[L - 1].g.nnodes;
     launch_dense_assemble(m->sd, L - 1, m->op0<double>(), m->opc<double>(L - 1), m->Ainv, s);
     CK(cudaMemsetAsync(m->d_err, 0, sizeof(int), s));
-    launch_gauss_jordan(m->Ainv, m->Awork, nc, m->d_err, s);
+    launch_gauss_jordan(m->Ainv, m->Awork, m->pinv, nc, m->d_err, s);
     CK(cudaGetLastError());
     int herr = 0;
     CK(cudaMemcpyAsync(&herr, m->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -45,10 +45,16 @@ __host__ __device__ constexpr int symidx(int i, int j) {
 }
 
 // ---------------------------------------------------------------- loaders
+// Loaders give the operator input at node q.  The raw interface (NR raw values of type R,
+// combined later) lets the time-marching kernels prefetch loads without consuming them.
 template <typename T, typename TX>
 struct LoadPlain {
     const TX* __restrict__ x;
+    using R = TX;
+    static constexpr int NR = 1;
     __device__ __forceinline__ T operator()(long long q) const { return (T)x[q]; }
+    __device__ __forceinline__ void raw(long long q, R* r) const { r[0] = x[q]; }
+    __device__ __forceinline__ static T combine(const R* r) { return (T)r[0]; }
 };
 
 // x_q = d_q u_q (right Jacobi preconditioning inside the smoother)
@@ -56,7 +62,14 @@ template <typename T>
 struct LoadScaled {
     const T* __restrict__ u;
     const T* __restrict__ d;
+    using R = T;
+    static constexpr int NR = 2;
     __device__ __forceinline__ T operator()(long long q) const { return u[q] * d[q]; }
+    __device__ __forceinline__ void raw(long long q, R* r) const {
+        r[0] = u[q];
+        r[1] = d[q];
+    }
+    __device__ __forceinline__ static T combine(const R* r) { return r[0] * r[1]; }
 };
 
 // ---------------------------------------------------------------- level 0 (matrix free)
@@ -286,6 +299,302 @@ __device__ __forceinline__ bool reduce_publish(const double (&v)[NQ], int nq, Re
     if (tid == 0) *rb.counter = 0u;
     __syncthreads();
     return true;
+}
+
+}  // namespace st
+
+namespace st {
+
+// ---------------------------------------------------------------- element blocks
+// Masked element matrix of element (slab, spatial ex, ey, ez) in block form:
+// F[a_t * 2 + b_t][sym(a_s, b_s)], rows and columns of prescribed nodes zeroed.
+template <int SD>
+__device__ void l0_blocks(const OpL0<double>& op, int slab, int ex, int ey, int ez, double* F) {
+    constexpr int NS = 1 << SD, NSYM = NS * (NS + 1) / 2;
+    const Geom& g = op.g;
+    const long long se = ((long long)ez * g.ney + ey) * g.nex + ex;
+    double C, k;
+    coef_l0(op, op.tc ? se : (long long)slab * g.sp_elems + se, C, k);
+    bool fr[2 * NS];
+    for (int at = 0; at < 2; ++at)
+        for (int as = 0; as < NS; ++as)
+            fr[at * NS + as] = (slab + at > 0) &&
+                               !sp_dir<SD>(g, ex + (as & 1), ey + ((as >> 1) & 1), SD == 3 ? ez + ((as >> 2) & 1) : 0);
+    const double Dt[2][2] = {{0.0, 0.0}, {-1.0, 1.0}};
+    const double Mt[2][2] = {{2.0 * op.dt6, op.dt6}, {op.dt6, 2.0 * op.dt6}};
+    for (int at = 0; at < 2; ++at)
+        for (int bt = 0; bt < 2; ++bt)
+            for (int as = 0; as < NS; ++as)
+                for (int bs = as; bs < NS; ++bs) {
+                    const double v = C * Dt[at][bt] * op.mxd[as ^ bs] + k * Mt[at][bt] * op.kxd[as ^ bs];
+                    const bool m = fr[at * NS + as] && fr[bt * NS + bs];
+                    F[(at * 2 + bt) * NSYM + symidx<NS>(as, bs)] = m ? v : 0.0;
+                }
+}
+
+// Interpolation weight of coarse local node b (0|1) at fine position r (0, 1, 2) along a
+// halved axis: r = 0 -> (1, 0), r = 1 -> (1/2, 1/2), r = 2 -> (0, 1).
+inline __device__ double q1(int r, int b) {
+    return r == 1 ? 0.5 : ((r == 0) == (b == 0) ? 1.0 : 0.0);
+}
+
+// ---------------------------------------------------------------- finalisers (last block, thread 0)
+__device__ __forceinline__ void sm_start_finish(SmState* st, double sum, int steps) {
+    const double beta = sqrt(sum);
+    st->beta = beta;
+    st->stop = !(beta > 0.0 && isfinite(beta));
+    st->s[0] = st->stop ? 0.0 : 1.0 / beta;
+    st->kdim = steps;
+    st->g[0] = beta;
+    for (int q = 0; q < kMaxSmooth; ++q) st->coef[q] = 0.0;
+}
+
+__device__ __forceinline__ void sm_apply_finish(SmState* st, const double* out, int j) {
+    for (int q = 0; q <= j; ++q) st->H[q * kMaxSmooth + j] = st->s[q] * st->s[j] * out[q];
+}
+
+__device__ __forceinline__ void fg_apply_finish(FgState* fs, const double* out, int j) {
+    for (int q = 0; q <= j; ++q) fs->h1[q] = out[q];
+}
+
+__device__ __forceinline__ void fg_residual_finish(FgState* fs, double sum) {
+    fs->beta = sqrt(sum);
+    fs->res_est = fs->beta;
+    fs->bad = !isfinite(fs->beta);
+}
+
+// ---------------------------------------------------------------- time-marching stencil core
+// Levels whose coefficients do not change along time (extruded designs) are applied as a
+// 27-point stencil: row(n, p) = sum over planes n-1, n, n+1 and the 3 x 3 neighbourhood of p.
+// Coefficients are stored [class][27][P] (structure of arrays over spatial nodes p) with
+// class 0: n = 1 < n_t, 1: interior, 2: n = n_t >= 2, 3: n_t == 1; prescribed rows (t = 0
+// plane, spatial sink flagged in dir) are the identity.
+struct MarchGrid {
+    int chunk;  // planes per block
+};
+
+inline __host__ MarchGrid march_grid(const Geom& g, dim3& grid, dim3& block) {
+    block = dim3(32, 8, 1);
+    const int gx = (g.nx1 + 31) / 32, gy = (g.ny1 + 7) / 8;
+    long long gz = (long long)kMaxBlocks / ((long long)gx * gy);
+    if (gz < 1) gz = 1;
+    if (gz > g.nt1) gz = g.nt1;
+    const int chunk = (int)((g.nt1 + gz - 1) / gz);
+    gz = (g.nt1 + chunk - 1) / chunk;
+    grid = dim3(gx, gy, (unsigned)gz);
+    return MarchGrid{chunk};
+}
+
+template <typename T, typename LD, typename EMIT>
+__device__ __forceinline__ void march2d(const Geom& g, const T* __restrict__ coef, const unsigned char* __restrict__ dir,
+                                        const LD& ld, int chunk, EMIT&& emit) {
+    // Each thread stages at most 2 of the 34 x 10 cells of a plane (tile + halo).  Planes are
+    // fetched 3 planes ahead into a register ring; loads use clamped (always valid) addresses
+    // and their validity is applied only when staged, so no instruction waits on a load
+    // before its plane is needed.  The plane loop is unrolled by 3 so that the prefetch ring
+    // and the 3-plane neighbourhood window rotate by register renaming.
+    __shared__ T tile_[2][10][34];
+    using R = typename LD::R;
+    constexpr int NR = LD::NR;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 8;
+    const int i = i0 + tx, jj = j0 + ty;
+    const int n0 = blockIdx.z * chunk;
+    const int n1 = min(n0 + chunk, g.nt1);
+    const long long P = (long long)g.nx1 * g.ny1;
+    const bool in = i < g.nx1 && jj < g.ny1;
+    const long long p = in ? (long long)jj * g.nx1 + i : 0;
+    const int nt = g.net;
+    long long cell_off[2];
+    bool cell_ok[2], cell_st[2];
+    int cell_sy[2], cell_sx[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int cidx = tid + r * 256;
+        cell_off[r] = 0;
+        cell_ok[r] = false;
+        cell_st[r] = cidx < 340;
+        cell_sy[r] = 0;
+        cell_sx[r] = 0;
+        if (cidx < 340) {
+            const int cy = cidx / 34, cx = cidx - cy * 34;
+            cell_sy[r] = cy;
+            cell_sx[r] = cx;
+            const int gi = i0 - 1 + cx, gj = j0 - 1 + cy;
+            if (gi >= 0 && gi < g.nx1 && gj >= 0 && gj < g.ny1) {
+                cell_off[r] = (long long)gj * g.nx1 + gi;
+                cell_ok[r] = true;
+            }
+        }
+    }
+    T c[27];
+#pragma unroll
+    for (int q = 0; q < 27; ++q) c[q] = in ? coef[(long long)(27 + q) * P + p] : T(0);
+    const bool dirp = in ? (dir[p] != 0) : true;
+
+    auto fetch = [&](int n, R (&v)[2][NR], bool& ok) {
+        ok = n >= 0 && n <= nt;
+        const long long base = (long long)(n < 0 ? 0 : (n > nt ? nt : n)) * P;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) ld.raw(base + cell_off[r], v[r]);
+    };
+    int buf = 0;
+    auto stage_read = [&](const R (&v)[2][NR], bool ok, T (&dst)[9]) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+            if (cell_st[r]) tile_[buf][cell_sy[r]][cell_sx[r]] = (ok && cell_ok[r]) ? LD::combine(v[r]) : T(0);
+        __syncthreads();
+#pragma unroll
+        for (int dj = 0; dj < 3; ++dj)
+#pragma unroll
+            for (int di = 0; di < 3; ++di) dst[dj * 3 + di] = tile_[buf][ty + dj][tx + di];
+        buf ^= 1;
+    };
+    auto row = [&](int n, const T (&xa)[9], const T (&xb)[9], const T (&xc)[9]) {
+        if (!in) return;
+        T y;
+        if (n == 0 || dirp) {
+            y = xb[4];
+        } else {
+            const int cls = (n == 1) ? (nt == 1 ? 3 : 0) : (n == nt ? 2 : 1);
+            T a0 = 0, a1 = 0, a2 = 0;
+            if (cls == 1) {
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    a0 += c[k] * xa[k];
+                    a1 += c[9 + k] * xb[k];
+                    a2 += c[18 + k] * xc[k];
+                }
+            } else {
+                const T* cc = coef + (long long)cls * 27 * P + p;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    a0 += cc[(long long)k * P] * xa[k];
+                    a1 += cc[(long long)(9 + k) * P] * xb[k];
+                    a2 += cc[(long long)(18 + k) * P] * xc[k];
+                }
+            }
+            y = a0 + a1 + a2;
+        }
+        emit((long long)n * P + p, y);
+    };
+    // prologue: planes n0-1 and n0 into the window, planes n0+1..n0+3 into the ring
+    T x0[9], x1[9], x2[9];
+    R p0[2][NR], p1[2][NR], p2[2][NR];
+    bool k0, k1, k2;
+    fetch(n0 - 1, p0, k0);
+    fetch(n0, p1, k1);
+    stage_read(p0, k0, x0);
+    stage_read(p1, k1, x1);
+    fetch(n0 + 1, p0, k0);
+    fetch(n0 + 2, p1, k1);
+    fetch(n0 + 3, p2, k2);
+    // step(n): window (a, b) = planes n-1, n; ring slot s holds plane n+1 -> stage it into c,
+    // refill s with plane n+4, emit row n.
+    for (int n = n0; n < n1; n += 3) {
+        stage_read(p0, k0, x2);
+        fetch(n + 4, p0, k0);
+        row(n, x0, x1, x2);
+        if (n + 1 < n1) {
+            stage_read(p1, k1, x0);
+            fetch(n + 5, p1, k1);
+            row(n + 1, x1, x2, x0);
+        }
+        if (n + 2 < n1) {
+            stage_read(p2, k2, x1);
+            fetch(n + 6, p2, k2);
+            row(n + 2, x2, x0, x1);
+        }
+    }
+}
+
+}  // namespace st
+
+namespace st {
+
+// Givens rotation of smoother column j and, when the Arnoldi process stops (breakdown or
+// the last step), the back substitution giving the final combination coefficients.
+__device__ inline void sm_givens_column_d(SmState* st, int j) {
+    double col[kMaxSmooth + 1];
+    for (int q = 0; q <= j + 1; ++q) col[q] = st->H[q * kMaxSmooth + j];
+    for (int q = 0; q < j; ++q) {
+        const double c = st->cs[q], s = st->sn[q];
+        const double a = col[q], b = col[q + 1];
+        col[q] = c * a + s * b;
+        col[q + 1] = -s * a + c * b;
+    }
+    const double a = col[j], b = col[j + 1];
+    const double r = hypot(a, b);
+    const double c = r > 0 ? a / r : 1.0, s = r > 0 ? b / r : 0.0;
+    st->cs[j] = c;
+    st->sn[j] = s;
+    col[j] = r;
+    col[j + 1] = 0;
+    st->g[j + 1] = -s * st->g[j];
+    st->g[j] = c * st->g[j];
+    for (int q = 0; q <= j + 1; ++q) st->R[q * kMaxSmooth + j] = col[q];
+}
+
+__device__ inline void sm_backsolve_d(SmState* st, int k) {
+    double y[kMaxSmooth];
+    for (int q = k - 1; q >= 0; --q) {
+        double a = st->g[q];
+        for (int l = q + 1; l < k; ++l) a -= st->R[q * kMaxSmooth + l] * y[l];
+        const double d = st->R[q * kMaxSmooth + q];
+        y[q] = d != 0 ? a / d : 0.0;
+    }
+    for (int q = 0; q < kMaxSmooth; ++q) st->coef[q] = q < k ? y[q] * st->s[q] : 0.0;
+}
+
+__device__ inline void sm_update_finish(SmState* st, double sum, int j, int steps) {
+    const double h = sqrt(sum);
+    st->H[(j + 1) * kMaxSmooth + j] = h;
+    sm_givens_column_d(st, j);
+    const bool brk = !(h > 1e-13 * st->beta) || !isfinite(h);
+    if (brk)
+        st->kdim = j + 1;
+    else
+        st->s[j + 1] = 1.0 / h;
+    if (brk || j + 1 == steps) sm_backsolve_d(st, j + 1);
+}
+
+__device__ inline void fg_givens_column_d(FgState* fs, int j) {
+    double* H = fs->H;
+    for (int q = 0; q < j; ++q) {
+        const double c = fs->cs[q], s = fs->sn[q];
+        const double a = H[q * kMaxRestart + j], b = H[(q + 1) * kMaxRestart + j];
+        H[q * kMaxRestart + j] = c * a + s * b;
+        H[(q + 1) * kMaxRestart + j] = -s * a + c * b;
+    }
+    const double a = H[j * kMaxRestart + j], b = H[(j + 1) * kMaxRestart + j];
+    const double r = hypot(a, b);
+    const double c = r > 0 ? a / r : 1.0, s = r > 0 ? b / r : 0.0;
+    fs->cs[j] = c;
+    fs->sn[j] = s;
+    H[j * kMaxRestart + j] = r;
+    H[(j + 1) * kMaxRestart + j] = 0;
+    fs->g[j + 1] = -s * fs->g[j];
+    fs->g[j] = c * fs->g[j];
+    fs->res_est = fabs(fs->g[j + 1]);
+}
+
+// CGS2 pass 0 done: keep the first projection in H, the second in h1.
+__device__ inline void fg_pass0_finish(FgState* fs, const double* cf, const double* out, int j) {
+    for (int q = 0; q <= j; ++q) {
+        fs->H[q * kMaxRestart + j] = cf[q];
+        fs->h1[q] = out[q];
+    }
+}
+
+// CGS2 pass 1 done: complete column j, its norm and Givens rotation.
+__device__ inline void fg_pass1_finish(FgState* fs, const double* cf, double sum, int j) {
+    for (int q = 0; q <= j; ++q) fs->H[q * kMaxRestart + j] += cf[q];
+    const double h = sqrt(sum);
+    fs->H[(j + 1) * kMaxRestart + j] = h;
+    fs->nrm = h;
+    fg_givens_column_d(fs, j);
+    fs->breakdown = !(h > 0.0);
+    fs->bad = !isfinite(h) || !isfinite(fs->res_est);
 }
 
 }  // namespace st

@@ -57,6 +57,8 @@ struct OpL0 {
     Simp simp;
     T mxd[8], kxd[8];              // M_x, K_x by (a ^ b) over spatial bits
     T dt6;                         // dt / 6 (time mass scale)
+    const T* st_coef[2];           // 27-point stencils [class][27][P] (forward, transposed), or null
+    const unsigned char* st_dir;   // spatial prescribed flags when stencils are present
 };
 
 // Coarse operator (levels >= 1): element matrices in block form, 4 symmetric
@@ -67,6 +69,8 @@ struct OpLc {
     Geom g;
     const T* elem;
     int tc;
+    const T* st_coef[2];           // as in OpL0
+    const unsigned char* st_dir;
 };
 
 // Per-call smoother state (device).
@@ -101,6 +105,12 @@ struct RedBuf {
 template <typename T>
 struct Basis {
     T* u[kMaxSmooth + 1];
+};
+
+// Basis pointers passed by value to the streaming kernels (smoother or FGMRES basis).
+template <typename T>
+struct Ptrs {
+    T* p[kMaxRestart + 1];
 };
 
 struct LaunchCfg {
@@ -163,6 +173,23 @@ void launch_fg_start(const Geom& g, double* v0, TZ* bmg, FgState* fs, cudaStream
 void launch_dot64(const Geom& g, const double* a, const double* b, double* out, RedBuf rb, cudaStream_t s);
 void launch_mask_copy(int sd, const Geom& g, const double* src, double* dst, cudaStream_t s);
 
+// ---- streaming Krylov kernels (k_stream.cu)
+// dots (w, U_q) for q < nq -> smoother column j (fin 0) or FGMRES first projection (fin 1)
+template <typename T>
+void launch_dots(long long n, const T* w, const Ptrs<T>& U, int nq, int j, int fin, void* state, RedBuf rb,
+                 cudaStream_t s);
+// y = a w - sum_{q<=j} c_q U_q; mode 0 smoother step, 1 / 2 FGMRES CGS2 passes (y = w)
+template <typename T>
+void launch_update(long long n, T* w, T* y, const Ptrs<T>& U, int j, int steps, int mode, void* state, RedBuf rb,
+                   cudaStream_t s);
+template <typename T>
+void launch_sm_combine(long long n, T* x, const T* dinv, const Ptrs<T>& U, int steps, bool zero_init,
+                       const SmState* st, cudaStream_t s);
+template <typename T>
+void launch_sm_norm(long long n, const T* b, int steps, SmState* st, RedBuf rb, cudaStream_t s);
+template <typename TZ>
+void launch_fg_combine(long long n, double* x, const Ptrs<TZ>& Z, int k, const FgState* fs, cudaStream_t s);
+
 // ---- setup kernels
 void launch_design_cast(const double* in, double* g64, __nv_bfloat16* g16, long long n, cudaStream_t s);
 void launch_build_from_l0(int sd, const OpL0<double>& f0, const Geom& gc, int kind, int tc, double* elem_c,
@@ -172,13 +199,16 @@ void launch_build_from_lc(int sd, const OpLc<double>& fc, const Geom& gc, int ki
 void launch_to_float(const double* in, float* out, long long n, cudaStream_t s);
 void launch_dense_assemble(int sd, int lvl, const OpL0<double>& o0, const OpLc<double>& oc, double* A,
                            cudaStream_t s);
-void launch_gauss_jordan(double* A, double* B, int n, int* err, cudaStream_t s);  // result in A
+void launch_gauss_jordan(double* A, double* B, double* pinv, int n, int* err, cudaStream_t s);  // result in A
 void launch_rhs(int sd, const Geom& g, int kind, double q0, double a, double b, double f, double* out,
                 cudaStream_t s);
 void launch_pnorm(int sd, const Geom& g, const double* s, int P, double* rhs, double* phi, RedBuf rb,
                   double* scratch, cudaStream_t st);
 void launch_sens(int sd, const OpL0<double>& op, const double* s, const double* lam, double* out,
                  cudaStream_t st);
+// 27-point stencils of a time-constant 2-D level (from level 0 or from stored element blocks)
+void launch_stencil_build(int lvl, const OpL0<double>& o0, const OpLc<double>& oc, double* st64, float* st32,
+                          unsigned char* dir, cudaStream_t s);
 
 // element storage sizes
 inline int nsp(int sd) { return 1 << sd; }

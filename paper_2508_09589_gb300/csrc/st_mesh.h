@@ -18,6 +18,9 @@ struct LevelH {
     long long nstore = 0;      // stored element matrices (levels >= 1)
     double* e64 = nullptr;     // FP64 element blocks
     float* e32 = nullptr;      // FP32 copy for the mixed V-cycle
+    double* st64 = nullptr;    // 27-point stencils [orientation][class][27][P] (extruded, 2-D)
+    float* st32 = nullptr;
+    unsigned char* sdir = nullptr;
 };
 
 template <typename T>
@@ -52,6 +55,7 @@ struct Mesh {
     // coarsest inverse
     double* Ainv = nullptr;
     double* Awork = nullptr;
+    double* pinv = nullptr;
     int* d_err = nullptr;
 
     // FP64 vectors

@@ -46,3 +46,11 @@ def rel_err(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def parity_rtol(A, s, f) -> float:
+    """Outer tolerance for tight parity runs: 1e-13, raised to 20x the FP64 residual floor
+    || |A| |s| || u / ||f|| when the problem's scaling puts the floor above it (the exact
+    solution's own residual in FP64 arithmetic is about that floor)."""
+    floor = np.linalg.norm(abs(A) @ np.abs(s)) * 1.11e-16 / np.linalg.norm(f)
+    return max(1e-13, 20.0 * floor)

@@ -3,15 +3,16 @@
 Sizes are chosen so the oracle finishes in seconds while the meshes span several
 32x8 thread tiles with ragged edges (node counts not multiples of the tile), both
 spatial dimensions (2+1D and 3+1D), both design layouts and every boundary kind.
-Tolerances: FP64 paths 1e-12 (operators) / 1e-10 (solves at rtol 1e-13); FP32 paths
+Tolerances: FP64 paths 1e-12 (operators) / 1e-10 (solves at rtol = max(1e-13, 20x the FP64
+residual floor of the case)); FP32 paths
 use the BF16-rounded design in the oracle and compare at 1e-4 of the largest entry
-(operators) or 2e-3 (ten FP32 GMRES steps).
+(operators) or 5e-3 (ten FP32 GMRES steps).
 """
 import numpy as np
 import pytest
 
 from oracle import st_oracle as O
-from tests.gpu_common import bf16_round, ensure_built, gpu_mesh, rel_err
+from tests.gpu_common import bf16_round, ensure_built, gpu_mesh, parity_rtol, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -51,6 +52,13 @@ def _dev(a, dtype=torch.float64):
     return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
 
 
+def _fp32_design(om, g):
+    """Design the FP32 level-0 operator is built from: extruded 2-D designs are applied as
+    FP32 27-point stencils computed from the FP64 design; all other cases read the BF16 design."""
+    extruded = g.size == int(np.prod(om.ns))
+    return g if (extruded and om.sd == 2) else bf16_round(g)
+
+
 @pytest.mark.parametrize("i", range(len(CASES)))
 @pytest.mark.parametrize("transpose", [False, True])
 def test_fine_operator_fp64_and_fp32(i, transpose):
@@ -63,8 +71,8 @@ def test_fine_operator_fp64_and_fp32(i, transpose):
     y = torch.empty(om.n_nodes, dtype=torch.float64, device="cuda")
     gm.apply(0, _dev(x), y, "fp64", transpose)
     assert rel_err(y.cpu().numpy(), A @ x) < 1e-13
-    # FP32 operator with the BF16 design
-    A16 = O.assemble(om, bf16_round(g))
+    # FP32 operator (BF16 design, or FP32 stencils for extruded 2-D designs)
+    A16 = O.assemble(om, _fp32_design(om, g))
     A16 = A16.T.tocsr() if transpose else A16
     y32 = torch.empty(om.n_nodes, dtype=torch.float32, device="cuda")
     gm.apply(0, _dev(x, torch.float32), y32, "mixed", transpose)
@@ -138,9 +146,9 @@ def test_smoother_matches_oracle_gmres(i, zero_init):
             assert rel_err(x.cpu().numpy(), ref) < 1e-9, (l, tr)
             x32 = _dev(x0, torch.float32)
             gm.smooth(l, _dev(b, torch.float32), x32, 10, zero_init, "mixed", tr)
-            ref32 = ref if l > 0 else O.gmres_jacobi(
-                (O.assemble(om, bf16_round(g)).T.tocsr() if tr else O.assemble(om, bf16_round(g))), b, x0, 10)
-            assert rel_err(x32.cpu().numpy(), ref32) < 2e-3, (l, tr)
+            A32 = O.assemble(om, _fp32_design(om, g))
+            ref32 = ref if l > 0 else O.gmres_jacobi(A32.T.tocsr() if tr else A32, b, x0, 10)
+            assert rel_err(x32.cpu().numpy(), ref32) < 5e-3, (l, tr)
 
 
 def test_smoother_zero_rhs_leaves_zero():
@@ -183,12 +191,14 @@ def test_forward_adjoint_sensitivities(i, precision):
     sens = O.sensitivities(om, g, sol.s, lam, extruded=g.size == int(np.prod(om.ns)))
     gm = gpu_mesh(om, coarse_dof_cap=300)
     gm.set_design(g)
-    st = gm.solve_forward(rtol=1e-13, precision=precision, max_it=400, **_src_kw(src))
-    assert st["converged"] and st["rel_res"] <= 1e-13
-    np.testing.assert_allclose(gm.state("rhs"), sol.f, rtol=0, atol=1e-15 * np.abs(sol.f).max())
+    rt = parity_rtol(sol.A, sol.s, sol.f)
+    st = gm.solve_forward(rtol=rt, precision=precision, max_it=400, **_src_kw(src))
+    assert st["converged"] and st["rel_res"] <= rt
+    np.testing.assert_allclose(gm.state("rhs"), sol.f, rtol=0, atol=1e-14 * np.abs(sol.f).max())
     s = gm.state("T")
     assert rel_err(s, sol.s) < 1e-10
-    phi, sta = gm.solve_adjoint("compliance", rtol=1e-13, precision=precision, max_it=400)
+    phi, sta = gm.solve_adjoint("compliance", rtol=parity_rtol(sol.A.T, lam, sol.f), precision=precision,
+                                max_it=400)
     assert sta["converged"]
     np.testing.assert_allclose(phi, O.compliance(sol.f, sol.s), rtol=1e-11)
     assert rel_err(gm.state("lambda"), lam) < 1e-10
@@ -204,8 +214,8 @@ def test_pnorm_objective_and_adjoint():
     lam = O.adjoint(sol.A, dphi, dm, sol.lu)
     gm = gpu_mesh(om, coarse_dof_cap=300)
     gm.set_design(g)
-    gm.solve_forward(rtol=1e-13, precision="fp64", max_it=400)
-    phi, st = gm.solve_adjoint("pnorm", P=20, rtol=1e-13, precision="fp64", max_it=400)
+    gm.solve_forward(rtol=parity_rtol(sol.A, sol.s, sol.f), precision="fp64", max_it=400)
+    phi, st = gm.solve_adjoint("pnorm", P=20, rtol=parity_rtol(sol.A.T, lam, dphi), precision="fp64", max_it=400)
     np.testing.assert_allclose(phi, phi_ref, rtol=1e-11)
     np.testing.assert_allclose(gm.state("adj_rhs"), np.where(dm, 0, dphi), rtol=1e-11, atol=1e-14 * np.abs(dphi).max())
     assert rel_err(gm.state("lambda"), lam) < 1e-10
@@ -221,7 +231,7 @@ def test_mixed_to_1e8_meets_1e6_and_fp64_meets_1e10():
     st = gm.solve_forward(rtol=1e-8, precision="mixed")
     assert st["converged"] and st["rel_res"] <= 1e-8
     assert rel_err(gm.state("T"), sol.s) < 1e-6
-    st = gm.solve_forward(rtol=1e-13, precision="fp64", max_it=400)
+    st = gm.solve_forward(rtol=parity_rtol(sol.A, sol.s, sol.f), precision="fp64", max_it=400)
     assert rel_err(gm.state("T"), sol.s) < 1e-10
 
 
@@ -235,9 +245,9 @@ def test_c0_workload_compliance():
     gm = gpu_mesh(om)
     gm.set_design(g)
     assert [L["ns"] + (L["nt"],) for L in gm.levels()] == [(32, 32, 32), (16, 16, 32), (16, 16, 16), (8, 8, 16)]
-    st = gm.solve_forward(rtol=1e-13, precision="fp64", max_it=400)
+    st = gm.solve_forward(rtol=parity_rtol(sol.A, sol.s, sol.f), precision="fp64", max_it=400)
     assert rel_err(gm.state("T"), sol.s) < 1e-10
-    phi, _ = gm.solve_adjoint("compliance", rtol=1e-13, precision="fp64", max_it=400)
+    phi, _ = gm.solve_adjoint("compliance", rtol=1e-12, precision="fp64", max_it=400)
     np.testing.assert_allclose(phi, O.compliance(sol.f, sol.s), rtol=1e-11)
 
 
