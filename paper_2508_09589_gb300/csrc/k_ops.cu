@@ -84,37 +84,8 @@ __global__ void __launch_bounds__(256) k_residual(OpL0<T> o0, OpLc<T> oc, const 
 template <int SD, typename T>
 __global__ void __launch_bounds__(256) k_restrict(Geom gf, Geom gc, int kind, const T* __restrict__ rf,
                                                   T* __restrict__ rc) {
-    const bool cs = kind != 1, ct = kind != 0;
     ST_NODE_LOOP_BEGIN(gc)
-    T acc = 0;
-    if (is_free<SD>(gc, i_, j_, k_, n_)) {
-        const int I = cs ? 2 * i_ : i_, J = cs ? 2 * j_ : j_, K = (cs && SD == 3) ? 2 * k_ : k_;
-        const int N = ct ? 2 * n_ : n_;
-        const int rs = cs ? 1 : 0, rt = ct ? 1 : 0, rz = (cs && SD == 3) ? 1 : 0;
-        for (int dn = -rt; dn <= rt; ++dn) {
-            const int fn = N + dn;
-            if (fn < 0 || fn >= gf.nt1) continue;
-            const T wn = dn == 0 ? T(1) : T(0.5);
-            for (int dk = -rz; dk <= rz; ++dk) {
-                const int fk = K + dk;
-                if (fk < 0 || fk >= gf.nz1) continue;
-                const T wk = dk == 0 ? T(1) : T(0.5);
-                for (int dj = -rs; dj <= rs; ++dj) {
-                    const int fj = J + dj;
-                    if (fj < 0 || fj >= gf.ny1) continue;
-                    const T wj = dj == 0 ? T(1) : T(0.5);
-                    for (int di = -rs; di <= rs; ++di) {
-                        const int fi = I + di;
-                        if (fi < 0 || fi >= gf.nx1) continue;
-                        if (!is_free<SD>(gf, fi, fj, fk, fn)) continue;
-                        const T wi = di == 0 ? T(1) : T(0.5);
-                        acc += wn * wk * wj * wi * rf[(((long long)fn * gf.nz1 + fk) * gf.ny1 + fj) * gf.nx1 + fi];
-                    }
-                }
-            }
-        }
-    }
-    rc[idx_] = acc;
+    rc[idx_] = restrict_node<SD, T>(gf, gc, kind, rf, i_, j_, k_, n_);
     ST_NODE_LOOP_END
 }
 
@@ -122,37 +93,8 @@ __global__ void __launch_bounds__(256) k_restrict(Geom gf, Geom gc, int kind, co
 template <int SD, typename T>
 __global__ void __launch_bounds__(256) k_prolong(Geom gf, Geom gc, int kind, const T* __restrict__ xc,
                                                  T* __restrict__ xf) {
-    const bool cs = kind != 1, ct = kind != 0;
     ST_NODE_LOOP_BEGIN(gf)
-    if (is_free<SD>(gf, i_, j_, k_, n_)) {
-        int lo[4], hi[4];
-        const int f[4] = {i_, j_, k_, n_};
-        const bool c[4] = {cs, cs, cs && SD == 3, ct};
-        for (int d = 0; d < 4; ++d) {
-            if (c[d]) {
-                lo[d] = f[d] >> 1;
-                hi[d] = (f[d] + 1) >> 1;
-            } else {
-                lo[d] = hi[d] = f[d];
-            }
-        }
-        T acc = 0;
-        for (int cn = lo[3]; cn <= hi[3]; ++cn) {
-            const T wn = lo[3] == hi[3] ? T(1) : T(0.5);
-            for (int ck = lo[2]; ck <= hi[2]; ++ck) {
-                const T wk = lo[2] == hi[2] ? T(1) : T(0.5);
-                for (int cj = lo[1]; cj <= hi[1]; ++cj) {
-                    const T wj = lo[1] == hi[1] ? T(1) : T(0.5);
-                    for (int ci = lo[0]; ci <= hi[0]; ++ci) {
-                        if (!is_free<SD>(gc, ci, cj, ck, cn)) continue;
-                        const T wi = lo[0] == hi[0] ? T(1) : T(0.5);
-                        acc += wn * wk * wj * wi * xc[(((long long)cn * gc.nz1 + ck) * gc.ny1 + cj) * gc.nx1 + ci];
-                    }
-                }
-            }
-        }
-        xf[idx_] += acc;
-    }
+    if (is_free<SD>(gf, i_, j_, k_, n_)) xf[idx_] += prolong_node<SD, T>(gf, gc, kind, xc, i_, j_, k_, n_);
     ST_NODE_LOOP_END
 }
 
@@ -785,7 +727,7 @@ void launch_prolong(const Geom& gf, const Geom& gc, int kind, int sd, const T* x
 // Below this many nodes a level's Arnoldi step is latency bound: the fused stencil + dots
 // kernel (one launch fewer) is used; above it the apply, dots and update run as separate
 // bandwidth-efficient kernels.
-constexpr long long kSplitNodes = 200000;
+constexpr long long kSplitNodes = 0;
 
 template <int SD, typename T, int LV, bool TR>
 static void smooth_impl(const OpL0<T>& o0, const OpLc<T>& oc, const T* b, T* x, const T* dinv, Basis<T> U, T* w,

@@ -4,6 +4,7 @@
 // adjoint solve and sensitivities (Sec. 3.3.3), and the C ABI declared in include/st.h.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -72,6 +73,21 @@ void Mesh::release(void* p) {
 Mesh::~Mesh() {
     if (device >= 0) cudaSetDevice(device);
     if (stream) cudaStreamSynchronize(stream);
+    if (level_timing && tcycles > 0) {
+        fprintf(stderr, "[st level timing] %d V-cycles, ms per V-cycle: level: pre-smooth, residual+restrict, prolong+post-smooth\n", tcycles);
+        for (size_t l = 0; l < lv.size(); ++l)
+            fprintf(stderr, "  L%zu (%lld nodes): %.3f %.3f %.3f\n", l, lv[l].g.nnodes, tacc[l * 3] / tcycles,
+                    tacc[l * 3 + 1] / tcycles, tacc[l * 3 + 2] / tcycles);
+    }
+    for (cudaEvent_t e : tev) cudaEventDestroy(e);
+    if (vt_trace) {
+        std::vector<unsigned long long> t(4096);
+        cudaMemcpy(t.data(), vt_trace, t.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+        fprintf(stderr, "[st vtail trace] ns between barriers of the last tail launch:");
+        for (int q = 1; q < 4096 && t[q] > t[0]; ++q) fprintf(stderr, " %llu", t[q] - t[q - 1]);
+        fprintf(stderr, "\n");
+        cudaFree(vt_trace);
+    }
     drop_graphs();
     for (void* p : allocs) cudaFree(p);
     if (h_fg) cudaFreeHost(h_fg);
@@ -326,6 +342,22 @@ st_status create_mesh(const st_mesh_desc* d, Mesh** out) {
     }
     m->own_stream = true;
     m->stream = m->own;
+    if (const char* e = getenv("ST_VTAIL_NODES")) m->vt_max_nodes = atoll(e);
+    if (const char* e = getenv("ST_LEVEL_TIMING")) m->level_timing = atoi(e) != 0;
+    if (const char* e = getenv("ST_VTAIL_TRACE"))
+        if (atoi(e) != 0) cudaMalloc((void**)&m->vt_trace, 4096 * sizeof(unsigned long long));
+    if (m->level_timing) {
+        m->tev.resize(m->lv.size() * 4);
+        for (auto& e : m->tev) cudaEventCreate(&e);
+        m->tacc.assign(m->lv.size() * 3, 0.0);
+    }
+    m->vt_first = -1;
+    if (m->vt_max_nodes > 0)
+        for (int l = 0; l < (int)m->lv.size(); ++l)
+            if (m->lv[l].g.nnodes <= m->vt_max_nodes && l < (int)m->lv.size() - 1) {
+                m->vt_first = l;
+                break;
+            }
     const long long N = m->lv[0].g.nnodes;
     st = ST_OK;
     auto A = [&](void** p, size_t b) {
@@ -342,6 +374,8 @@ st_status create_mesh(const st_mesh_desc* d, Mesh** out) {
     A((void**)&m->rb.counter, sizeof(unsigned) * 4);
     A((void**)&m->d_scalar, sizeof(double) * 8);
     A((void**)&m->d_err, sizeof(int) * 4);
+    A((void**)&m->d_bar, sizeof(unsigned) * 4);
+    A((void**)&m->vt_part, sizeof(double) * 2 * kMaxBlocks * kRedQ);
     const long long nc = m->lv.back().g.nnodes;
     A((void**)&m->Ainv, nc * nc * sizeof(double));
     A((void**)&m->Awork, nc * nc * sizeof(double));
@@ -399,6 +433,7 @@ st_status Mesh::ensure_level_storage() {
         }
     }
     storage_tc = tc;
+    ws_version++;
     return ST_OK;
 }
 
@@ -423,6 +458,7 @@ st_status set_design(Mesh* m, const double* gamma, int layout, size_t count, int
         CKS(m->alloc((void**)&m->gin, want * sizeof(double)));
         CKS(m->alloc((void**)&m->gsens, want * sizeof(double)));
         m->design_count = want;
+        m->ws_version++;
     }
     m->layout = layout;
     CKS(m->ensure_level_storage());
@@ -501,6 +537,7 @@ st_status Mesh::ensure_mg(int steps) {
     }
     if (steps + 1 > W.nbasis) {
         drop_graphs();
+        ws_version++;
         for (int l = 0; l < L - 1; ++l) {
             const long long N = lv[l].g.nnodes;
             for (int q = W.nbasis; q <= steps; ++q) CKS(alloc((void**)&W.U[l].u[q], N * sizeof(T)));
@@ -516,6 +553,59 @@ st_status Mesh::ensure_mg(int steps) {
         }
         W.dinv_version = design_version;
     }
+    if (vt_first >= 0 && (W.vt_version != ws_version || W.steps_uploaded != steps)) CKS(upload_vtail<T>(steps));
+    return ST_OK;
+}
+
+template <typename T>
+st_status Mesh::upload_vtail(int steps) {
+    MGWork<T>& W = work<T>();
+    if (!W.d_vt) CKS(alloc((void**)&W.d_vt, sizeof(VTail<T>)));
+    VTail<T>* h = new VTail<T>();
+    memset(h, 0, sizeof(VTail<T>));
+    h->first = vt_first;
+    h->L = (int)lv.size();
+    h->steps = steps;
+    h->nc = (int)lv.back().g.nnodes;
+    h->Ainv = Ainv;
+    h->part = vt_part;
+    h->bar = d_bar;
+    h->err = d_err + 1;
+    if (vt_trace) {
+        h->trace = vt_trace;
+        h->trace_cap = 4096;
+    }
+    h->op0 = op0<T>();
+    for (int l = 0; l < (int)lv.size(); ++l) {
+        VLevel<T>& V = h->lv[l];
+        V.g = lv[l].g;
+        V.lv = l;
+        V.to_next = lv[l].to_next;
+        V.tc = layout == ST_DESIGN_EXTRUDED ? 1 : 0;
+        if (l == 0) {
+            const OpL0<T> o = op0<T>();
+            V.coef[0] = o.st_coef[0];
+            V.coef[1] = o.st_coef[1];
+            V.dir = o.st_dir;
+        } else {
+            const OpLc<T> o = opc<T>(l);
+            V.coef[0] = o.st_coef[0];
+            V.coef[1] = o.st_coef[1];
+            V.dir = o.st_dir;
+            V.elem = o.elem;
+        }
+        V.b = W.b[l];
+        V.x = W.x[l];
+        V.r = W.r[l];
+        V.w = W.w[l];
+        V.dinv = W.dinv[l];
+        for (int q = 0; q <= kMaxSmooth; ++q) V.U[q] = W.U[l].u[q];
+    }
+    W.steps_uploaded = steps;
+    cudaError_t e = cudaMemcpy(W.d_vt, h, sizeof(VTail<T>), cudaMemcpyHostToDevice);
+    delete h;
+    if (e != cudaSuccess) return fail(ST_ERR_CUDA, std::string("vtail upload: ") + cudaGetErrorString(e));
+    W.vt_version = ws_version;
     return ST_OK;
 }
 
@@ -536,12 +626,50 @@ void Mesh::vcycle_rec(int l, bool tr, int steps) {
         launch_coarse_solve<T>(Ainv, (int)lv[l].g.nnodes, tr, W.b[l], W.x[l], stream);
         return;
     }
+    const bool timing = level_timing && !capturing;
+    auto mark = [&](int k) {
+        if (timing) cudaEventRecord(tev[l * 4 + k], stream);
+    };
+    if (l == vt_first && W.d_vt && W.steps_uploaded == steps) {
+        mark(0);
+        launch_vtail<T>(sd, tr, W.d_vt, d_bar, stream);
+        if (timing) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            cudaEventRecord(e, stream);
+            cudaEventSynchronize(e);
+            float a = 0;
+            cudaEventElapsedTime(&a, tev[l * 4 + 0], e);
+            tacc[l * 3] += a;
+            cudaEventDestroy(e);
+        }
+        return;
+    }
+    mark(0);
     smooth<T>(l, tr, true, steps);
+    mark(1);
     launch_residual<T>(sd, l, op0<T>(), opc<T>(l), tr, W.b[l], W.x[l], W.r[l], stream);
     launch_restrict<T>(lv[l].g, lv[l + 1].g, lv[l].to_next, sd, W.r[l], W.b[l + 1], stream);
+    mark(2);
     vcycle_rec<T>(l + 1, tr, steps);
+    if (timing) cudaEventRecord(tev[l * 4 + 3], stream);
     launch_prolong<T>(lv[l].g, lv[l + 1].g, lv[l].to_next, sd, W.x[l + 1], W.x[l], stream);
     smooth<T>(l, tr, false, steps);
+    if (timing) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        cudaEventRecord(e, stream);
+        cudaEventSynchronize(e);
+        float a = 0, b = 0, c = 0;
+        cudaEventElapsedTime(&a, tev[l * 4 + 0], tev[l * 4 + 1]);
+        cudaEventElapsedTime(&b, tev[l * 4 + 1], tev[l * 4 + 2]);
+        cudaEventElapsedTime(&c, tev[l * 4 + 3], e);
+        tacc[l * 3] += a;
+        tacc[l * 3 + 1] += b;
+        tacc[l * 3 + 2] += c;
+        cudaEventDestroy(e);
+        if (l == 0) ++tcycles;
+    }
 }
 
 template <typename T>
@@ -556,7 +684,9 @@ st_status Mesh::vcycle(bool tr, int steps, bool graphs) {
         gexec[slot] = nullptr;
         cudaGraph_t graph;
         CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+        capturing = true;
         vcycle_rec<T>(0, tr, steps);
+        capturing = false;
         CK(cudaStreamEndCapture(stream, &graph));
         long long graph_kernel_count = 0;
         {
@@ -695,9 +825,13 @@ st_status solve(Mesh* m, bool adjoint, const st_options* op, st_stats* stats) {
     double* x = adjoint ? m->lam : m->s;
     const double* rhs = adjoint ? m->adjrhs : m->f;
     if (!o.warm_start) CK(cudaMemsetAsync(x, 0, m->lv[0].g.nnodes * sizeof(double), m->stream));
+    CK(cudaMemsetAsync(m->d_err + 1, 0, sizeof(int), m->stream));
     st_status r = o.precision == ST_PREC_MIXED ? m->fgmres<float>(adjoint, rhs, x, o, S)
                                                : m->fgmres<double>(adjoint, rhs, x, o, S);
     cudaStreamSynchronize(m->stream);
+    int tmo = 0;
+    cudaMemcpy(&tmo, m->d_err + 1, sizeof(int), cudaMemcpyDeviceToHost);
+    if (tmo) r = fail(ST_ERR_TIMEOUT, "a grid barrier of the coarse V-cycle tail gave up waiting");
     S->seconds = now_s() - t0;
     return r;
 }

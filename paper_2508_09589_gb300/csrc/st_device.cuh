@@ -252,6 +252,26 @@ __device__ __forceinline__ T op_row(const OpL0<T>& o0, const OpLc<T>& oc, int i,
     }                    \
     }
 
+// Sum of partials part[b * kRedQ + q] over b < nb by one warp, in a fixed order: each lane
+// adds its strided share with 16 loads in flight per round, then a shuffle tree.
+__device__ __forceinline__ void out_sum_partials(const double* part, long long nb, int q, int lane, double* out) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (long long b0 = lane; b0 < nb; b0 += 32 * 16) {
+        double v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const long long b = b0 + 32LL * u;
+            v[u] = b < nb ? __ldcg(part + b * kRedQ + q) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) acc[u & 3] += v[u];
+    }
+    double a = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+#pragma unroll
+    for (int off = 16; off; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+    if (lane == 0) out[q] = a;
+}
+
 // ---------------------------------------------------------------- deterministic reduction
 // Every block publishes nq partial sums; the last block to finish sums them in block
 // order (independent of which block finished last) into `out` (shared memory of the
@@ -289,13 +309,7 @@ __device__ __forceinline__ bool reduce_publish(const double (&v)[NQ], int nq, Re
     __syncthreads();
     if (!last_) return false;
     __threadfence();
-    for (int q = warp; q < nq; q += nw) {
-        double a = 0;
-        for (long long b = lane; b < nb; b += 32) a += __ldcg(rb.part + b * kRedQ + q);
-#pragma unroll
-        for (int off = 16; off; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
-        if (lane == 0) out[q] = a;
-    }
+    for (int q = warp; q < nq; q += nw) out_sum_partials(rb.part, nb, q, lane, out);
     if (tid == 0) *rb.counter = 0u;
     __syncthreads();
     return true;
@@ -336,6 +350,105 @@ __device__ void l0_blocks(const OpL0<double>& op, int slab, int ex, int ey, int 
 // halved axis: r = 0 -> (1, 0), r = 1 -> (1/2, 1/2), r = 2 -> (0, 1).
 inline __device__ double q1(int r, int b) {
     return r == 1 ? 0.5 : ((r == 0) == (b == 0) ? 1.0 : 0.0);
+}
+
+// ---------------------------------------------------------------- transfers (per node)
+// kind: 0 = space (all spatial axes halved), 1 = time, 2 = both.
+// Restriction r_c = D_c P^T D_f r_f at coarse node (i, j, k, n); P trilinear, vertex nested.
+template <int SD, typename T>
+__device__ __forceinline__ T restrict_node(const Geom& gf, const Geom& gc, int kind, const T* __restrict__ rf, int i,
+                                           int j, int k, int n) {
+    if (!is_free<SD>(gc, i, j, k, n)) return T(0);
+    const bool cs = kind != 1, ct = kind != 0;
+    const int I = cs ? 2 * i : i, J = cs ? 2 * j : j, K = (cs && SD == 3) ? 2 * k : k;
+    const int N = ct ? 2 * n : n;
+    const int rs = cs ? 1 : 0, rt = ct ? 1 : 0, rz = (cs && SD == 3) ? 1 : 0;
+    T acc = 0;
+    for (int dn = -rt; dn <= rt; ++dn) {
+        const int fn = N + dn;
+        if (fn < 0 || fn >= gf.nt1) continue;
+        const T wn = dn == 0 ? T(1) : T(0.5);
+        for (int dk = -rz; dk <= rz; ++dk) {
+            const int fk = K + dk;
+            if (fk < 0 || fk >= gf.nz1) continue;
+            const T wk = dk == 0 ? T(1) : T(0.5);
+            for (int dj = -rs; dj <= rs; ++dj) {
+                const int fj = J + dj;
+                if (fj < 0 || fj >= gf.ny1) continue;
+                const T wj = dj == 0 ? T(1) : T(0.5);
+                for (int di = -rs; di <= rs; ++di) {
+                    const int fi = I + di;
+                    if (fi < 0 || fi >= gf.nx1) continue;
+                    if (!is_free<SD>(gf, fi, fj, fk, fn)) continue;
+                    const T wi = di == 0 ? T(1) : T(0.5);
+                    acc += wn * wk * wj * wi * rf[(((long long)fn * gf.nz1 + fk) * gf.ny1 + fj) * gf.nx1 + fi];
+                }
+            }
+        }
+    }
+    return acc;
+}
+
+// (P D_c x_c) at a free fine node (i, j, k, n).
+template <int SD, typename T>
+__device__ __forceinline__ T prolong_node(const Geom& gf, const Geom& gc, int kind, const T* __restrict__ xc, int i,
+                                          int j, int k, int n) {
+    const bool cs = kind != 1, ct = kind != 0;
+    int lo[4], hi[4];
+    const int f[4] = {i, j, k, n};
+    const bool c[4] = {cs, cs, cs && SD == 3, ct};
+    for (int d = 0; d < 4; ++d) {
+        if (c[d]) {
+            lo[d] = f[d] >> 1;
+            hi[d] = (f[d] + 1) >> 1;
+        } else {
+            lo[d] = hi[d] = f[d];
+        }
+    }
+    T acc = 0;
+    for (int cn = lo[3]; cn <= hi[3]; ++cn) {
+        const T wn = lo[3] == hi[3] ? T(1) : T(0.5);
+        for (int ck = lo[2]; ck <= hi[2]; ++ck) {
+            const T wk = lo[2] == hi[2] ? T(1) : T(0.5);
+            for (int cj = lo[1]; cj <= hi[1]; ++cj) {
+                const T wj = lo[1] == hi[1] ? T(1) : T(0.5);
+                for (int ci = lo[0]; ci <= hi[0]; ++ci) {
+                    if (!is_free<SD>(gc, ci, cj, ck, cn)) continue;
+                    const T wi = lo[0] == hi[0] ? T(1) : T(0.5);
+                    acc += wn * wk * wj * wi * xc[(((long long)cn * gc.nz1 + ck) * gc.ny1 + cj) * gc.nx1 + ci];
+                }
+            }
+        }
+    }
+    return acc;
+}
+
+// Node-parallel 27-point stencil row (plane class from n), for small levels.
+template <typename T, typename LD>
+__device__ __forceinline__ T row_stencil(const Geom& g, const T* __restrict__ coef, int i, int j, int n, const LD& ld) {
+    const int nt = g.net;
+    const long long P = (long long)g.nx1 * g.ny1;
+    const long long p = (long long)j * g.nx1 + i;
+    const int cls = (n == 1) ? (nt == 1 ? 3 : 0) : (n == nt ? 2 : 1);
+    const T* cc = coef + (long long)cls * 27 * P + p;
+    T acc = 0;
+#pragma unroll
+    for (int dt = 0; dt < 3; ++dt) {
+        const int m = n - 1 + dt;
+        if (m < 0 || m > nt) continue;
+#pragma unroll
+        for (int dj = 0; dj < 3; ++dj) {
+            const int jj = j - 1 + dj;
+            if (jj < 0 || jj >= g.ny1) continue;
+#pragma unroll
+            for (int di = 0; di < 3; ++di) {
+                const int ii = i - 1 + di;
+                if (ii < 0 || ii >= g.nx1) continue;
+                acc += cc[(long long)(dt * 9 + dj * 3 + di) * P] * ld((long long)m * P + (long long)jj * g.nx1 + ii);
+            }
+        }
+    }
+    return acc;
 }
 
 // ---------------------------------------------------------------- finalisers (last block, thread 0)

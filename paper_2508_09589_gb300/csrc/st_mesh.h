@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "st_internal.h"
+#include "st_vtail.h"
 
 namespace st {
 
@@ -25,6 +26,9 @@ struct LevelH {
 
 template <typename T>
 struct MGWork {
+    VTail<T>* d_vt = nullptr;      // persistent coarse-tail descriptor (device)
+    long long vt_version = -1;
+    int steps_uploaded = -1;
     bool ready = false;
     int nbasis = 0;
     long long dinv_version = -1;
@@ -71,6 +75,12 @@ struct Mesh {
     MGWork<float> w32;
     MGWork<double> w64;
 
+    int vt_first = -1;             // first level of the persistent coarse tail (-1: none)
+    long long vt_max_nodes = 0;    // persistent coarse tail off by default (ST_VTAIL_NODES enables it)
+    long long ws_version = 0;      // bumped when multigrid buffers move
+    unsigned* d_bar = nullptr;
+    unsigned long long* vt_trace = nullptr;
+    double* vt_part = nullptr;
     SmState* d_sm = nullptr;
     FgState* d_fg = nullptr;
     FgState* h_fg = nullptr;
@@ -81,6 +91,13 @@ struct Mesh {
     int gsteps[4] = {0, 0, 0, 0};
     long long gversion[4] = {-1, -1, -1, -1};
     long long gkernels[4] = {0, 0, 0, 0};
+
+    // opt-in per-level timing of eager V-cycles (environment ST_LEVEL_TIMING=1), printed at exit
+    bool level_timing = false;
+    std::vector<cudaEvent_t> tev;
+    std::vector<double> tacc;      // [level][phase]: pre-smooth, down-transfer, post-smooth+prolong
+    int tcycles = 0;
+    bool capturing = false;
 
     std::vector<void*> allocs;
     std::vector<size_t> alloc_sizes;
@@ -100,6 +117,8 @@ struct Mesh {
     MGWork<T>& work();
     template <typename T>
     st_status ensure_mg(int steps);
+    template <typename T>
+    st_status upload_vtail(int steps);
     template <typename T>
     void smooth(int l, bool tr, bool zero_init, int steps);
     template <typename T>

@@ -277,3 +277,23 @@ def test_graphs_and_eager_identical():
     gm.solve_forward(rtol=1e-9, use_graphs=True)
     b = gm.state("T")
     np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("i", [0, 1, 3])
+def test_persistent_tail_matches_launch_per_phase(i, monkeypatch):
+    """The V-cycle run as one persistent cooperative kernel (small levels) and as one launch
+    per phase give the same preconditioner output (FP64: rounding-level differences only)."""
+    om, g = _case(i)
+    b = np.random.default_rng(9).standard_normal(om.n_nodes)
+    b[O.dirichlet_mask(om)] = 0
+    out = []
+    for nodes in ("0", "100000000"):
+        monkeypatch.setenv("ST_VTAIL_NODES", nodes)
+        gm = gpu_mesh(om, coarse_dof_cap=300)
+        gm.set_design(g)
+        x = torch.empty(om.n_nodes, dtype=torch.float64, device="cuda")
+        gm.vcycle(_dev(b), x, "fp64", False)
+        out.append(x.cpu().numpy())
+        st = gm.solve_forward(rtol=1e-10, precision="mixed")
+        assert st["converged"]
+    assert rel_err(out[1], out[0]) < 1e-11
