@@ -246,6 +246,26 @@ long long st_kernel_launches(void);
 /* Device-memory estimate used by admission control for a mesh description. */
 long long st_footprint_bytes(const st_mesh_desc* d, int precision, int restart);
 
+/* ---- Allocation-free residual for callers that cannot allocate device memory ----
+ * The paper has no counterpart; this entry point exists for callers that must not call
+ * cudaMalloc (code running inside another framework's stream capture or memory pool, or
+ * a real-time loop).  It computes r = f - J x and ||r||_2 for the FP64 fine-level operator
+ * of mesh description d and design gamma (layout ST_DESIGN_*; values used as given, not
+ * clipped), matrix free, queued on
+ * `stream` (a cudaStream_t, NULL = legacy default stream).  All pointers are device
+ * pointers owned by the caller: gamma (design size), x, f, r (node count each) and norm
+ * (one double, written when the stream reaches the kernel).  No mesh is needed and nothing
+ * is allocated: the only scratch is a static 32 KiB device array that every GPU loading
+ * the library keeps until exit.  The first call on a device looks up that array's address
+ * (cudaGetSymbolAddress), so make it before any stream capture.  Limits: the x-y plane may
+ * hold at most 4096 tiles of 32 x 8 nodes (e.g. 1024 x 1024 spatial elements) and the
+ * mesh at most 2^31 - 1 nodes; larger sizes return ST_ERR_ARG.  All calls share the one
+ * array (it keeps the last call's partial sums; the completion counter is cleared at the
+ * start of each call), so calls that overlap on the GPU (different streams, or host
+ * threads on the same device) race and must be serialised by the caller. */
+st_status st_residual_norm_noalloc(const st_mesh_desc* d, const double* gamma, int layout, const double* x,
+                                   const double* f, double* r, double* norm, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,9 +18,16 @@
 namespace st {
 
 thread_local std::string g_last_error;
+thread_local const char* g_last_error_static = nullptr;
 
 st_status fail(st_status code, const std::string& msg) {
     g_last_error = msg;
+    g_last_error_static = nullptr;
+    return code;
+}
+
+st_status set_c_error(st_status code, const char* msg) {
+    g_last_error_static = msg;
     return code;
 }
 
@@ -886,7 +893,9 @@ extern "C" {
 
 const char* st_version(void) { return "st-gb300 0.1 (sm_103a)"; }
 
-const char* st_last_error(void) { return st::g_last_error.c_str(); }
+const char* st_last_error(void) {
+    return st::g_last_error_static ? st::g_last_error_static : st::g_last_error.c_str();
+}
 
 void st_mesh_desc_default(st_mesh_desc* d) {
     if (!d) return;
