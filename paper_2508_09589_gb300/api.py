@@ -282,3 +282,71 @@ def plan_hierarchy(ns, nt, **kw):
 def footprint_bytes(ns, nt, precision: str = "mixed", restart: int = 30, **kw) -> int:
     d = mesh_desc(ns, nt, **kw)
     return int(L.lib().st_footprint_bytes(C.byref(d), L.PREC[precision], int(restart)))
+
+
+class Server:
+    """Continuous-batching request server (st_server_create / st_submit / st_poll)."""
+
+    def __init__(self, hbm_budget: int, max_inflight: int = 4, device: int = 0):
+        d = L.ServerDesc(int(hbm_budget), int(max_inflight), int(device))
+        h = C.c_void_p()
+        L.check(L.lib().st_server_create(C.byref(d), C.byref(h)), "st_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, ns, nt, gamma, layout: Optional[str] = None, src: Optional[L.Source] = None,
+               opts: Optional[L.Options] = None, objective: str = "compliance", P: int = 20,
+               want_gradient: bool = True, **mesh_kw) -> int:
+        arr = np.ascontiguousarray(np.asarray(gamma, dtype=np.float64)).reshape(-1)
+        if layout is None:
+            layout = "extruded" if arr.size == int(np.prod(ns)) else "spacetime"
+        r = L.Request()
+        r.mesh = mesh_desc(ns, nt, **mesh_kw)
+        r.gamma = arr.ctypes.data_as(C.POINTER(C.c_double))
+        r.layout = L.LAYOUT[layout]
+        r.count = arr.size
+        r.source = src or source()
+        r.objective = L.Objective(L.OBJ[objective], int(P))
+        r.options = opts or options()
+        r.want_gradient = int(bool(want_gradient))
+        t = C.c_uint64()
+        L.check(L.lib().st_submit(self._h, C.byref(r), C.byref(t)), "st_submit")
+        self._keep[t.value] = arr.size
+        return t.value
+
+    def poll(self, ticket: int):
+        """(done, result dict or None, gradient or None)."""
+        res = L.Result()
+        done = C.c_int()
+        n = self._keep.get(ticket, 0)
+        grad = np.empty(n, dtype=np.float64)
+        L.check(L.lib().st_poll(self._h, C.c_uint64(ticket), C.byref(res), C.c_void_p(grad.ctypes.data), n,
+                                C.byref(done)), "st_poll")
+        if not done.value:
+            return False, None, None
+        self._keep.pop(ticket, None)
+        out = dict(status=res.status, phi=res.phi, forward=res.forward.as_dict(), adjoint=res.adjoint.as_dict(),
+                   latency_s=res.latency_s, queue_s=res.queue_s, footprint=res.footprint)
+        return True, out, grad
+
+    def wait(self, ticket: int, timeout: float = 600.0, poll_s: float = 0.001):
+        import time
+        t0 = time.time()
+        while True:
+            done, res, grad = self.poll(ticket)
+            if done:
+                return res, grad
+            if time.time() - t0 > timeout:
+                raise TimeoutError(f"request {ticket} not finished after {timeout} s")
+            time.sleep(poll_s)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            L.lib().st_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
