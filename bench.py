@@ -156,6 +156,7 @@ def run_native(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed")
         ev0.record(stream)
         t0 = time.perf_counter()
         its_f, its_a = [], []
@@ -166,6 +167,7 @@ def run_native(args):
         ev1.record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
+        torch.cuda.nvtx.range_pop()
     launches = L.st_kernel_launches() - k0
     # the library synchronises its own stream inside each solve, so host wall time brackets
     # all device work of the step; the torch events bracket the same region on the device

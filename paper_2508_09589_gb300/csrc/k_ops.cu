@@ -102,39 +102,6 @@ __global__ void __launch_bounds__(256) k_prolong(Geom gf, Geom gc, int kind, con
 // Right-preconditioned GMRES on A D^{-1} y = b - A x0, x = x0 + D^{-1} y, with the
 // basis kept unnormalised (u_j) and scales s_j = 1 / ||u_j|| (classical Gram-Schmidt,
 // one reduction per step); Givens rotations are applied as columns arrive.
-__device__ void sm_givens_column(SmState* st, int j) {
-    double* H = st->H;
-    double col[kMaxSmooth + 1];
-    for (int q = 0; q <= j + 1; ++q) col[q] = H[q * kMaxSmooth + j];
-    for (int q = 0; q < j; ++q) {
-        const double c = st->cs[q], s = st->sn[q];
-        const double a = col[q], b = col[q + 1];
-        col[q] = c * a + s * b;
-        col[q + 1] = -s * a + c * b;
-    }
-    const double a = col[j], b = col[j + 1];
-    const double r = hypot(a, b);
-    const double c = r > 0 ? a / r : 1.0, s = r > 0 ? b / r : 0.0;
-    st->cs[j] = c;
-    st->sn[j] = s;
-    col[j] = r;
-    col[j + 1] = 0;
-    st->g[j + 1] = -s * st->g[j];
-    st->g[j] = c * st->g[j];
-    for (int q = 0; q <= j + 1; ++q) st->R[q * kMaxSmooth + j] = col[q];
-}
-
-__device__ void sm_backsolve(SmState* st, int k) {
-    double y[kMaxSmooth];
-    for (int q = k - 1; q >= 0; --q) {
-        double a = st->g[q];
-        for (int l = q + 1; l < k; ++l) a -= st->R[q * kMaxSmooth + l] * y[l];
-        const double d = st->R[q * kMaxSmooth + q];
-        y[q] = d != 0 ? a / d : 0.0;
-    }
-    for (int q = 0; q < kMaxSmooth; ++q) st->coef[q] = q < k ? y[q] * st->s[q] : 0.0;
-}
-
 template <int SD, typename T, int LV, bool TR, bool ZERO>
 __global__ void __launch_bounds__(256) k_sm_start(OpL0<T> o0, OpLc<T> oc, const T* __restrict__ b,
                                                   const T* __restrict__ x, T* __restrict__ u0, int steps,
@@ -156,10 +123,11 @@ __global__ void __launch_bounds__(256) k_sm_start(OpL0<T> o0, OpLc<T> oc, const 
     }
     accT += r * r;
     ST_NODE_LOOP_END
-    acc[0] = (double)accT;
+    T accv[1] = {accT};
+    (void)acc;
     __shared__ double out[1];
-    if (reduce_publish<1>(acc, 1, rb, out)) {
-        if (threadIdx.x == 0 && threadIdx.y == 0) sm_start_finish(st, out[0], steps);
+    if (reduce_publish_t<T, 1>(accv, 1, rb, out)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) sm_start_finish<T>(st, out[0], steps);
     }
 }
 
@@ -167,7 +135,7 @@ template <int SD, typename T, int LV, bool TR>
 __global__ void __launch_bounds__(256) k_sm_apply(OpL0<T> o0, OpLc<T> oc, const T* __restrict__ dinv,
                                                   Basis<T> U, T* __restrict__ w, int j, SmState* st,
                                                   RedBuf rb) {
-    if (st->stop || j >= st->kdim) return;
+    if (smt<T>(st)->stop || j >= smt<T>(st)->kdim) return;
     const Geom& g = LV == 0 ? o0.g : oc.g;
     LoadScaled<T> ld{U.u[j], dinv};
     T accT[kMaxSmooth];
@@ -184,70 +152,10 @@ __global__ void __launch_bounds__(256) k_sm_apply(OpL0<T> o0, OpLc<T> oc, const 
     for (int q = 0; q < kMaxSmooth; ++q)
         if (q <= j) accT[q] += v * U.u[q][idx_];
     ST_NODE_LOOP_END
-    double acc[kMaxSmooth];
-#pragma unroll
-    for (int q = 0; q < kMaxSmooth; ++q) acc[q] = (double)accT[q];
     __shared__ double out[kMaxSmooth];
-    if (reduce_publish<kMaxSmooth>(acc, j + 1, rb, out)) {
-        if (threadIdx.x == 0 && threadIdx.y == 0) sm_apply_finish(st, out, j);
+    if (reduce_publish_t<T, kMaxSmooth>(accT, j + 1, rb, out)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) sm_apply_finish<T>(st, out, j);
     }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_sm_update(Geom g, Basis<T> U, const T* __restrict__ w, int j, int steps,
-                                                   SmState* st, RedBuf rb) {
-    if (st->stop || j >= st->kdim) return;
-    __shared__ T cf[kMaxSmooth];
-    __shared__ T sj;
-    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    if (tid <= j) cf[tid] = (T)(st->H[tid * kMaxSmooth + j] * st->s[tid]);
-    if (tid == 0) sj = (T)st->s[j];
-    __syncthreads();
-    T* un = U.u[j + 1];
-    double acc[1] = {0.0};
-    T accT = T(0);
-    ST_NODE_LOOP_BEGIN(g)
-    T v = sj * w[idx_];
-#pragma unroll
-    for (int q = 0; q < kMaxSmooth; ++q)
-        if (q <= j) v -= cf[q] * U.u[q][idx_];
-    un[idx_] = v;
-    accT += v * v;
-    ST_NODE_LOOP_END
-    acc[0] = (double)accT;
-    __shared__ double out[1];
-    if (reduce_publish<1>(acc, 1, rb, out)) {
-        if (tid == 0) {
-            const double h = sqrt(out[0]);
-            st->H[(j + 1) * kMaxSmooth + j] = h;
-            sm_givens_column(st, j);
-            const bool brk = !(h > 1e-13 * st->beta) || !isfinite(h);
-            if (brk) {
-                st->kdim = j + 1;
-            } else {
-                st->s[j + 1] = 1.0 / h;
-            }
-            if (brk || j + 1 == steps) sm_backsolve(st, j + 1);
-        }
-    }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_sm_finish(Geom g, T* __restrict__ x, const T* __restrict__ dinv,
-                                                   Basis<T> U, int zero_init, SmState* st) {
-    __shared__ T cf[kMaxSmooth];
-    __shared__ int kd;
-    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    if (tid == 0) kd = st->stop ? 0 : st->kdim;
-    if (tid < kMaxSmooth) cf[tid] = st->stop ? T(0) : (T)st->coef[tid];
-    __syncthreads();
-    const int k = kd;
-    ST_NODE_LOOP_BEGIN(g)
-    T v = 0;
-    for (int q = 0; q < k; ++q) v += cf[q] * U.u[q][idx_];
-    v *= dinv[idx_];
-    x[idx_] = zero_init ? v : x[idx_] + v;
-    ST_NODE_LOOP_END
 }
 
 // ---------------------------------------------------------------- coarsest solve
@@ -500,10 +408,10 @@ __global__ void __launch_bounds__(256) km_sm_start(Geom g, const T* __restrict__
         u0[q] = r;
         accT += r * r;
     });
-    double acc[1] = {(double)accT};
+    T acc[1] = {accT};
     __shared__ double out[1];
-    if (reduce_publish<1>(acc, 1, rb, out)) {
-        if (threadIdx.x == 0 && threadIdx.y == 0) sm_start_finish(st, out[0], steps);
+    if (reduce_publish_t<T, 1>(acc, 1, rb, out)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) sm_start_finish<T>(st, out[0], steps);
     }
 }
 
@@ -512,7 +420,7 @@ __global__ void __launch_bounds__(256) km_sm_apply(Geom g, const T* __restrict__
                                                    const unsigned char* __restrict__ dir, int chunk,
                                                    const T* __restrict__ dinv, Basis<T> U, T* __restrict__ w, int j,
                                                    SmState* st, RedBuf rb) {
-    if (st->stop || j >= st->kdim) return;
+    if (smt<T>(st)->stop || j >= smt<T>(st)->kdim) return;
     LoadScaled<T> ld{U.u[j], dinv};
     T accT[kMaxSmooth];
 #pragma unroll
@@ -523,12 +431,9 @@ __global__ void __launch_bounds__(256) km_sm_apply(Geom g, const T* __restrict__
         for (int s = 0; s < kMaxSmooth; ++s)
             if (s <= j) accT[s] += v * U.u[s][q];
     });
-    double acc[kMaxSmooth];
-#pragma unroll
-    for (int q = 0; q < kMaxSmooth; ++q) acc[q] = (double)accT[q];
     __shared__ double out[kMaxSmooth];
-    if (reduce_publish<kMaxSmooth>(acc, j + 1, rb, out)) {
-        if (threadIdx.x == 0 && threadIdx.y == 0) sm_apply_finish(st, out, j);
+    if (reduce_publish_t<T, kMaxSmooth>(accT, j + 1, rb, out)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) sm_apply_finish<T>(st, out, j);
     }
 }
 
@@ -579,7 +484,7 @@ __global__ void __launch_bounds__(256) km_sm_applyw(Geom g, const T* __restrict_
                                                     const unsigned char* __restrict__ dir, int chunk,
                                                     const T* __restrict__ dinv, const T* __restrict__ uj,
                                                     T* __restrict__ w, int j, const SmState* st) {
-    if (st->stop || j >= st->kdim) return;
+    if (smt<T>(st)->stop || j >= smt<T>(st)->kdim) return;
     LoadScaled<T> ld{uj, dinv};
     march2d<T>(g, coef, dir, ld, chunk, [&](long long q, T v) { w[q] = v; });
 }
@@ -588,7 +493,7 @@ template <int SD, typename T, int LV, bool TR>
 __global__ void __launch_bounds__(256) k_sm_applyw(OpL0<T> o0, OpLc<T> oc, const T* __restrict__ dinv,
                                                    const T* __restrict__ uj, T* __restrict__ w, int j,
                                                    const SmState* st) {
-    if (st->stop || j >= st->kdim) return;
+    if (smt<T>(st)->stop || j >= smt<T>(st)->kdim) return;
     const Geom& g = LV == 0 ? o0.g : oc.g;
     LoadScaled<T> ld{uj, dinv};
     ST_NODE_LOOP_BEGIN(g)
@@ -731,7 +636,7 @@ constexpr long long kSplitNodes = 0;
 
 template <int SD, typename T, int LV, bool TR>
 static void smooth_impl(const OpL0<T>& o0, const OpLc<T>& oc, const T* b, T* x, const T* dinv, Basis<T> U, T* w,
-                        int steps, bool zero_init, SmState* st, RedBuf rb, cudaStream_t s) {
+                        T* w2, int steps, bool zero_init, SmState* st, RedBuf rb, cudaStream_t s) {
     const Geom& g = LV == 0 ? o0.g : oc.g;
     const long long N = g.nnodes;
     const LaunchCfg c = node_cfg(g);
@@ -744,6 +649,11 @@ static void smooth_impl(const OpL0<T>& o0, const OpLc<T>& oc, const T* b, T* x, 
     Ptrs<T> P{};
     for (int q = 0; q <= steps; ++q) P.p[q] = U.u[q];
     const bool split = N >= kSplitNodes;
+    // The fused Arnoldi step (one pass per step, halo recomputed) only pays on tiny, latency
+    // bound levels; on large levels the split apply / dots / update kernels stream faster.
+    constexpr long long kFusedMaxNodes = 15000;
+    const bool fused = march && std::is_same<T, float>::value && w2 != nullptr && steps >= 2 && steps + 1 <= 16 &&
+                       N <= kFusedMaxNodes;
     if (zero_init) {
         launch_sm_norm<T>(N, b, steps, st, rb, s);
     } else {
@@ -752,6 +662,26 @@ static void smooth_impl(const OpL0<T>& o0, const OpLc<T>& oc, const T* b, T* x, 
             km_sm_start<T><<<mgrid, mblock, 0, s>>>(g, coef, dir, mg.chunk, b, x, U.u[0], steps, st, rb);
         else
             k_sm_start<SD, T, LV, TR, false><<<c.grid, c.block, 0, s>>>(o0, oc, b, x, U.u[0], steps, st, rb);
+    }
+    if (fused) {
+        if constexpr (std::is_same<T, float>::value) {
+            // step 0: w = A D^{-1} u_0 and (w, u_0); then fused steps j -> j+1; the last
+            // update only closes the Hessenberg matrix (norm of u_m) before the combination.
+            note_launch(s);
+            km_sm_applyw<T><<<mgrid, mblock, 0, s>>>(g, coef, dir, mg.chunk, dinv, U.u[0], w, 0, st);
+            launch_dots<T>(N, w, P, 1, 0, 0, st, rb, s);
+            T* wc = w;
+            T* wn = w2;
+            for (int j = 0; j + 1 < steps; ++j) {
+                launch_arnoldi(g, coef, dir, dinv, P, wc, wn, j, st, rb, s);
+                T* t = wc;
+                wc = wn;
+                wn = t;
+            }
+            launch_update<T>(N, wc, U.u[steps], P, steps - 1, steps, 0, st, rb, s);
+            launch_sm_combine<T>(N, x, dinv, P, steps, zero_init, st, s);
+            return;
+        }
     }
     for (int j = 0; j < steps; ++j) {
         note_launch(s);
@@ -773,13 +703,13 @@ static void smooth_impl(const OpL0<T>& o0, const OpLc<T>& oc, const T* b, T* x, 
 
 template <typename T>
 void launch_smooth(int sd, int lvl, const OpL0<T>& o0, const OpLc<T>& oc, bool tr, const T* b, T* x, const T* dinv,
-                   Basis<T> U, T* w, int steps, bool zero_init, SmState* st, RedBuf rb, cudaStream_t s) {
+                   Basis<T> U, T* w, T* w2, int steps, bool zero_init, SmState* st, RedBuf rb, cudaStream_t s) {
     if (lvl == 0) {
-        ST_SD_DISPATCH(sd, if (tr) smooth_impl<SD, T, 0, true>(o0, oc, b, x, dinv, U, w, steps, zero_init, st, rb, s);
-                       else smooth_impl<SD, T, 0, false>(o0, oc, b, x, dinv, U, w, steps, zero_init, st, rb, s));
+        ST_SD_DISPATCH(sd, if (tr) smooth_impl<SD, T, 0, true>(o0, oc, b, x, dinv, U, w, w2, steps, zero_init, st, rb, s);
+                       else smooth_impl<SD, T, 0, false>(o0, oc, b, x, dinv, U, w, w2, steps, zero_init, st, rb, s));
     } else {
-        ST_SD_DISPATCH(sd, if (tr) smooth_impl<SD, T, 1, true>(o0, oc, b, x, dinv, U, w, steps, zero_init, st, rb, s);
-                       else smooth_impl<SD, T, 1, false>(o0, oc, b, x, dinv, U, w, steps, zero_init, st, rb, s));
+        ST_SD_DISPATCH(sd, if (tr) smooth_impl<SD, T, 1, true>(o0, oc, b, x, dinv, U, w, w2, steps, zero_init, st, rb, s);
+                       else smooth_impl<SD, T, 1, false>(o0, oc, b, x, dinv, U, w, w2, steps, zero_init, st, rb, s));
     }
 }
 
@@ -878,7 +808,7 @@ void launch_mask_copy(int sd, const Geom& g, const double* src, double* dst, cud
     template void launch_restrict<T>(const Geom&, const Geom&, int, int, const T*, T*, cudaStream_t);               \
     template void launch_prolong<T>(const Geom&, const Geom&, int, int, const T*, T*, cudaStream_t);                \
     template void launch_smooth<T>(int, int, const OpL0<T>&, const OpLc<T>&, bool, const T*, T*, const T*, Basis<T>, \
-                                   T*, int, bool, SmState*, RedBuf, cudaStream_t);                                  \
+                                   T*, T*, int, bool, SmState*, RedBuf, cudaStream_t);                              \
     template void launch_coarse_solve<T>(const double*, int, bool, const T*, T*, cudaStream_t);                     \
     template void launch_fg_apply_dots<T>(int, const OpL0<double>&, bool, const T*, T*, double*, double* const*,    \
                                           int, FgState*, RedBuf, cudaStream_t);                                      \

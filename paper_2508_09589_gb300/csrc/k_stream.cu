@@ -13,7 +13,7 @@ template <typename T, int NQ, int FIN>
 __global__ void __launch_bounds__(256) k_dots(long long n, const T* __restrict__ w, Ptrs<T> U, int nq, int j,
                                               void* state, RedBuf rb) {
     if (FIN == 0) {
-        const SmState* st = (const SmState*)state;
+        const SmStateT<T>* st = smt<T>((const SmState*)state);
         if (st->stop || j >= st->kdim) return;
     }
     constexpr int W = Vec16<T>::W;
@@ -39,14 +39,11 @@ __global__ void __launch_bounds__(256) k_dots(long long n, const T* __restrict__
                     if (q < nq) acc[q] += w[e] * U.p[q][e];
         }
     });
-    double d[NQ];
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) d[q] = (double)acc[q];
     __shared__ double out[NQ];
-    if (reduce_publish<NQ>(d, nq, rb, out)) {
+    if (reduce_publish_t<T, NQ>(acc, nq, rb, out)) {
         if (threadIdx.x == 0) {
             if (FIN == 0)
-                sm_apply_finish((SmState*)state, out, j);
+                sm_apply_finish<T>((SmState*)state, out, j);
             else
                 fg_apply_finish((FgState*)state, out, j);
         }
@@ -66,10 +63,10 @@ __global__ void __launch_bounds__(256) k_update(long long n, T* __restrict__ w, 
     __shared__ T a_s;
     const int nq = j + 1;
     if (MODE == 0) {
-        SmState* st = (SmState*)state;
+        const SmStateT<T>* st = smt<T>((const SmState*)state);
         if (st->stop || j >= st->kdim) return;
-        if (threadIdx.x < nq) cf[threadIdx.x] = (T)(st->H[threadIdx.x * kMaxSmooth + j] * st->s[threadIdx.x]);
-        if (threadIdx.x == 0) a_s = (T)st->s[j];
+        if (threadIdx.x < nq) cf[threadIdx.x] = st->H[threadIdx.x * kMaxSmooth + j] * st->s[threadIdx.x];
+        if (threadIdx.x == 0) a_s = st->s[j];
     } else {
         FgState* fs = (FgState*)state;
         if (threadIdx.x < nq) {
@@ -125,14 +122,11 @@ __global__ void __launch_bounds__(256) k_update(long long n, T* __restrict__ w, 
             }
         }
     });
-    double d[NA];
-#pragma unroll
-    for (int q = 0; q < NA; ++q) d[q] = (double)acc[q];
     __shared__ double out[NA];
-    if (reduce_publish<NA>(d, MODE == 1 ? nq : 1, rb, out)) {
+    if (reduce_publish_t<T, NA>(acc, MODE == 1 ? nq : 1, rb, out)) {
         if (threadIdx.x == 0) {
             if (MODE == 0)
-                sm_update_finish((SmState*)state, out[0], j, steps);
+                sm_update_finish<T>((SmState*)state, out[0], j, steps);
             else if (MODE == 1)
                 fg_pass0_finish((FgState*)state, cfd, out, j);
             else
@@ -144,12 +138,13 @@ __global__ void __launch_bounds__(256) k_update(long long n, T* __restrict__ w, 
 // ---------------------------------------------------------------- smoother finish: x = [x +] d (.) sum_q c_q u_q
 template <typename T, int NQ>
 __global__ void __launch_bounds__(256) k_sm_combine(long long n, T* __restrict__ x, const T* __restrict__ dinv,
-                                                    Ptrs<T> U, int zero_init, const SmState* st) {
+                                                    Ptrs<T> U, int zero_init, const SmState* st_) {
     constexpr int W = Vec16<T>::W;
+    const SmStateT<T>* st = smt<T>(st_);
     __shared__ T cf[NQ];
     __shared__ int kd_s;
     if (threadIdx.x == 0) kd_s = st->stop ? 0 : st->kdim;
-    if (threadIdx.x < NQ) cf[threadIdx.x] = st->stop ? T(0) : (T)st->coef[threadIdx.x];
+    if (threadIdx.x < NQ) cf[threadIdx.x] = st->stop ? T(0) : st->coef[threadIdx.x];
     __syncthreads();
     const int kd = kd_s;
     stream_loop<T>(n, [&](long long v, bool full) {
@@ -196,10 +191,10 @@ __global__ void __launch_bounds__(256) k_sm_norm(long long n, const T* __restric
             for (long long e = v * W; e < n; ++e) acc += b[e] * b[e];
         }
     });
-    double d[1] = {(double)acc};
+    T d[1] = {acc};
     __shared__ double out[1];
-    if (reduce_publish<1>(d, 1, rb, out)) {
-        if (threadIdx.x == 0) sm_start_finish(st, out[0], steps);
+    if (reduce_publish_t<T, 1>(d, 1, rb, out)) {
+        if (threadIdx.x == 0) sm_start_finish<T>(st, out[0], steps);
     }
 }
 

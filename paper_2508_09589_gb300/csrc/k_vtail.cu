@@ -52,29 +52,30 @@ __device__ __forceinline__ void gbar(GBar& b) {
 }
 
 // Grid sum of nq per-thread values into out[] (shared, identical in every block).
-template <int NQ>
-__device__ void gsum(const double (&v)[NQ], int nq, double* part, int& parity, GBar& bar, double* out) {
-    __shared__ double sm[NQ][32];
+template <typename TA, int NQ>
+__device__ void gsum(const TA (&v)[NQ], int nq, double* part_d, int& parity, GBar& bar, double* out) {
+    __shared__ TA sm[NQ][32];
+    TA* part = reinterpret_cast<TA*>(part_d);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
         if (q < nq) {
-            double a = v[q];
+            TA a = v[q];
 #pragma unroll
             for (int off = 16; off; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
             if (lane == 0) sm[q][warp] = a;
         }
     }
     __syncthreads();
-    double* pb = part + (size_t)parity * kMaxBlocks * kRedQ;
+    TA* pb = part + (size_t)parity * kMaxBlocks * kRedQ;
     if (tid < nq) {
-        double a = 0;
+        TA a = 0;
         for (int w = 0; w < nw; ++w) a += sm[tid][w];
         pb[(size_t)blockIdx.x * kRedQ + tid] = a;
     }
     gbar(bar);
     const int nb = gridDim.x;
-    for (int q = warp; q < nq; q += nw) out_sum_partials(pb, nb, q, lane, out);
+    for (int q = warp; q < nq; q += nw) out_sum_partials_t<TA>(pb, nb, q, lane, out);
     parity ^= 1;
     __syncthreads();
 }
@@ -110,19 +111,20 @@ __device__ __forceinline__ T prow(const VTail<T>& pv, const VLevel<T>& L, int i,
     return row_lc<SD, T, TR>(oc, i, j, k, n, ld);
 }
 
+template <typename T>
 struct SmLocal {
-    double H[(kMaxSmooth + 1) * kMaxSmooth];
-    double s[kMaxSmooth + 1];
-    double cs[kMaxSmooth], sn[kMaxSmooth], g[kMaxSmooth + 1];
-    double coef[kMaxSmooth];
-    double beta;
+    T H[(kMaxSmooth + 1) * kMaxSmooth];
+    T s[kMaxSmooth + 1];
+    T cs[kMaxSmooth], sn[kMaxSmooth], g[kMaxSmooth + 1];
+    T coef[kMaxSmooth];
+    T beta;
     int kdim, stop;
 };
 
 // Jacobi-GMRES smoothing on level L (zero_init: x = 0 start, u_0 = b).
 template <int SD, typename T, bool TR>
 __device__ void psmooth(const VTail<T>& pv, const VLevel<T>& L, bool zero_init, int steps, double* part, int& parity,
-                        GBar& bar, SmLocal& S) {
+                        GBar& bar, SmLocal<T>& S) {
     const Geom& g = L.g;
     const long long N = g.nnodes;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -144,16 +146,16 @@ __device__ void psmooth(const VTail<T>& pv, const VLevel<T>& L, bool zero_init, 
             }
             acc += r * r;
         }
-        double v[1] = {(double)acc};
-        gsum<1>(v, 1, part, parity, bar, red);
+        T v[1] = {acc};
+        gsum<T, 1>(v, 1, part, parity, bar, red);
         if (threadIdx.x == 0) {
-            const double beta = sqrt(red[0]);
+            const T beta = (T)sqrt(red[0]);
             S.beta = beta;
-            S.stop = !(beta > 0.0 && isfinite(beta));
-            S.s[0] = S.stop ? 0.0 : 1.0 / beta;
+            S.stop = !(beta > T(0) && isfinite(beta));
+            S.s[0] = S.stop ? T(0) : T(1) / beta;
             S.kdim = steps;
             S.g[0] = beta;
-            for (int q = 0; q < kMaxSmooth; ++q) S.coef[q] = 0.0;
+            for (int q = 0; q < kMaxSmooth; ++q) S.coef[q] = T(0);
         }
         __syncthreads();
     }
@@ -179,20 +181,17 @@ __device__ void psmooth(const VTail<T>& pv, const VLevel<T>& L, bool zero_init, 
                 for (int s = 0; s < kMaxSmooth; ++s)
                     if (s <= j) acc[s] += w * uu[s];
             }
-            double v[kMaxSmooth];
-#pragma unroll
-            for (int s = 0; s < kMaxSmooth; ++s) v[s] = (double)acc[s];
-            gsum<kMaxSmooth>(v, j + 1, part, parity, bar, red);
+            gsum<T, kMaxSmooth>(acc, j + 1, part, parity, bar, red);
             if (threadIdx.x == 0)
-                for (int s = 0; s <= j; ++s) S.H[s * kMaxSmooth + j] = S.s[s] * S.s[j] * red[s];
+                for (int s = 0; s <= j; ++s) S.H[s * kMaxSmooth + j] = S.s[s] * S.s[j] * (T)red[s];
             __syncthreads();
         }
         // u_{j+1} = s_j w - sum_q H[q][j] s_q u_q and its norm
         {
             __shared__ T cf[kMaxSmooth];
             __shared__ T sj;
-            if (threadIdx.x <= j) cf[threadIdx.x] = (T)(S.H[threadIdx.x * kMaxSmooth + j] * S.s[threadIdx.x]);
-            if (threadIdx.x == 0) sj = (T)S.s[j];
+            if (threadIdx.x <= j) cf[threadIdx.x] = S.H[threadIdx.x * kMaxSmooth + j] * S.s[threadIdx.x];
+            if (threadIdx.x == 0) sj = S.s[j];
             __syncthreads();
             T acc = 0;
             T* un = L.U[j + 1];
@@ -207,34 +206,46 @@ __device__ void psmooth(const VTail<T>& pv, const VLevel<T>& L, bool zero_init, 
                 un[q] = v;
                 acc += v * v;
             }
-            double v[1] = {(double)acc};
-            gsum<1>(v, 1, part, parity, bar, red);
+            T v[1] = {acc};
+            gsum<T, 1>(v, 1, part, parity, bar, red);
             if (threadIdx.x == 0) {
-                const double h = sqrt(red[0]);
+                const T h = (T)sqrt(red[0]);
                 S.H[(j + 1) * kMaxSmooth + j] = h;
-                // Givens rotation of column j
-                double col[kMaxSmooth + 1];
-                for (int q = 0; q <= j + 1; ++q) col[q] = S.H[q * kMaxSmooth + j];
-                for (int q = 0; q < j; ++q) {
-                    const double c = S.cs[q], s = S.sn[q];
-                    const double a = col[q], b = col[q + 1];
-                    col[q] = c * a + s * b;
-                    col[q + 1] = -s * a + c * b;
-                }
-                const double a = col[j], b = col[j + 1];
-                const double r = hypot(a, b);
-                const double c = r > 0 ? a / r : 1.0, s = r > 0 ? b / r : 0.0;
+                // Givens rotation of column j (register array, unrolled)
+                T col[kMaxSmooth + 1];
+#pragma unroll
+                for (int q = 0; q <= kMaxSmooth; ++q) col[q] = q <= j + 1 ? S.H[q * kMaxSmooth + j] : T(0);
+#pragma unroll
+                for (int q = 0; q < kMaxSmooth; ++q)
+                    if (q < j) {
+                        const T c = S.cs[q], s = S.sn[q];
+                        const T a = col[q], b = col[q + 1];
+                        col[q] = c * a + s * b;
+                        col[q + 1] = -s * a + c * b;
+                    }
+                T a = T(0), b = T(0);
+#pragma unroll
+                for (int q = 0; q < kMaxSmooth; ++q)
+                    if (q == j) {
+                        a = col[q];
+                        b = col[q + 1];
+                    }
+                const T r = sqrt(a * a + b * b);
+                const T c = r > T(0) ? a / r : T(1), s = r > T(0) ? b / r : T(0);
                 S.cs[j] = c;
                 S.sn[j] = s;
-                col[j] = r;
-                S.g[j + 1] = -s * S.g[j];
-                S.g[j] = c * S.g[j];
-                for (int q = 0; q <= j; ++q) S.H[q * kMaxSmooth + j] = col[q];  // R column (upper part)
-                const bool brk = !(h > 1e-13 * S.beta) || !isfinite(h);
+                const T gj = S.g[j];
+                S.g[j + 1] = -s * gj;
+                S.g[j] = c * gj;
+#pragma unroll
+                for (int q = 0; q < kMaxSmooth; ++q)
+                    if (q <= j) S.H[q * kMaxSmooth + j] = q == j ? r : col[q];  // R column (upper part)
+                const T tol = sizeof(T) == 4 ? T(1e-6) : T(1e-13);
+                const bool brk = !(h > tol * S.beta) || !isfinite(h);
                 if (brk)
                     S.kdim = j + 1;
                 else
-                    S.s[j + 1] = 1.0 / h;
+                    S.s[j + 1] = T(1) / h;
             }
             __syncthreads();
         }
@@ -242,20 +253,27 @@ __device__ void psmooth(const VTail<T>& pv, const VLevel<T>& L, bool zero_init, 
     // back substitution (R is stored in the upper part of H) and x update
     if (threadIdx.x == 0) {
         const int k = S.stop ? 0 : S.kdim;
-        double y[kMaxSmooth];
-        for (int q = k - 1; q >= 0; --q) {
-            double a = S.g[q];
-            for (int l = q + 1; l < k; ++l) a -= S.H[q * kMaxSmooth + l] * y[l];
-            const double d = S.H[q * kMaxSmooth + q];
-            y[q] = d != 0 ? a / d : 0.0;
+        T y[kMaxSmooth];
+#pragma unroll
+        for (int q = kMaxSmooth - 1; q >= 0; --q) {
+            y[q] = T(0);
+            if (q < k) {
+                T a = S.g[q];
+#pragma unroll
+                for (int l = 0; l < kMaxSmooth; ++l)
+                    if (l > q && l < k) a -= S.H[q * kMaxSmooth + l] * y[l];
+                const T d = S.H[q * kMaxSmooth + q];
+                y[q] = d != T(0) ? a / d : T(0);
+            }
         }
-        for (int q = 0; q < kMaxSmooth; ++q) S.coef[q] = q < k ? y[q] * S.s[q] : 0.0;
+#pragma unroll
+        for (int q = 0; q < kMaxSmooth; ++q) S.coef[q] = q < k ? y[q] * S.s[q] : T(0);
         S.kdim = k;
     }
     __syncthreads();
     {
         __shared__ T cf[kMaxSmooth];
-        if (threadIdx.x < kMaxSmooth) cf[threadIdx.x] = (T)S.coef[threadIdx.x];
+        if (threadIdx.x < kMaxSmooth) cf[threadIdx.x] = S.coef[threadIdx.x];
         __syncthreads();
         const int k = S.kdim;
         for (long long q = t0; q < N; q += stride) {
@@ -301,7 +319,7 @@ __global__ void __launch_bounds__(256) k_vtail(const VTail<T>* __restrict__ pvp)
         pv.trace[0] = t;
     }
     int parity = 0;
-    __shared__ SmLocal S;
+    __shared__ SmLocal<T> S;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int Lc = pv.L - 1;

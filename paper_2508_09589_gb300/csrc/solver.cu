@@ -526,6 +526,7 @@ st_status Mesh::ensure_mg(int steps) {
         W.x.assign(L, nullptr);
         W.r.assign(L, nullptr);
         W.w.assign(L, nullptr);
+        W.w2.assign(L, nullptr);
         W.dinv.assign(L, nullptr);
         W.U.assign(L, Basis<T>{});
         for (int l = 0; l < L; ++l) {
@@ -536,6 +537,7 @@ st_status Mesh::ensure_mg(int steps) {
             CKS(alloc((void**)&W.dinv[l], N * sizeof(T)));
             if (l < L - 1) {
                 CKS(alloc((void**)&W.w[l], N * sizeof(T)));
+                CKS(alloc((void**)&W.w2[l], N * sizeof(T)));
             }
         }
         W.nbasis = 0;
@@ -619,8 +621,8 @@ st_status Mesh::upload_vtail(int steps) {
 template <typename T>
 void Mesh::smooth(int l, bool tr, bool zero_init, int steps) {
     MGWork<T>& W = work<T>();
-    launch_smooth<T>(sd, l, op0<T>(), opc<T>(l), tr, W.b[l], W.x[l], W.dinv[l], W.U[l], W.w[l], steps, zero_init, d_sm,
-                     rb, stream);
+    launch_smooth<T>(sd, l, op0<T>(), opc<T>(l), tr, W.b[l], W.x[l], W.dinv[l], W.U[l], W.w[l], W.w2[l], steps,
+                     zero_init, d_sm, rb, stream);
 }
 
 // One V-cycle on level l: pre-smoothing from zero, residual, restriction, coarse
@@ -867,8 +869,10 @@ static st_status smooth_entry(Mesh* mm, int level, int transpose, const void* b,
     const long long N = mm->lv[level].g.nnodes;
     CK(cudaMemcpyAsync(W.b[level], b, N * sizeof(T), cudaMemcpyDeviceToDevice, mm->stream));
     CK(cudaMemcpyAsync(W.x[level], x, N * sizeof(T), cudaMemcpyDeviceToDevice, mm->stream));
-    if (level == (int)mm->lv.size() - 1 && W.w[level] == nullptr)
+    if (level == (int)mm->lv.size() - 1 && W.w[level] == nullptr) {
         CKS(mm->alloc((void**)&W.w[level], N * sizeof(T)));
+        CKS(mm->alloc((void**)&W.w2[level], N * sizeof(T)));
+    }
     if (W.U[level].u[0] == nullptr)
         for (int q = 0; q < W.nbasis; ++q) CKS(mm->alloc((void**)&W.U[level].u[q], N * sizeof(T)));
     mm->smooth<T>(level, transpose != 0, zero_init != 0, steps);

@@ -253,40 +253,48 @@ __device__ __forceinline__ T op_row(const OpL0<T>& o0, const OpLc<T>& oc, int i,
     }
 
 // Sum of partials part[b * kRedQ + q] over b < nb by one warp, in a fixed order: each lane
-// adds its strided share with 16 loads in flight per round, then a shuffle tree.
-__device__ __forceinline__ void out_sum_partials(const double* part, long long nb, int q, int lane, double* out) {
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+// adds its strided share with 16 loads in flight per round, then a shuffle tree.  TA is
+// the accumulation type: float in the FP32 multigrid (FP64 arithmetic is a slow path on
+// this GPU, a few FMAs per clock per SM), double in the FP64 Krylov solver.
+template <typename TA>
+__device__ __forceinline__ void out_sum_partials_t(const TA* part, long long nb, int q, int lane, double* out) {
+    TA acc[4] = {TA(0), TA(0), TA(0), TA(0)};
     for (long long b0 = lane; b0 < nb; b0 += 32 * 16) {
-        double v[16];
+        TA v[16];
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
             const long long b = b0 + 32LL * u;
-            v[u] = b < nb ? __ldcg(part + b * kRedQ + q) : 0.0;
+            v[u] = b < nb ? __ldcg(part + b * kRedQ + q) : TA(0);
         }
 #pragma unroll
         for (int u = 0; u < 16; ++u) acc[u & 3] += v[u];
     }
-    double a = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+    TA a = (acc[0] + acc[1]) + (acc[2] + acc[3]);
 #pragma unroll
     for (int off = 16; off; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
-    if (lane == 0) out[q] = a;
+    if (lane == 0) out[q] = (double)a;
+}
+
+__device__ __forceinline__ void out_sum_partials(const double* part, long long nb, int q, int lane, double* out) {
+    out_sum_partials_t<double>(part, nb, q, lane, out);
 }
 
 // ---------------------------------------------------------------- deterministic reduction
 // Every block publishes nq partial sums; the last block to finish sums them in block
 // order (independent of which block finished last) into `out` (shared memory of the
 // last block).  Returns true in the last block, after a __syncthreads().
-template <int NQ>
-__device__ __forceinline__ bool reduce_publish(const double (&v)[NQ], int nq, RedBuf rb, double* out) {
-    __shared__ double sm_[NQ][32];
+template <typename TA, int NQ>
+__device__ __forceinline__ bool reduce_publish_t(const TA (&v)[NQ], int nq, RedBuf rb, double* out) {
+    __shared__ TA sm_[NQ][32];
     __shared__ int last_;
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     const int nthr = blockDim.x * blockDim.y;
     const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+    TA* part = reinterpret_cast<TA*>(rb.part);
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
         if (q < nq) {
-            double a = v[q];
+            TA a = v[q];
 #pragma unroll
             for (int off = 16; off; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
             if (lane == 0) sm_[q][warp] = a;
@@ -296,9 +304,9 @@ __device__ __forceinline__ bool reduce_publish(const double (&v)[NQ], int nq, Re
     const long long bid = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
     const long long nb = (long long)gridDim.x * gridDim.y * gridDim.z;
     if (tid < nq) {
-        double a = 0;
+        TA a = 0;
         for (int w = 0; w < nw; ++w) a += sm_[tid][w];
-        rb.part[bid * kRedQ + tid] = a;
+        part[bid * kRedQ + tid] = a;
     }
     __threadfence();
     __syncthreads();
@@ -309,10 +317,15 @@ __device__ __forceinline__ bool reduce_publish(const double (&v)[NQ], int nq, Re
     __syncthreads();
     if (!last_) return false;
     __threadfence();
-    for (int q = warp; q < nq; q += nw) out_sum_partials(rb.part, nb, q, lane, out);
+    for (int q = warp; q < nq; q += nw) out_sum_partials_t<TA>(part, nb, q, lane, out);
     if (tid == 0) *rb.counter = 0u;
     __syncthreads();
     return true;
+}
+
+template <int NQ>
+__device__ __forceinline__ bool reduce_publish(const double (&v)[NQ], int nq, RedBuf rb, double* out) {
+    return reduce_publish_t<double, NQ>(v, nq, rb, out);
 }
 
 }  // namespace st
@@ -452,18 +465,22 @@ __device__ __forceinline__ T row_stencil(const Geom& g, const T* __restrict__ co
 }
 
 // ---------------------------------------------------------------- finalisers (last block, thread 0)
-__device__ __forceinline__ void sm_start_finish(SmState* st, double sum, int steps) {
-    const double beta = sqrt(sum);
+template <typename T>
+__device__ __forceinline__ void sm_start_finish(SmState* st_, double sum, int steps) {
+    SmStateT<T>* st = smt<T>(st_);
+    const T beta = (T)sqrt(sum);
     st->beta = beta;
-    st->stop = !(beta > 0.0 && isfinite(beta));
-    st->s[0] = st->stop ? 0.0 : 1.0 / beta;
+    st->stop = !(beta > T(0) && isfinite(beta));
+    st->s[0] = st->stop ? T(0) : T(1) / beta;
     st->kdim = steps;
     st->g[0] = beta;
-    for (int q = 0; q < kMaxSmooth; ++q) st->coef[q] = 0.0;
+    for (int q = 0; q < kMaxSmooth; ++q) st->coef[q] = T(0);
 }
 
-__device__ __forceinline__ void sm_apply_finish(SmState* st, const double* out, int j) {
-    for (int q = 0; q <= j; ++q) st->H[q * kMaxSmooth + j] = st->s[q] * st->s[j] * out[q];
+template <typename T>
+__device__ __forceinline__ void sm_apply_finish(SmState* st_, const double* out, int j) {
+    SmStateT<T>* st = smt<T>(st_);
+    for (int q = 0; q <= j; ++q) st->H[q * kMaxSmooth + j] = st->s[q] * st->s[j] * (T)out[q];
 }
 
 __device__ __forceinline__ void fg_apply_finish(FgState* fs, const double* out, int j) {
@@ -627,48 +644,71 @@ namespace st {
 
 // Givens rotation of smoother column j and, when the Arnoldi process stops (breakdown or
 // the last step), the back substitution giving the final combination coefficients.
-__device__ inline void sm_givens_column_d(SmState* st, int j) {
-    double col[kMaxSmooth + 1];
-    for (int q = 0; q <= j + 1; ++q) col[q] = st->H[q * kMaxSmooth + j];
-    for (int q = 0; q < j; ++q) {
-        const double c = st->cs[q], s = st->sn[q];
-        const double a = col[q], b = col[q + 1];
-        col[q] = c * a + s * b;
-        col[q + 1] = -s * a + c * b;
-    }
-    const double a = col[j], b = col[j + 1];
-    const double r = hypot(a, b);
-    const double c = r > 0 ? a / r : 1.0, s = r > 0 ? b / r : 0.0;
+template <typename T>
+__device__ inline void sm_givens_column_t(SmStateT<T>* st, int j) {
+    T col[kMaxSmooth + 1];
+#pragma unroll
+    for (int q = 0; q <= kMaxSmooth; ++q)
+        if (q <= j + 1) col[q] = st->H[q * kMaxSmooth + j];
+#pragma unroll
+    for (int q = 0; q < kMaxSmooth; ++q)
+        if (q < j) {
+            const T c = st->cs[q], s = st->sn[q];
+            const T a = col[q], b = col[q + 1];
+            col[q] = c * a + s * b;
+            col[q + 1] = -s * a + c * b;
+        }
+    T a = T(0), b = T(0);
+#pragma unroll
+    for (int q = 0; q < kMaxSmooth; ++q)
+        if (q == j) {
+            a = col[q];
+            b = col[q + 1];
+        }
+    const T r = sqrt(a * a + b * b);
+    const T c = r > T(0) ? a / r : T(1), s = r > T(0) ? b / r : T(0);
     st->cs[j] = c;
     st->sn[j] = s;
-    col[j] = r;
-    col[j + 1] = 0;
-    st->g[j + 1] = -s * st->g[j];
-    st->g[j] = c * st->g[j];
-    for (int q = 0; q <= j + 1; ++q) st->R[q * kMaxSmooth + j] = col[q];
+    const T gj = st->g[j];
+    st->g[j + 1] = -s * gj;
+    st->g[j] = c * gj;
+#pragma unroll
+    for (int q = 0; q <= kMaxSmooth; ++q)
+        if (q <= j + 1) st->R[q * kMaxSmooth + j] = q == j ? r : (q == j + 1 ? T(0) : col[q]);
 }
 
-__device__ inline void sm_backsolve_d(SmState* st, int k) {
-    double y[kMaxSmooth];
-    for (int q = k - 1; q >= 0; --q) {
-        double a = st->g[q];
-        for (int l = q + 1; l < k; ++l) a -= st->R[q * kMaxSmooth + l] * y[l];
-        const double d = st->R[q * kMaxSmooth + q];
-        y[q] = d != 0 ? a / d : 0.0;
+template <typename T>
+__device__ inline void sm_backsolve_t(SmStateT<T>* st, int k) {
+    T y[kMaxSmooth];
+#pragma unroll
+    for (int q = kMaxSmooth - 1; q >= 0; --q) {
+        y[q] = T(0);
+        if (q < k) {
+            T a = st->g[q];
+#pragma unroll
+            for (int l = 0; l < kMaxSmooth; ++l)
+                if (l > q && l < k) a -= st->R[q * kMaxSmooth + l] * y[l];
+            const T d = st->R[q * kMaxSmooth + q];
+            y[q] = d != T(0) ? a / d : T(0);
+        }
     }
-    for (int q = 0; q < kMaxSmooth; ++q) st->coef[q] = q < k ? y[q] * st->s[q] : 0.0;
+#pragma unroll
+    for (int q = 0; q < kMaxSmooth; ++q) st->coef[q] = q < k ? y[q] * st->s[q] : T(0);
 }
 
-__device__ inline void sm_update_finish(SmState* st, double sum, int j, int steps) {
-    const double h = sqrt(sum);
+template <typename T>
+__device__ inline void sm_update_finish(SmState* st_, double sum, int j, int steps) {
+    SmStateT<T>* st = smt<T>(st_);
+    const T h = (T)sqrt(sum);
     st->H[(j + 1) * kMaxSmooth + j] = h;
-    sm_givens_column_d(st, j);
-    const bool brk = !(h > 1e-13 * st->beta) || !isfinite(h);
+    sm_givens_column_t<T>(st, j);
+    const T tol = sizeof(T) == 4 ? T(1e-6) : T(1e-13);  // breakdown relative to the initial residual
+    const bool brk = !(h > tol * st->beta) || !isfinite(h);
     if (brk)
         st->kdim = j + 1;
     else
-        st->s[j + 1] = 1.0 / h;
-    if (brk || j + 1 == steps) sm_backsolve_d(st, j + 1);
+        st->s[j + 1] = T(1) / h;
+    if (brk || j + 1 == steps) sm_backsolve_t<T>(st, j + 1);
 }
 
 __device__ inline void fg_givens_column_d(FgState* fs, int j) {

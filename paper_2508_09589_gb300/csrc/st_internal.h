@@ -73,17 +73,33 @@ struct OpLc {
     const unsigned char* st_dir;
 };
 
-// Per-call smoother state (device).
-struct SmState {
-    double H[(kMaxSmooth + 1) * kMaxSmooth];   // Hessenberg matrix, row-major
-    double R[(kMaxSmooth + 1) * kMaxSmooth];   // after Givens rotations
-    double s[kMaxSmooth + 1];                  // basis scales 1 / ||u_j||
-    double cs[kMaxSmooth], sn[kMaxSmooth], g[kMaxSmooth + 1];
-    double coef[kMaxSmooth];                   // y_j s_j of the final update
-    double beta;
+// Per-call smoother state (device), in the arithmetic type T of its multigrid (float for
+// the mixed V-cycle: FP64 arithmetic is a slow path on this GPU).  SmState is the opaque
+// storage (large enough for either type); kernels view it as SmStateT<T>.
+template <typename T>
+struct SmStateT {
+    T H[(kMaxSmooth + 1) * kMaxSmooth];   // Hessenberg matrix, row-major
+    T R[(kMaxSmooth + 1) * kMaxSmooth];   // after Givens rotations
+    T s[kMaxSmooth + 1];                  // basis scales 1 / ||u_j||
+    T cs[kMaxSmooth], sn[kMaxSmooth], g[kMaxSmooth + 1];
+    T coef[kMaxSmooth];                   // y_j s_j of the final update
+    T beta;
     int kdim;
     int stop;
 };
+
+struct alignas(16) SmState {
+    unsigned char bytes[sizeof(SmStateT<double>)];
+};
+
+template <typename T>
+__host__ __device__ inline SmStateT<T>* smt(SmState* s) {
+    return reinterpret_cast<SmStateT<T>*>(s);
+}
+template <typename T>
+__host__ __device__ inline const SmStateT<T>* smt(const SmState* s) {
+    return reinterpret_cast<const SmStateT<T>*>(s);
+}
 
 // FGMRES state (device).
 struct FgState {
@@ -145,11 +161,15 @@ void launch_restrict(const Geom& gf, const Geom& gc, int kind, int sd, const T* 
 template <typename T>
 void launch_prolong(const Geom& gf, const Geom& gc, int kind, int sd, const T* xc, T* xf, cudaStream_t s);
 
-// Jacobi-GMRES smoother on one level.
+// Jacobi-GMRES smoother on one level (w2: second scratch vector for the fused FP32 steps).
 template <typename T>
 void launch_smooth(int sd, int lvl, const OpL0<T>& o0, const OpLc<T>& oc, bool tr, const T* b, T* x,
-                   const T* dinv, Basis<T> U, T* w, int steps, bool zero_init, SmState* st, RedBuf rb,
+                   const T* dinv, Basis<T> U, T* w, T* w2, int steps, bool zero_init, SmState* st, RedBuf rb,
                    cudaStream_t s);
+// Fused FP32 Arnoldi step j -> j+1 on a stencil level (k_arnoldi.cu).
+void launch_arnoldi(const Geom& g, const float* coef, const unsigned char* dir, const float* dinv,
+                    const Ptrs<float>& U, const float* w_in, float* w_out, int j, SmState* st, RedBuf rb,
+                    cudaStream_t s);
 
 // Coarsest solve x = Ainv b (or Ainv^T b).
 template <typename T>

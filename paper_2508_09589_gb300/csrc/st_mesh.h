@@ -32,7 +32,7 @@ struct MGWork {
     bool ready = false;
     int nbasis = 0;
     long long dinv_version = -1;
-    std::vector<T*> b, x, r, w, dinv;
+    std::vector<T*> b, x, r, w, w2, dinv;
     std::vector<Basis<T>> U;
 };
 
