@@ -180,7 +180,7 @@ def run_native(args):
     # end to end through the C ABI with host buffers (design in, sensitivities out)
     sens_h = np.empty(gamma_h.size)
     e2e_t = []
-    for _ in range(max(1, args.steps // 2)):
+    for _ in range(max(1, args.steps // 2) if args.e2e else 0):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         mesh.set_design(gamma_h, layout)
@@ -188,7 +188,7 @@ def run_native(args):
         mesh.solve_adjoint("compliance", opts=opt)
         sens_h = mesh.sensitivities()
         e2e_t.append(time.perf_counter() - t0)
-    e2e_step = max_over_ranks(statistics.median(e2e_t), world)
+    e2e_step = max_over_ranks(statistics.median(e2e_t), world) if e2e_t else float("nan")
 
     # all-FP64 comparison arm (one step), mixed vs FP64 at the same 1e-8 outer tolerance
     fp64 = None
@@ -325,6 +325,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--cpu-sample", default="24")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false", help="skip the host-buffer end-to-end leg")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
