@@ -238,13 +238,73 @@ def run_native(args):
             "roofline": roof,
             "clocks": clk.summary(),
         }
+    mesh.close()
+    if rank == 0:
+        if args.serve_requests > 0:
+            line["serving"] = serving_bench(args)
         if args.cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_sample)
         print(json.dumps(line), flush=True)
-    mesh.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def serving_bench(args):
+    """Serving stream (the first R requests of the 256-request stream: 2-D + time meshes with
+    per-axis element counts log-uniform in 32..512, time 32..256, own seeded designs), each a
+    forward + adjoint solve to 1e-8 with sensitivities.  Per precision: a closed-loop run
+    (all requests submitted at once) gives the saturation throughput; an open-loop run with
+    Poisson arrivals at a fraction of that rate gives the latency distribution."""
+    import torch
+    from paper_2508_09589_gb300 import Server, options, source
+    reqs = W.serving_requests()[: args.serve_requests]
+    designs = [W.make_design(w).reshape(-1) for w in reqs]
+    dofs = [(w.ns[0] + 1) * (w.ns[1] + 1) * (w.nt + 1) for w in reqs]
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(0.85 * free)
+    src = source("uniform", 1.0)
+
+    def run(precision, arrivals):
+        opt = options(rtol=1e-8, precision=precision, max_it=400)
+        srv = Server(budget, max_inflight=args.serve_slots)
+        t0 = time.perf_counter()
+        tickets, pending = {}, set()
+        k = 0
+        res = {}
+        while k < len(reqs) or pending:
+            now = time.perf_counter() - t0
+            while k < len(reqs) and arrivals[k] <= now:
+                w = reqs[k]
+                tickets[k] = srv.submit(w.ns, w.nt, designs[k], "extruded", src=src, opts=opt,
+                                        material=w.material, bc=w.bc, bc_width=w.bc_width)
+                pending.add(k)
+                k += 1
+            for q in list(pending):
+                done, r, _ = srv.poll(tickets[q])
+                if done:
+                    res[q] = r
+                    pending.discard(q)
+            time.sleep(0.0005)
+        span = time.perf_counter() - t0
+        srv.close()
+        lat = np.array([res[q]["latency_s"] for q in range(len(reqs))])
+        bad = sum(1 for q in range(len(reqs)) if res[q]["status"] != 0)
+        return {"requests": len(reqs), "seconds": span, "req_per_s": len(reqs) / span,
+                "dof_per_s": 2.0 * sum(dofs) / span,
+                "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                "max_ms": 1e3 * float(lat.max()), "failed": bad}
+
+    out = {"stream": f"first {len(reqs)} of the 256-request stream", "slots": args.serve_slots,
+           "hbm_budget_gb": budget / 1e9, "dofs_total": int(sum(dofs))}
+    for precision in ("mixed", "fp64"):
+        closed = run(precision, np.zeros(len(reqs)))
+        rate = args.serve_load * closed["req_per_s"]
+        arrivals = W.poisson_arrivals(len(reqs), rate)
+        opened = run(precision, arrivals)
+        opened["offered_req_per_s"] = rate
+        out[precision] = {"saturation": closed, f"poisson_{int(100 * args.serve_load)}pct": opened}
+    return out
 
 
 def kernel_roofline(mesh, N, args):
@@ -270,6 +330,30 @@ def kernel_roofline(mesh, N, args):
     return {"kernel": "k_apply<2,float,L0> (level-0 FP32 operator)", "bound": "hbm", "achieved": ach,
             "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
             "peak_source": kind, "algorithmic_bytes_per_launch": byts, "launch_ms": 1e3 * t}
+
+
+def run_vcycles(args):
+    """Kernel-profiling mode: design set-up and K mixed-precision V-cycles on the workload
+    (no Krylov solve, so only the multigrid storage is resident: a few GB at 256^2 x 256)."""
+    import torch
+    from paper_2508_09589_gb300 import Mesh
+    w = W.WORKLOADS[args.workload]
+    mesh = Mesh(w.ns, w.nt, material=w.material, bc=w.bc, bc_width=w.bc_width, tau=w.tau)
+    mesh.set_design(W.make_design(w).reshape(-1), "extruded" if w.extruded else "spacetime")
+    N = mesh.n_nodes
+    g = torch.Generator(device="cuda").manual_seed(5)
+    b = torch.randn(N, dtype=torch.float32, device="cuda", generator=g)
+    x = torch.empty_like(b)
+    mesh.vcycle(b, x, "mixed")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.vcycles):
+        mesh.vcycle(b, x, "mixed")
+    torch.cuda.synchronize()
+    t = (time.perf_counter() - t0) / max(1, args.vcycles)
+    print(json.dumps({"mode": "vcycles", "workload": w.name, "vcycles": args.vcycles, "ms_per_vcycle": 1e3 * t,
+                      "device_gb": mesh.device_bytes / 1e9, "finite": bool(torch.isfinite(x).all())}), flush=True)
+    mesh.close()
 
 
 # ---------------------------------------------------------------------------- oracle (CPU) arm
@@ -325,9 +409,16 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--cpu-sample", default="24")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--serve-requests", type=int, default=48, help="serving leg size (0 skips it)")
+    ap.add_argument("--serve-slots", type=int, default=4, help="concurrent solves in the server")
+    ap.add_argument("--serve-load", type=float, default=0.7, help="Poisson rate as a fraction of saturation")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--vcycles", type=int, default=0,
+                    help="profiling mode: only K mixed V-cycles on the workload, no solve")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.vcycles > 0:
+        run_vcycles(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_native(args)
