@@ -148,10 +148,14 @@ def run_native(args):
         mesh.sensitivities(sens_d)
         stats.update(fwd=f, adj=a, phi=phi)
 
+    # event timing of the level-0 smoother operator apply inside the solves (event nodes are
+    # captured into the V-cycle graphs during warm-up; the totals restart at the timed region)
+    mesh.apply_timer(True)
     for _ in range(args.warmup):
         step_device()
     torch.cuda.synchronize()
     barrier(world)
+    mesh.apply_timer(True)
     k0 = L.st_kernel_launches()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
@@ -169,6 +173,8 @@ def run_native(args):
         wall = time.perf_counter() - t0
         torch.cuda.nvtx.range_pop()
     launches = L.st_kernel_launches() - k0
+    apply_ms, apply_n = mesh.apply_timer_read()
+    mesh.apply_timer(False)
     # the library synchronises its own stream inside each solve, so host wall time brackets
     # all device work of the step; the torch events bracket the same region on the device
     dev_s = max(ev0.elapsed_time(ev1) / 1e3, wall)
@@ -211,9 +217,7 @@ def run_native(args):
                 "rel_res_fwd": f64["rel_res"], "rel_res_adj": a64["rel_res"],
                 "mixed_vs_fp64_rel_T_diff": float(np.abs(s_mixed - s64).max() / np.abs(s64).max())}
 
-    # dominant kernel, timed live with CUDA events on the launching stream: the level-0
-    # Jacobi-GMRES smoothing sweep (10 Arnoldi steps) of the mixed V-cycle
-    roof = kernel_roofline(mesh, N, args)
+    roof = kernel_roofline(N, gamma_h.size if layout == "spacetime" else 0, apply_ms, apply_n, args)
 
     if rank == 0:
         f, a = stats["fwd"], stats["adj"]
@@ -307,53 +311,30 @@ def serving_bench(args):
     return out
 
 
-def kernel_roofline(mesh, N, args):
-    """Level-0 FP32 operator apply, events on the launching stream; algorithmic bytes =
-    4 B read + 4 B write per node (the extruded design and masks are O(n_x n_y))."""
-    import torch
+def kernel_roofline(N, n_st_elems, apply_ms, apply_n, args):
+    """Dominant kernel: the level-0 smoother operator apply w = A D^-1 u_j (20 launches per
+    V-cycle), its launches timed with CUDA events on the mesh stream inside the timed steps.
+    Algorithmic bytes per launch: u_j and D^-1 read, w written (12 B per node in FP32), plus
+    the BF16 density (2 B per space-time element) on space-time designs; the per-spatial-node
+    stencils of time-constant designs are O(n_x n_y) and stay in L2."""
     peak, kind = _peaks()
-    x = torch.randn(N, dtype=torch.float32, device="cuda")
-    y = torch.empty_like(x)
-    for _ in range(3):
-        mesh.apply(0, x, y, "mixed")
-    reps = 20
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record()
-    for _ in range(reps):
-        mesh.apply(0, x, y, "mixed")
-    e1.record()
-    torch.cuda.synchronize()
-    t = e0.elapsed_time(e1) / 1e3 / reps
-    byts = 8.0 * N
+    tsz = 4 if args.precision == "mixed" else 8
+    byts = 3.0 * tsz * N + (2.0 * n_st_elems if args.precision == "mixed" else 8.0 * n_st_elems)
+    if apply_n <= 0:
+        return {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None, "traffic": None}
+    t = apply_ms / 1e3 / apply_n
     ach = byts / t / 1e9
-    return {"kernel": "k_apply<2,float,L0> (level-0 FP32 operator)", "bound": "hbm", "achieved": ach,
-            "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
-            "peak_source": kind, "algorithmic_bytes_per_launch": byts, "launch_ms": 1e3 * t}
+    name = "km_sm_applyw" if n_st_elems == 0 else "k_sm_applyw"
+    return {"kernel": f"{name} level 0 ({'FP32' if tsz == 4 else 'FP64'} smoother operator apply)",
+            "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "traffic": TRAFFIC_PER_LAUNCH.get((name, args.workload, args.precision)),
+            "peak_source": kind, "algorithmic_bytes_per_launch": byts, "launch_ms": 1e3 * t,
+            "launches_timed": int(apply_n)}
 
 
-def run_vcycles(args):
-    """Kernel-profiling mode: design set-up and K mixed-precision V-cycles on the workload
-    (no Krylov solve, so only the multigrid storage is resident: a few GB at 256^2 x 256)."""
-    import torch
-    from paper_2508_09589_gb300 import Mesh
-    w = W.WORKLOADS[args.workload]
-    mesh = Mesh(w.ns, w.nt, material=w.material, bc=w.bc, bc_width=w.bc_width, tau=w.tau)
-    mesh.set_design(W.make_design(w).reshape(-1), "extruded" if w.extruded else "spacetime")
-    N = mesh.n_nodes
-    g = torch.Generator(device="cuda").manual_seed(5)
-    b = torch.randn(N, dtype=torch.float32, device="cuda", generator=g)
-    x = torch.empty_like(b)
-    mesh.vcycle(b, x, "mixed")
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.vcycles):
-        mesh.vcycle(b, x, "mixed")
-    torch.cuda.synchronize()
-    t = (time.perf_counter() - t0) / max(1, args.vcycles)
-    print(json.dumps({"mode": "vcycles", "workload": w.name, "vcycles": args.vcycles, "ms_per_vcycle": 1e3 * t,
-                      "device_gb": mesh.device_bytes / 1e9, "finite": bool(torch.isfinite(x).all())}), flush=True)
-    mesh.close()
+# DRAM read + write bytes of one launch, from an ncu capture of the current kernel version
+# (profiles/ names the capture); None when no capture of this version exists.
+TRAFFIC_PER_LAUNCH = {}
 
 
 # ---------------------------------------------------------------------------- oracle (CPU) arm

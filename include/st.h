@@ -60,6 +60,11 @@ enum { ST_SRC_UNIFORM = 0, ST_SRC_SIN_T = 1 };
 enum { ST_OBJ_COMPLIANCE = 0, ST_OBJ_PNORM = 1 };
 enum { ST_STATE_T = 0, ST_STATE_LAMBDA = 1, ST_STATE_RHS = 2, ST_STATE_ADJ_RHS = 3 };
 enum { ST_COARSEN_SEMI = 0, ST_COARSEN_FULL = 1 };
+/* Coarsest-level solver: AUTO = dense FP64 inverse when the coarsest level has at most 4096
+ * nodes, else Jacobi-GMRES; DENSE = always the dense inverse (error above 4096 nodes);
+ * GMRES = FP64 right-Jacobi-preconditioned restarted GMRES(16), the paper's coarsest solve
+ * (Sec. 3.2), stopped at coarse_rtol or after coarse_max_it iterations. */
+enum { ST_COARSE_AUTO = 0, ST_COARSE_DENSE = 1, ST_COARSE_GMRES = 2 };
 
 /* Modified SIMP (Sec. 2.2): C = C_ins + (C_con - C_ins) g^p_c, k = k_ins + (k_con - k_ins) g^p_k.
  * Integer powers p_c, p_k >= 1. */
@@ -84,6 +89,11 @@ typedef struct {
     int max_levels;          /* 0 = no limit */
     int coarsening;          /* ST_COARSEN_SEMI (Algorithm 1) or ST_COARSEN_FULL (ablation) */
     int device;              /* CUDA device ordinal */
+    int coarse_solver;       /* ST_COARSE_* */
+    int coarse_max_it;       /* Jacobi-GMRES iterations on the coarsest level (0: 200) */
+    double coarse_rtol;      /* its relative residual target (0: 1e-6) */
+    int march_blocks;        /* tuning: thread-block budget of the time-marching stencil kernels
+                                (0: 4096); a smaller budget gives each block a longer time chunk */
 } st_mesh_desc;
 
 typedef struct {
@@ -198,8 +208,21 @@ st_status st_vcycle(st_mesh* m, int precision, int transpose, const void* b, voi
  * spatial block (row-major, i <= j).  Extruded designs store 2 versions (first slab, other
  * slabs) per spatial element.  count is in doubles; host pointer. */
 st_status st_level_elements(st_mesh* m, int level, double* out, size_t count);
-/* Copy the FP64 inverse of the coarsest operator (n x n, row-major) to a host buffer. */
+/* Copy the FP64 inverse of the coarsest operator (n x n, row-major) to a host buffer.
+ * ST_ERR_STATE when the coarsest level is solved by Jacobi-GMRES (no dense inverse). */
 st_status st_coarse_inverse(st_mesh* m, double* out, size_t count);
+
+/* ---- Diagnostics (no counterpart in the paper) ----
+ * CUDA-event timing of the level-0 smoother operator apply (w = A D^-1 u_j, the most
+ * frequently launched stencil kernel of the V-cycle, Sec. 3.2) inside real solves.
+ * enable = 1 resets the totals and records an event pair around every such launch on the
+ * mesh stream (event nodes inside captured V-cycles; cached V-cycle graphs are rebuilt when
+ * the setting changes); the pairs are read after the host synchronisation that ends each
+ * outer Krylov iteration.  enable = 0 stops recording and keeps the totals.  Synchronises
+ * the mesh stream.  Errors: ST_ERR_ARG (null mesh), ST_ERR_CUDA (event creation). */
+st_status st_apply_timer(st_mesh* m, int enable);
+/* Totals since the last st_apply_timer(m, 1): summed launch time in ms and launch count. */
+st_status st_apply_timer_read(st_mesh* m, double* total_ms, long long* launches);
 
 /* ---- Serving: continuous batching of forward + adjoint + sensitivity requests ---- */
 typedef struct {

@@ -22,6 +22,7 @@ SRC = {"uniform": 0, "sin_t": 1}
 OBJ = {"compliance": 0, "pnorm": 1}
 WHICH = {"T": 0, "lambda": 1, "rhs": 2, "adj_rhs": 3}
 COARSEN = {"semi": 0, "full": 1}
+COARSE = {"auto": 0, "dense": 1, "gmres": 2}
 
 
 class Material(C.Structure):
@@ -33,7 +34,8 @@ class MeshDesc(C.Structure):
     _fields_ = [("ndim_space", C.c_int), ("n", C.c_int * 3), ("n_t", C.c_int), ("ext", C.c_double * 3),
                 ("tau", C.c_double), ("mat", Material), ("bc", C.c_int), ("bc_width", C.c_double),
                 ("lambda_crit", C.c_double), ("coarse_dof_cap", C.c_longlong), ("max_levels", C.c_int),
-                ("coarsening", C.c_int), ("device", C.c_int)]
+                ("coarsening", C.c_int), ("device", C.c_int), ("coarse_solver", C.c_int),
+                ("coarse_max_it", C.c_int), ("coarse_rtol", C.c_double), ("march_blocks", C.c_int)]
 
 
 class Source(C.Structure):
@@ -111,6 +113,8 @@ SIGNATURES = {
     "st_vcycle": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "st_level_elements": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t]),
     "st_coarse_inverse": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "st_apply_timer": (C.c_int, [C.c_void_p, C.c_int]),
+    "st_apply_timer_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "st_server_create": (C.c_int, [C.POINTER(ServerDesc), C.POINTER(C.c_void_p)]),
     "st_server_destroy": (C.c_int, [C.c_void_p]),
     "st_submit": (C.c_int, [C.c_void_p, C.POINTER(Request), C.POINTER(C.c_uint64)]),

@@ -40,7 +40,8 @@ def _material(m: Optional[dict]) -> L.Material:
 def mesh_desc(ns: Sequence[int], nt: int, *, ext: Optional[Sequence[float]] = None, tau: float = 1.0,
               material: Optional[dict] = None, bc: str = "patch_left", bc_width: float = 0.1,
               lambda_crit: float = 0.5, coarse_dof_cap: int = 2000, max_levels: int = 0,
-              coarsening: str = "semi", device: int = 0) -> L.MeshDesc:
+              coarsening: str = "semi", device: int = 0, coarse_solver: str = "auto",
+              coarse_max_it: int = 0, coarse_rtol: float = 0.0, march_blocks: int = 0) -> L.MeshDesc:
     d = L.MeshDesc()
     L.lib().st_mesh_desc_default(C.byref(d))
     d.ndim_space = len(ns)
@@ -59,6 +60,10 @@ def mesh_desc(ns: Sequence[int], nt: int, *, ext: Optional[Sequence[float]] = No
     d.max_levels = int(max_levels)
     d.coarsening = L.COARSEN[coarsening]
     d.device = int(device)
+    d.coarse_solver = L.COARSE[coarse_solver]
+    d.coarse_max_it = int(coarse_max_it)
+    d.coarse_rtol = float(coarse_rtol)
+    d.march_blocks = int(march_blocks)
     return d
 
 
@@ -266,6 +271,17 @@ class Mesh:
         out = np.empty(n * n, dtype=np.float64)
         L.check(L.lib().st_coarse_inverse(self._h, C.c_void_p(out.ctypes.data), out.size), "st_coarse_inverse")
         return out.reshape(n, n)
+
+    def apply_timer(self, enable: bool = True):
+        """Start (reset) or stop CUDA-event timing of the level-0 smoother operator apply."""
+        L.check(L.lib().st_apply_timer(self._h, int(bool(enable))), "st_apply_timer")
+
+    def apply_timer_read(self):
+        """(summed launch time in ms, number of timed launches) since apply_timer(True)."""
+        ms = C.c_double()
+        n = C.c_longlong()
+        L.check(L.lib().st_apply_timer_read(self._h, C.byref(ms), C.byref(n)), "st_apply_timer_read")
+        return ms.value, n.value
 
 
 def plan_hierarchy(ns, nt, **kw):

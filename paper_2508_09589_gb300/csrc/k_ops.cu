@@ -629,6 +629,16 @@ void launch_prolong(const Geom& gf, const Geom& gc, int kind, int sd, const T* x
     ST_SD_DISPATCH(sd, k_prolong<SD, T><<<c.grid, c.block, 0, s>>>(gf, gc, kind, xc, xf));
 }
 
+// Timing event on stream s: an event node when the stream is being captured into a graph,
+// a plain record otherwise.  A failure only loses the sample (the reader skips pairs whose
+// elapsed time cannot be read), so its error is cleared here.
+static void record_timing_event(cudaEvent_t e, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) cs = cudaStreamCaptureStatusNone;
+    const unsigned flags = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+    if (cudaEventRecordWithFlags(e, s, flags) != cudaSuccess) cudaGetLastError();
+}
+
 // Below this many nodes a level's Arnoldi step is latency bound: the fused stencil + dots
 // kernel (one launch fewer) is used; above it the apply, dots and update run as separate
 // bandwidth-efficient kernels.
@@ -636,7 +646,8 @@ constexpr long long kSplitNodes = 0;
 
 template <int SD, typename T, int LV, bool TR>
 static void smooth_impl(const OpL0<T>& o0, const OpLc<T>& oc, const T* b, T* x, const T* dinv, Basis<T> U, T* w,
-                        T* w2, int steps, bool zero_init, SmState* st, RedBuf rb, cudaStream_t s) {
+                        T* w2, int steps, bool zero_init, SmState* st, RedBuf rb, cudaStream_t s,
+                        cudaEvent_t* ev) {
     const Geom& g = LV == 0 ? o0.g : oc.g;
     const long long N = g.nnodes;
     const LaunchCfg c = node_cfg(g);
@@ -653,7 +664,7 @@ static void smooth_impl(const OpL0<T>& o0, const OpLc<T>& oc, const T* b, T* x, 
     // bound levels; on large levels the split apply / dots / update kernels stream faster.
     constexpr long long kFusedMaxNodes = 15000;
     const bool fused = march && std::is_same<T, float>::value && w2 != nullptr && steps >= 2 && steps + 1 <= 16 &&
-                       N <= kFusedMaxNodes;
+                       N <= kFusedMaxNodes && ev == nullptr;
     if (zero_init) {
         launch_sm_norm<T>(N, b, steps, st, rb, s);
     } else {
@@ -686,10 +697,13 @@ static void smooth_impl(const OpL0<T>& o0, const OpLc<T>& oc, const T* b, T* x, 
     for (int j = 0; j < steps; ++j) {
         note_launch(s);
         if (split) {
+            // optional timing events around the operator apply (event nodes when captured)
+            if (ev) record_timing_event(ev[2 * j], s);
             if (march)
                 km_sm_applyw<T><<<mgrid, mblock, 0, s>>>(g, coef, dir, mg.chunk, dinv, U.u[j], w, j, st);
             else
                 k_sm_applyw<SD, T, LV, TR><<<c.grid, c.block, 0, s>>>(o0, oc, dinv, U.u[j], w, j, st);
+            if (ev) record_timing_event(ev[2 * j + 1], s);
             launch_dots<T>(N, w, P, j + 1, j, 0, st, rb, s);
         } else if (march) {
             km_sm_apply<T><<<mgrid, mblock, 0, s>>>(g, coef, dir, mg.chunk, dinv, U, w, j, st, rb);
@@ -703,13 +717,14 @@ static void smooth_impl(const OpL0<T>& o0, const OpLc<T>& oc, const T* b, T* x, 
 
 template <typename T>
 void launch_smooth(int sd, int lvl, const OpL0<T>& o0, const OpLc<T>& oc, bool tr, const T* b, T* x, const T* dinv,
-                   Basis<T> U, T* w, T* w2, int steps, bool zero_init, SmState* st, RedBuf rb, cudaStream_t s) {
+                   Basis<T> U, T* w, T* w2, int steps, bool zero_init, SmState* st, RedBuf rb, cudaStream_t s,
+                   cudaEvent_t* ev) {
     if (lvl == 0) {
-        ST_SD_DISPATCH(sd, if (tr) smooth_impl<SD, T, 0, true>(o0, oc, b, x, dinv, U, w, w2, steps, zero_init, st, rb, s);
-                       else smooth_impl<SD, T, 0, false>(o0, oc, b, x, dinv, U, w, w2, steps, zero_init, st, rb, s));
+        ST_SD_DISPATCH(sd, if (tr) smooth_impl<SD, T, 0, true>(o0, oc, b, x, dinv, U, w, w2, steps, zero_init, st, rb, s, ev);
+                       else smooth_impl<SD, T, 0, false>(o0, oc, b, x, dinv, U, w, w2, steps, zero_init, st, rb, s, ev));
     } else {
-        ST_SD_DISPATCH(sd, if (tr) smooth_impl<SD, T, 1, true>(o0, oc, b, x, dinv, U, w, w2, steps, zero_init, st, rb, s);
-                       else smooth_impl<SD, T, 1, false>(o0, oc, b, x, dinv, U, w, w2, steps, zero_init, st, rb, s));
+        ST_SD_DISPATCH(sd, if (tr) smooth_impl<SD, T, 1, true>(o0, oc, b, x, dinv, U, w, w2, steps, zero_init, st, rb, s, ev);
+                       else smooth_impl<SD, T, 1, false>(o0, oc, b, x, dinv, U, w, w2, steps, zero_init, st, rb, s, ev));
     }
 }
 
@@ -808,7 +823,7 @@ void launch_mask_copy(int sd, const Geom& g, const double* src, double* dst, cud
     template void launch_restrict<T>(const Geom&, const Geom&, int, int, const T*, T*, cudaStream_t);               \
     template void launch_prolong<T>(const Geom&, const Geom&, int, int, const T*, T*, cudaStream_t);                \
     template void launch_smooth<T>(int, int, const OpL0<T>&, const OpLc<T>&, bool, const T*, T*, const T*, Basis<T>, \
-                                   T*, T*, int, bool, SmState*, RedBuf, cudaStream_t);                              \
+                                   T*, T*, int, bool, SmState*, RedBuf, cudaStream_t, cudaEvent_t*);                \
     template void launch_coarse_solve<T>(const double*, int, bool, const T*, T*, cudaStream_t);                     \
     template void launch_fg_apply_dots<T>(int, const OpL0<double>&, bool, const T*, T*, double*, double* const*,    \
                                           int, FgState*, RedBuf, cudaStream_t);                                      \

@@ -287,6 +287,35 @@ void launch_sm_combine(long long n, T* x, const T* dinv, const Ptrs<T>& U, int s
 }
 
 template <typename T>
+__global__ void k_cg_begin(SmState* st, T rtol) {
+    SmStateT<T>* t = smt<T>(st);
+    t->rtol_rel = rtol;
+    t->atol = T(-1);
+}
+
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(256) k_convert(const TI* __restrict__ in, TO* __restrict__ out, long long n) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+        out[q] = (TO)in[q];
+}
+
+template <typename T>
+void launch_cg_begin(SmState* st, double rtol, cudaStream_t s) {
+    note_launch(s);
+    k_cg_begin<T><<<1, 1, 0, s>>>(st, (T)rtol);
+}
+
+template <typename TI, typename TO>
+void launch_convert(const TI* in, TO* out, long long n, cudaStream_t s) {
+    note_launch(s);
+    k_convert<TI, TO><<<stream_blocks(n, 1), 256, 0, s>>>(in, out, n);
+}
+
+template void launch_cg_begin<double>(SmState*, double, cudaStream_t);
+template void launch_convert<float, double>(const float*, double*, long long, cudaStream_t);
+template void launch_convert<double, float>(const double*, float*, long long, cudaStream_t);
+
+template <typename T>
 void launch_sm_norm(long long n, const T* b, int steps, SmState* st, RedBuf rb, cudaStream_t s) {
     note_launch(s);
     k_sm_norm<T><<<stream_blocks(n, Vec16<T>::W), 256, 0, s>>>(n, b, steps, st, rb);

@@ -229,7 +229,9 @@ long long st_footprint_bytes(const st_mesh_desc* d, int precision, int restart) 
     }
     bytes += N0 * 8LL * (5 + restart + 1) + N0 * (long long)tsz * restart;  // FP64 vectors, V, Z
     bytes += ne0 * 26LL;                                                     // design copies, sensitivities
-    bytes += 2 * nc * nc * 8 + (4 << 20);
+    const bool iter = d->coarse_solver == ST_COARSE_GMRES || (d->coarse_solver == ST_COARSE_AUTO && nc > 4096);
+    bytes += iter ? nc * 8LL * 23 : 2 * nc * nc * 8;  // Jacobi-GMRES(16) vectors or the dense inverse
+    bytes += 4 << 20;
     return bytes;
 }
 

@@ -87,6 +87,8 @@ Mesh::~Mesh() {
                     tacc[l * 3 + 1] / tcycles, tacc[l * 3 + 2] / tcycles);
     }
     for (cudaEvent_t e : tev) cudaEventDestroy(e);
+    for (cudaEvent_t e : at_ev)
+        if (e) cudaEventDestroy(e);
     if (vt_trace) {
         std::vector<unsigned long long> t(4096);
         cudaMemcpy(t.data(), vt_trace, t.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
@@ -99,6 +101,22 @@ Mesh::~Mesh() {
     for (void* p : allocs) cudaFree(p);
     if (h_fg) cudaFreeHost(h_fg);
     if (own_stream && own) cudaStreamDestroy(own);
+}
+
+void Mesh::timer_collect() {
+    if (!at_pending) return;
+    at_pending = false;
+    for (int sw = 0; sw < 2; ++sw)
+        for (int j = 0; j < at_steps; ++j) {
+            float ms = 0.f;
+            cudaEvent_t* e = at_ev + sw * 2 * kMaxSmooth + 2 * j;
+            if (cudaEventElapsedTime(&ms, e[0], e[1]) == cudaSuccess) {
+                at_ms += ms;
+                ++at_launches;
+            } else {
+                cudaGetLastError();
+            }
+        }
 }
 
 void Mesh::drop_graphs() {
@@ -142,6 +160,7 @@ static Geom make_geom(const st_mesh_desc& d, const int n[3], int nt, const doubl
         g.phi[q] = -1;
     }
     for (int q = 0; q < sd; ++q) patch_range(n[q], d.bc_width, g.plo[q], g.phi[q]);
+    g.march_blocks = d.march_blocks;
     return g;
 }
 
@@ -198,10 +217,13 @@ static st_status build_levels(const st_mesh_desc& d, std::vector<LevelH>& lv) {
 static st_status build_hierarchy(Mesh* m) {
     CKS(build_levels(m->desc, m->lv));
     const long long nc = m->lv.back().g.nnodes;
-    if (nc > kMaxCoarse)
+    m->coarse_iter = m->desc.coarse_solver == ST_COARSE_GMRES ||
+                     (m->desc.coarse_solver == ST_COARSE_AUTO && nc > kMaxCoarse);
+    if (nc > kMaxCoarse && !m->coarse_iter)
         return fail(ST_ERR_ARG, "coarsest level has " + std::to_string(nc) + " nodes (> " +
                                     std::to_string(kMaxCoarse) +
-                                    "): the element counts cannot be halved far enough; use counts with more factors of 2");
+                                    "): the element counts cannot be halved far enough for the dense coarsest solve; "
+                                    "use counts with more factors of 2 or the Jacobi-GMRES coarsest solver");
     return ST_OK;
 }
 
@@ -291,6 +313,12 @@ st_status validate_desc(const st_mesh_desc* d) {
     if (!(d->mat.C_ins > 0 && d->mat.C_con > 0 && d->mat.k_ins > 0 && d->mat.k_con > 0))
         return fail(ST_ERR_ARG, "material constants must be positive");
     if (d->bc < 0 || d->bc > 3) return fail(ST_ERR_ARG, "unknown boundary-condition kind");
+    if (d->march_blocks < 0 || d->march_blocks > kMaxBlocks)
+        return fail(ST_ERR_ARG, "march_blocks must be in [0, " + std::to_string(kMaxBlocks) + "]");
+    if (d->coarse_solver < ST_COARSE_AUTO || d->coarse_solver > ST_COARSE_GMRES)
+        return fail(ST_ERR_ARG, "unknown coarse_solver");
+    if (d->coarse_max_it < 0 || d->coarse_rtol < 0 || !(d->coarse_rtol < 1))
+        return fail(ST_ERR_ARG, "coarse_max_it must be >= 0 and coarse_rtol in [0, 1)");
     if (d->coarse_dof_cap < 1 || d->coarse_dof_cap > kMaxCoarse)
         return fail(ST_ERR_ARG, "coarse_dof_cap must be in [1, " + std::to_string(kMaxCoarse) + "]");
     long long nn = d->n_t + 1;
@@ -359,7 +387,7 @@ st_status create_mesh(const st_mesh_desc* d, Mesh** out) {
         m->tacc.assign(m->lv.size() * 3, 0.0);
     }
     m->vt_first = -1;
-    if (m->vt_max_nodes > 0)
+    if (m->vt_max_nodes > 0 && !m->coarse_iter)
         for (int l = 0; l < (int)m->lv.size(); ++l)
             if (m->lv[l].g.nnodes <= m->vt_max_nodes && l < (int)m->lv.size() - 1) {
                 m->vt_first = l;
@@ -384,9 +412,22 @@ st_status create_mesh(const st_mesh_desc* d, Mesh** out) {
     A((void**)&m->d_bar, sizeof(unsigned) * 4);
     A((void**)&m->vt_part, sizeof(double) * 2 * kMaxBlocks * kRedQ);
     const long long nc = m->lv.back().g.nnodes;
-    A((void**)&m->Ainv, nc * nc * sizeof(double));
-    A((void**)&m->Awork, nc * nc * sizeof(double));
-    A((void**)&m->pinv, (nc + 1) * sizeof(double));
+    if (m->coarse_iter) {
+        const int cmax = m->desc.coarse_max_it > 0 ? m->desc.coarse_max_it : 200;
+        m->cg_m = std::min(kMaxSmooth, cmax);
+        m->cg_cycles = (cmax + m->cg_m - 1) / m->cg_m;
+        A((void**)&m->cg_b, nc * sizeof(double));
+        A((void**)&m->cg_x, nc * sizeof(double));
+        A((void**)&m->cg_dinv, nc * sizeof(double));
+        A((void**)&m->cg_w, nc * sizeof(double));
+        A((void**)&m->cg_w2, nc * sizeof(double));
+        for (int q = 0; q <= m->cg_m; ++q) A((void**)&m->cg_U.u[q], nc * sizeof(double));
+        A((void**)&m->d_smc, sizeof(SmState));
+    } else {
+        A((void**)&m->Ainv, nc * nc * sizeof(double));
+        A((void**)&m->Awork, nc * nc * sizeof(double));
+        A((void**)&m->pinv, (nc + 1) * sizeof(double));
+    }
     if (st == ST_OK && cudaMallocHost((void**)&m->h_fg, sizeof(FgState)) != cudaSuccess) {
         cudaGetLastError();
         st = fail(ST_ERR_OOM, "pinned host allocation failed");
@@ -396,6 +437,8 @@ st_status create_mesh(const st_mesh_desc* d, Mesh** out) {
         return st;
     }
     cudaMemsetAsync(m->rb.counter, 0, sizeof(unsigned) * 4, m->stream);
+    cudaMemsetAsync(m->d_sm, 0, sizeof(SmState), m->stream);
+    if (m->d_smc) cudaMemsetAsync(m->d_smc, 0, sizeof(SmState), m->stream);
     cudaMemsetAsync(m->s, 0, N * sizeof(double), m->stream);
     cudaMemsetAsync(m->lam, 0, N * sizeof(double), m->stream);
     cudaMemsetAsync(m->f, 0, N * sizeof(double), m->stream);
@@ -491,14 +534,17 @@ st_status set_design(Mesh* m, const double* gamma, int layout, size_t count, int
             launch_stencil_build(l, o0, oc, m->lv[l].st64, m->lv[l].st32, m->lv[l].sdir, s);
         }
     }
-    // coarsest operator, dense, and its inverse
-    const int nc = (int)m->lv[L - 1].g.nnodes;
-    launch_dense_assemble(m->sd, L - 1, m->op0<double>(), m->opc<double>(L - 1), m->Ainv, s);
-    CK(cudaMemsetAsync(m->d_err, 0, sizeof(int), s));
-    launch_gauss_jordan(m->Ainv, m->Awork, m->pinv, nc, m->d_err, s);
-    CK(cudaGetLastError());
+    // coarsest operator, dense, and its inverse (the iterative coarsest solve needs only its
+    // Jacobi diagonal, built with the multigrid workspace)
     int herr = 0;
-    CK(cudaMemcpyAsync(&herr, m->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (!m->coarse_iter) {
+        const int nc = (int)m->lv[L - 1].g.nnodes;
+        launch_dense_assemble(m->sd, L - 1, m->op0<double>(), m->opc<double>(L - 1), m->Ainv, s);
+        CK(cudaMemsetAsync(m->d_err, 0, sizeof(int), s));
+        launch_gauss_jordan(m->Ainv, m->Awork, m->pinv, nc, m->d_err, s);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(&herr, m->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    }
     CK(cudaStreamSynchronize(s));
     if (herr) return fail(ST_ERR_NUMERIC, "zero pivot in the coarsest-level inverse");
     m->design_version++;
@@ -552,6 +598,13 @@ st_status Mesh::ensure_mg(int steps) {
             for (int q = W.nbasis; q <= steps; ++q) CKS(alloc((void**)&W.U[l].u[q], N * sizeof(T)));
         }
         W.nbasis = steps + 1;
+    }
+    if (coarse_iter && cg_dinv_version != design_version) {
+        if (L == 1)
+            launch_diag_l0<double>(sd, op0<double>(), cg_dinv, true, stream);
+        else
+            launch_diag_lc<double>(sd, opc<double>(L - 1), cg_dinv, true, stream);
+        cg_dinv_version = design_version;
     }
     if (W.dinv_version != design_version) {
         for (int l = 0; l < L; ++l) {
@@ -618,11 +671,39 @@ st_status Mesh::upload_vtail(int steps) {
     return ST_OK;
 }
 
+// Coarsest level solved by FP64 right-Jacobi-preconditioned restarted GMRES(cg_m) to the
+// relative tolerance coarse_rtol (the paper's coarsest solve, Sec. 3.2): the smoother's
+// kernels, restarted cg_cycles times, with a stop test in its device state so that the
+// fixed launch sequence (graph capturable) does no work after convergence.
+template <typename T>
+void Mesh::coarse_gmres(bool tr) {
+    MGWork<T>& W = work<T>();
+    const int l = (int)lv.size() - 1;
+    const long long n = lv[l].g.nnodes;
+    if constexpr (std::is_same<T, double>::value)
+        cudaMemcpyAsync(cg_b, W.b[l], n * sizeof(double), cudaMemcpyDeviceToDevice, stream);
+    else
+        launch_convert<float, double>(W.b[l], cg_b, n, stream);
+    launch_cg_begin<double>(d_smc, desc.coarse_rtol > 0 ? desc.coarse_rtol : 1e-6, stream);
+    for (int c = 0; c < cg_cycles; ++c)
+        launch_smooth<double>(sd, l, op0<double>(), opc<double>(l), tr, cg_b, cg_x, cg_dinv, cg_U, cg_w, cg_w2, cg_m,
+                              c == 0, d_smc, rb, stream, nullptr);
+    if constexpr (std::is_same<T, double>::value)
+        cudaMemcpyAsync(W.x[l], cg_x, n * sizeof(double), cudaMemcpyDeviceToDevice, stream);
+    else
+        launch_convert<double, float>(cg_x, W.x[l], n, stream);
+}
+
 template <typename T>
 void Mesh::smooth(int l, bool tr, bool zero_init, int steps) {
     MGWork<T>& W = work<T>();
+    cudaEvent_t* ev = nullptr;
+    if (at_on && l == 0 && l < (int)lv.size() - 1) {
+        ev = at_ev + (zero_init ? 0 : 2 * kMaxSmooth);
+        at_steps = steps;
+    }
     launch_smooth<T>(sd, l, op0<T>(), opc<T>(l), tr, W.b[l], W.x[l], W.dinv[l], W.U[l], W.w[l], W.w2[l], steps,
-                     zero_init, d_sm, rb, stream);
+                     zero_init, d_sm, rb, stream, ev);
 }
 
 // One V-cycle on level l: pre-smoothing from zero, residual, restriction, coarse
@@ -632,7 +713,10 @@ void Mesh::vcycle_rec(int l, bool tr, int steps) {
     MGWork<T>& W = work<T>();
     const int L = (int)lv.size();
     if (l == L - 1) {
-        launch_coarse_solve<T>(Ainv, (int)lv[l].g.nnodes, tr, W.b[l], W.x[l], stream);
+        if (coarse_iter)
+            coarse_gmres<T>(tr);
+        else
+            launch_coarse_solve<T>(Ainv, (int)lv[l].g.nnodes, tr, W.b[l], W.x[l], stream);
         return;
     }
     const bool timing = level_timing && !capturing;
@@ -684,6 +768,7 @@ void Mesh::vcycle_rec(int l, bool tr, int steps) {
 template <typename T>
 st_status Mesh::vcycle(bool tr, int steps, bool graphs) {
     const int slot = (sizeof(T) == 4 ? 0 : 2) + (tr ? 1 : 0);
+    if (at_on && lv.size() > 1) at_pending = true;
     if (!graphs) {
         vcycle_rec<T>(0, tr, steps);
         return ST_OK;
@@ -768,6 +853,7 @@ st_status Mesh::fgmres(bool tr, const double* rhs, double* x, const st_options& 
     auto read_fg = [&]() -> st_status {
         CK(cudaMemcpyAsync(h_fg, d_fg, sizeof(FgState), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
+        timer_collect();
         return ST_OK;
     };
     launch_fg_residual(sd, A64, tr, rhs, x, V[0], d_fg, rb, s);
@@ -890,7 +976,9 @@ static st_status vcycle_entry(Mesh* mm, int transpose, const void* b, void* x) {
     CK(cudaMemcpyAsync(W.b[0], b, N * sizeof(T), cudaMemcpyDeviceToDevice, mm->stream));
     CKS(mm->vcycle<T>(transpose != 0, o.smooth_steps, false));
     CK(cudaMemcpyAsync(x, W.x[0], N * sizeof(T), cudaMemcpyDeviceToDevice, mm->stream));
-    return finish_sync(mm);
+    const st_status r = finish_sync(mm);
+    mm->timer_collect();
+    return r;
 }
 
 extern "C" {
@@ -1196,10 +1284,36 @@ st_status st_level_elements(st_mesh* m, int level, double* out, size_t count) {
     return finish(mm);
 }
 
+st_status st_apply_timer(st_mesh* m, int enable) {
+    if (!m) return fail(ST_ERR_ARG, "null argument");
+    Mesh* mm = M(m);
+    if (mm->device >= 0) cudaSetDevice(mm->device);
+    CK(cudaStreamSynchronize(mm->stream));
+    if (enable) {
+        for (cudaEvent_t& e : mm->at_ev)
+            if (!e) CK(cudaEventCreate(&e));
+        mm->at_ms = 0.0;
+        mm->at_launches = 0;
+    }
+    mm->at_pending = false;
+    if ((enable != 0) != mm->at_on) mm->drop_graphs();  // recapture with or without the event nodes
+    mm->at_on = enable != 0;
+    return ST_OK;
+}
+
+st_status st_apply_timer_read(st_mesh* m, double* total_ms, long long* launches) {
+    if (!m || !total_ms || !launches) return fail(ST_ERR_ARG, "null argument");
+    Mesh* mm = M(m);
+    *total_ms = mm->at_ms;
+    *launches = mm->at_launches;
+    return ST_OK;
+}
+
 st_status st_coarse_inverse(st_mesh* m, double* out, size_t count) {
     if (!m || !out) return fail(ST_ERR_ARG, "null argument");
     Mesh* mm = M(m);
     CKS(comp_check(mm, 0, ST_PREC_FP64));
+    if (mm->coarse_iter) return fail(ST_ERR_STATE, "the coarsest level is solved iteratively (no dense inverse)");
     const long long n = mm->lv.back().g.nnodes;
     if ((long long)count != n * n) return fail(ST_ERR_ARG, "count must be n*n of the coarsest level");
     CK(cudaMemcpyAsync(out, mm->Ainv, n * n * sizeof(double), cudaMemcpyDeviceToHost, mm->stream));

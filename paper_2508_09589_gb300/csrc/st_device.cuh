@@ -471,6 +471,12 @@ __device__ __forceinline__ void sm_start_finish(SmState* st_, double sum, int st
     const T beta = (T)sqrt(sum);
     st->beta = beta;
     st->stop = !(beta > T(0) && isfinite(beta));
+    if (st->rtol_rel > T(0)) {
+        if (st->atol < T(0))
+            st->atol = st->rtol_rel * beta;  // first start of a solve: beta = ||b||
+        else if (beta <= st->atol)
+            st->stop = 1;                    // converged: this and later cycles change nothing
+    }
     st->s[0] = st->stop ? T(0) : T(1) / beta;
     st->kdim = steps;
     st->g[0] = beta;
@@ -506,7 +512,8 @@ struct MarchGrid {
 inline __host__ MarchGrid march_grid(const Geom& g, dim3& grid, dim3& block) {
     block = dim3(32, 8, 1);
     const int gx = (g.nx1 + 31) / 32, gy = (g.ny1 + 7) / 8;
-    long long gz = (long long)kMaxBlocks / ((long long)gx * gy);
+    const long long budget = g.march_blocks > 0 && g.march_blocks < kMaxBlocks ? g.march_blocks : kMaxBlocks;
+    long long gz = budget / ((long long)gx * gy);
     if (gz < 1) gz = 1;
     if (gz > g.nt1) gz = g.nt1;
     const int chunk = (int)((g.nt1 + gz - 1) / gz);
@@ -518,38 +525,40 @@ inline __host__ MarchGrid march_grid(const Geom& g, dim3& grid, dim3& block) {
 template <typename T, typename LD, typename EMIT>
 __device__ __forceinline__ void march2d(const Geom& g, const T* __restrict__ coef, const unsigned char* __restrict__ dir,
                                         const LD& ld, int chunk, EMIT&& emit) {
-    // Each thread stages at most 2 of the 34 x 10 cells of a plane (tile + halo).  Planes are
-    // fetched 3 planes ahead into a register ring; loads use clamped (always valid) addresses
-    // and their validity is applied only when staged, so no instruction waits on a load
-    // before its plane is needed.  The plane loop is unrolled by 3 so that the prefetch ring
-    // and the 3-plane neighbourhood window rotate by register renaming.
-    __shared__ T tile_[2][10][34];
+    // A 32 x 8 tile of spatial nodes marches up the time axis over the rows [n0, n1).  Plane
+    // m (tile + 1-node halo, 34 x 10 cells, at most 2 cells per thread) is staged once in
+    // shared memory; each thread reads its 9-point neighbourhood of the plane and adds it to
+    // the three rows it touches: the lower-plane part of row m + 1, the own-plane part of row
+    // m and the upper-plane part of row m - 1, which is then complete and written.  Rows keep
+    // the summation order (lower + own) + upper of a row-by-row evaluation.  Plane loads are
+    // issued 3 planes ahead into a register ring; the loop is unrolled by 3 so that the ring
+    // slot, the shared buffer and the three row accumulators rotate by register renaming.
+    __shared__ T tile_[3][10 * 34];
     using R = typename LD::R;
     constexpr int NR = LD::NR;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
     const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 8;
     const int i = i0 + tx, jj = j0 + ty;
+    const int nt = g.net;
     const int n0 = blockIdx.z * chunk;
-    const int n1 = min(n0 + chunk, g.nt1);
+    const int n1 = min(n0 + chunk, nt + 1);
+    const int ms = n0 > 0 ? n0 - 1 : 0;  // planes [ms, me] feed rows [n0, n1)
+    const int me = n1 <= nt ? n1 : nt;
     const long long P = (long long)g.nx1 * g.ny1;
     const bool in = i < g.nx1 && jj < g.ny1;
     const long long p = in ? (long long)jj * g.nx1 + i : 0;
-    const int nt = g.net;
     long long cell_off[2];
     bool cell_ok[2], cell_st[2];
-    int cell_sy[2], cell_sx[2];
+    int cell_sm[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         const int cidx = tid + r * 256;
         cell_off[r] = 0;
         cell_ok[r] = false;
         cell_st[r] = cidx < 340;
-        cell_sy[r] = 0;
-        cell_sx[r] = 0;
+        cell_sm[r] = cidx < 340 ? cidx : 0;
         if (cidx < 340) {
             const int cy = cidx / 34, cx = cidx - cy * 34;
-            cell_sy[r] = cy;
-            cell_sx[r] = cx;
             const int gi = i0 - 1 + cx, gj = j0 - 1 + cy;
             if (gi >= 0 && gi < g.nx1 && gj >= 0 && gj < g.ny1) {
                 cell_off[r] = (long long)gj * g.nx1 + gi;
@@ -557,84 +566,80 @@ __device__ __forceinline__ void march2d(const Geom& g, const T* __restrict__ coe
             }
         }
     }
+    const int rd = ty * 34 + tx;  // top-left of this thread's 3 x 3 neighbourhood
     T c[27];
 #pragma unroll
     for (int q = 0; q < 27; ++q) c[q] = in ? coef[(long long)(27 + q) * P + p] : T(0);
     const bool dirp = in ? (dir[p] != 0) : true;
 
-    auto fetch = [&](int n, R (&v)[2][NR], bool& ok) {
-        ok = n >= 0 && n <= nt;
-        const long long base = (long long)(n < 0 ? 0 : (n > nt ? nt : n)) * P;
+    auto fetch = [&](int m, R (&v)[2][NR]) {
+        if (m <= me) {
+            const long long base = (long long)m * P;
 #pragma unroll
-        for (int r = 0; r < 2; ++r) ld.raw(base + cell_off[r], v[r]);
+            for (int r = 0; r < 2; ++r) ld.raw(base + cell_off[r], v[r]);
+        }
     };
-    int buf = 0;
-    auto stage_read = [&](const R (&v)[2][NR], bool ok, T (&dst)[9]) {
+    // plane m: stage, refill the ring slot with plane m + 3, read the neighbourhood, add the
+    // three row parts, write row m - 1 (and row n_t after the last plane)
+    auto step = [&](int m, R (&slot)[2][NR], T* buf, T& a_prev, T& a_cur, T& a_next, T& c_prev, T& c_cur) {
 #pragma unroll
         for (int r = 0; r < 2; ++r)
-            if (cell_st[r]) tile_[buf][cell_sy[r]][cell_sx[r]] = (ok && cell_ok[r]) ? LD::combine(v[r]) : T(0);
+            if (cell_st[r]) buf[cell_sm[r]] = cell_ok[r] ? LD::combine(slot[r]) : T(0);
+        fetch(m + 3, slot);
         __syncthreads();
+        T v[9];
 #pragma unroll
         for (int dj = 0; dj < 3; ++dj)
 #pragma unroll
-            for (int di = 0; di < 3; ++di) dst[dj * 3 + di] = tile_[buf][ty + dj][tx + di];
-        buf ^= 1;
-    };
-    auto row = [&](int n, const T (&xa)[9], const T (&xb)[9], const T (&xc)[9]) {
-        if (!in) return;
-        T y;
-        if (n == 0 || dirp) {
-            y = xb[4];
-        } else {
-            const int cls = (n == 1) ? (nt == 1 ? 3 : 0) : (n == nt ? 2 : 1);
-            T a0 = 0, a1 = 0, a2 = 0;
-            if (cls == 1) {
+            for (int di = 0; di < 3; ++di) v[dj * 3 + di] = buf[rd + dj * 34 + di];
+        c_cur = v[4];
+        if (m >= 3 && m + 2 <= nt) {  // rows m - 1, m, m + 1 are all interior
+            T s0 = 0, s1 = 0, s2 = 0;
 #pragma unroll
-                for (int k = 0; k < 9; ++k) {
-                    a0 += c[k] * xa[k];
-                    a1 += c[9 + k] * xb[k];
-                    a2 += c[18 + k] * xc[k];
-                }
-            } else {
-                const T* cc = coef + (long long)cls * 27 * P + p;
-#pragma unroll
-                for (int k = 0; k < 9; ++k) {
-                    a0 += cc[(long long)k * P] * xa[k];
-                    a1 += cc[(long long)(9 + k) * P] * xb[k];
-                    a2 += cc[(long long)(18 + k) * P] * xc[k];
-                }
+            for (int k = 0; k < 9; ++k) {
+                s0 += c[k] * v[k];
+                s1 += c[9 + k] * v[k];
+                s2 += c[18 + k] * v[k];
             }
-            y = a0 + a1 + a2;
+            a_next = s0;
+            a_cur += s1;
+            a_prev += s2;
+        } else {
+#pragma unroll
+            for (int part = 0; part < 3; ++part) {
+                const int r = m + 1 - part;  // row receiving this part
+                T sum = 0;
+                if (r >= 1 && r <= nt) {
+                    const int cl = (r == 1) ? (nt == 1 ? 3 : 0) : (r == nt ? 2 : 1);
+                    if (cl == 1) {
+#pragma unroll
+                        for (int k = 0; k < 9; ++k) sum += c[part * 9 + k] * v[k];
+                    } else {
+                        const T* cc = coef + (long long)(cl * 27 + part * 9) * P + p;
+#pragma unroll
+                        for (int k = 0; k < 9; ++k) sum += cc[(long long)k * P] * v[k];
+                    }
+                }
+                if (part == 0)
+                    a_next = sum;
+                else if (part == 1)
+                    a_cur += sum;
+                else
+                    a_prev += sum;
+            }
         }
-        emit((long long)n * P + p, y);
+        if (in && m - 1 >= n0 && m - 1 < n1) emit((long long)(m - 1) * P + p, (m - 1 == 0 || dirp) ? c_prev : a_prev);
+        if (in && m == nt && nt >= n0 && nt < n1) emit((long long)nt * P + p, dirp ? c_cur : a_cur);
     };
-    // prologue: planes n0-1 and n0 into the window, planes n0+1..n0+3 into the ring
-    T x0[9], x1[9], x2[9];
-    R p0[2][NR], p1[2][NR], p2[2][NR];
-    bool k0, k1, k2;
-    fetch(n0 - 1, p0, k0);
-    fetch(n0, p1, k1);
-    stage_read(p0, k0, x0);
-    stage_read(p1, k1, x1);
-    fetch(n0 + 1, p0, k0);
-    fetch(n0 + 2, p1, k1);
-    fetch(n0 + 3, p2, k2);
-    // step(n): window (a, b) = planes n-1, n; ring slot s holds plane n+1 -> stage it into c,
-    // refill s with plane n+4, emit row n.
-    for (int n = n0; n < n1; n += 3) {
-        stage_read(p0, k0, x2);
-        fetch(n + 4, p0, k0);
-        row(n, x0, x1, x2);
-        if (n + 1 < n1) {
-            stage_read(p1, k1, x0);
-            fetch(n + 5, p1, k1);
-            row(n + 1, x1, x2, x0);
-        }
-        if (n + 2 < n1) {
-            stage_read(p2, k2, x1);
-            fetch(n + 6, p2, k2);
-            row(n + 2, x2, x0, x1);
-        }
+    R s0[2][NR], s1[2][NR], s2[2][NR];
+    fetch(ms, s0);
+    fetch(ms + 1, s1);
+    fetch(ms + 2, s2);
+    T A = 0, B = 0, Cc = 0, E0 = 0, E1 = 0, E2 = 0;
+    for (int m = ms; m <= me; m += 3) {
+        step(m, s0, tile_[0], A, B, Cc, E0, E1);
+        if (m + 1 <= me) step(m + 1, s1, tile_[1], B, Cc, A, E1, E2);
+        if (m + 2 <= me) step(m + 2, s2, tile_[2], Cc, A, B, E2, E0);
     }
 }
 
@@ -703,7 +708,8 @@ __device__ inline void sm_update_finish(SmState* st_, double sum, int j, int ste
     st->H[(j + 1) * kMaxSmooth + j] = h;
     sm_givens_column_t<T>(st, j);
     const T tol = sizeof(T) == 4 ? T(1e-6) : T(1e-13);  // breakdown relative to the initial residual
-    const bool brk = !(h > tol * st->beta) || !isfinite(h);
+    const bool conv = st->rtol_rel > T(0) && fabs(st->g[j + 1]) <= st->atol;
+    const bool brk = !(h > tol * st->beta) || !isfinite(h) || conv;
     if (brk)
         st->kdim = j + 1;
     else

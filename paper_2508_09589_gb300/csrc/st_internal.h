@@ -37,6 +37,7 @@ struct Geom {
     int bc;                        // ST_BC_*
     int face;                      // patch face axis (0: x = 0, 1: y = 0)
     int plo[3], phi[3];            // patch node range per spatial axis (inclusive)
+    int march_blocks;              // thread-block budget of the time-marching kernels (<= 0: kMaxBlocks)
 };
 
 // Modified SIMP parameters (C = C_ins + dC g^p_c, k = k_ins + dk g^p_k).
@@ -86,6 +87,11 @@ struct SmStateT {
     T beta;
     int kdim;
     int stop;
+    // Restarted use as a solver (the coarsest-level Jacobi-GMRES): rtol_rel > 0 stops the
+    // Arnoldi process once the residual estimate reaches atol = rtol_rel ||b|| (atol < 0:
+    // taken from the next start) and skips every later restart cycle.  0 for the smoother.
+    T rtol_rel;
+    T atol;
 };
 
 struct alignas(16) SmState {
@@ -165,7 +171,7 @@ void launch_prolong(const Geom& gf, const Geom& gc, int kind, int sd, const T* x
 template <typename T>
 void launch_smooth(int sd, int lvl, const OpL0<T>& o0, const OpLc<T>& oc, bool tr, const T* b, T* x,
                    const T* dinv, Basis<T> U, T* w, T* w2, int steps, bool zero_init, SmState* st, RedBuf rb,
-                   cudaStream_t s);
+                   cudaStream_t s, cudaEvent_t* apply_ev = nullptr);
 // Fused FP32 Arnoldi step j -> j+1 on a stencil level (k_arnoldi.cu).
 void launch_arnoldi(const Geom& g, const float* coef, const unsigned char* dir, const float* dinv,
                     const Ptrs<float>& U, const float* w_in, float* w_out, int j, SmState* st, RedBuf rb,
@@ -217,6 +223,12 @@ void launch_build_from_l0(int sd, const OpL0<double>& f0, const Geom& gc, int ki
 void launch_build_from_lc(int sd, const OpLc<double>& fc, const Geom& gc, int kind, double* elem_c,
                           cudaStream_t s);
 void launch_to_float(const double* in, float* out, long long n, cudaStream_t s);
+// Coarsest-level Jacobi-GMRES (k_stream.cu): set the relative tolerance of the solver state,
+// and convert the level vectors between the V-cycle precision and FP64.
+template <typename T>
+void launch_cg_begin(SmState* st, double rtol, cudaStream_t s);
+template <typename TI, typename TO>
+void launch_convert(const TI* in, TO* out, long long n, cudaStream_t s);
 void launch_dense_assemble(int sd, int lvl, const OpL0<double>& o0, const OpLc<double>& oc, double* A,
                            cudaStream_t s);
 void launch_gauss_jordan(double* A, double* B, double* pinv, int n, int* err, cudaStream_t s);  // result in A

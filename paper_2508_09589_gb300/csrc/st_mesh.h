@@ -56,7 +56,21 @@ struct Mesh {
     double* gsens = nullptr;
     bool have_design = false, have_state = false, have_adjoint = false;
 
-    // coarsest inverse
+    // coarsest level: dense inverse, or the iterative Jacobi-GMRES solve (coarse_iter) with
+    // its FP64 vectors, restart length cg_m and cycle count
+    bool coarse_iter = false;
+    int cg_m = 16;
+    int cg_cycles = 0;
+    double* cg_b = nullptr;
+    double* cg_x = nullptr;
+    double* cg_dinv = nullptr;
+    double* cg_w = nullptr;
+    double* cg_w2 = nullptr;
+    Basis<double> cg_U{};
+    SmState* d_smc = nullptr;
+    long long cg_dinv_version = -1;
+    template <typename T>
+    void coarse_gmres(bool tr);
     double* Ainv = nullptr;
     double* Awork = nullptr;
     double* pinv = nullptr;
@@ -98,6 +112,17 @@ struct Mesh {
     std::vector<double> tacc;      // [level][phase]: pre-smooth, down-transfer, post-smooth+prolong
     int tcycles = 0;
     bool capturing = false;
+
+    // opt-in CUDA-event timing of every level-0 smoother operator apply (st_apply_timer):
+    // event pairs [sweep][step] recorded around the launches (event nodes inside captured
+    // V-cycles) and read after the host synchronisation that follows each V-cycle
+    bool at_on = false;
+    bool at_pending = false;
+    int at_steps = 0;
+    cudaEvent_t at_ev[4 * kMaxSmooth] = {};
+    double at_ms = 0.0;
+    long long at_launches = 0;
+    void timer_collect();
 
     std::vector<void*> allocs;
     std::vector<size_t> alloc_sizes;

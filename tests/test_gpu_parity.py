@@ -279,6 +279,27 @@ def test_graphs_and_eager_identical():
     np.testing.assert_array_equal(a, b)
 
 
+@pytest.mark.parametrize("i", [0, 3])
+def test_apply_timer_counts_level0_applies_and_changes_nothing(i):
+    """The event timer records every level-0 smoother apply (2 sweeps x 10 steps per outer
+    iteration, graphs and eager) and leaves the solution bit for bit unchanged."""
+    om, g = _case(i)
+    gm = gpu_mesh(om, coarse_dof_cap=300)
+    gm.set_design(g)
+    for graphs in (True, False):
+        gm.solve_forward(rtol=1e-9, use_graphs=graphs)
+        a = gm.state("T")
+        gm.apply_timer(True)
+        st = gm.solve_forward(rtol=1e-9, use_graphs=graphs)
+        ms, n = gm.apply_timer_read()
+        gm.apply_timer(False)
+        np.testing.assert_array_equal(gm.state("T"), a)
+        assert n == 2 * 10 * st["outer_its"]
+        assert ms > 0
+        phi, sa = gm.solve_adjoint()
+        assert gm.apply_timer_read() == (ms, n)  # stopped: totals kept, nothing added
+
+
 @pytest.mark.parametrize("i", [0, 1, 3])
 def test_persistent_tail_matches_launch_per_phase(i, monkeypatch):
     """The V-cycle run as one persistent cooperative kernel (small levels) and as one launch
@@ -297,3 +318,95 @@ def test_persistent_tail_matches_launch_per_phase(i, monkeypatch):
         st = gm.solve_forward(rtol=1e-10, precision="mixed")
         assert st["converged"]
     assert rel_err(out[1], out[0]) < 1e-11
+
+
+@pytest.mark.parametrize("i", [1, 2])
+@pytest.mark.parametrize("blocks", [1, 12, 18, 30])
+def test_march_kernels_with_long_and_ragged_time_chunks(i, blocks):
+    """The time-marching stencil kernels with thread-block budgets that give each block the
+    whole time axis or chunks of 9, 6 or 4 planes with a ragged last chunk: operator,
+    smoother and full forward / adjoint solves against the oracle."""
+    om, g = _case(i)
+    gm = gpu_mesh(om, coarse_dof_cap=300, march_blocks=blocks)
+    gm.set_design(g)
+    A = O.assemble(om, g)
+    x = np.random.default_rng(11).standard_normal(om.n_nodes)
+    for tr in (False, True):
+        At = A.T.tocsr() if tr else A
+        y = torch.empty(om.n_nodes, dtype=torch.float64, device="cuda")
+        gm.apply(0, _dev(x), y, "fp64", tr)
+        assert rel_err(y.cpu().numpy(), At @ x) < 1e-13
+        y32 = torch.empty(om.n_nodes, dtype=torch.float32, device="cuda")
+        gm.apply(0, _dev(x, torch.float32), y32, "mixed", tr)
+        assert rel_err(y32.cpu().numpy(), At @ x.astype(np.float32).astype(np.float64)) < 1e-4
+        b = x * (~O.dirichlet_mask(om))
+        ref = O.gmres_jacobi(At, b, np.zeros_like(b), 10)
+        xs = torch.zeros(om.n_nodes, dtype=torch.float64, device="cuda")
+        gm.smooth(0, _dev(b), xs, 10, True, "fp64", tr)
+        assert rel_err(xs.cpu().numpy(), ref) < 1e-9
+    sol = O.forward(om, g, "uniform", 1.0)
+    lam = O.adjoint(sol.A, sol.f, O.dirichlet_mask(om), sol.lu)
+    for precision in ("fp64", "mixed"):
+        st = gm.solve_forward(rtol=parity_rtol(sol.A, sol.s, sol.f), precision=precision, max_it=400)
+        assert st["converged"]
+        assert rel_err(gm.state("T"), sol.s) < (1e-10 if precision == "fp64" else 1e-6)
+        gm.solve_adjoint("compliance", rtol=parity_rtol(sol.A.T, lam, sol.f), precision=precision, max_it=400)
+        assert rel_err(gm.state("lambda"), lam) < (1e-10 if precision == "fp64" else 1e-6)
+
+
+def test_coarse_gmres_single_level_reaches_its_tolerance():
+    """One-level hierarchy: the V-cycle is the coarsest Jacobi-GMRES solve alone; its output
+    meets the requested relative residual (and converges to the exact solve when tight)."""
+    om = O.Mesh((10, 6), 4, mat=MATS["unitcap"], bc="patch_bottom", bc_width=0.3)
+    g = np.random.default_rng(12).random((6, 10))
+    A = O.assemble(om, g)
+    b = np.random.default_rng(12).standard_normal(om.n_nodes)
+    b[O.dirichlet_mask(om)] = 0
+    exact = O.solve_direct(A, b)
+    for rtol, it in ((1e-6, 400), (1e-12, 2000)):
+        gm = gpu_mesh(om, max_levels=1, coarse_solver="gmres", coarse_rtol=rtol, coarse_max_it=it)
+        gm.set_design(g)
+        assert len(gm.levels()) == 1
+        x = torch.empty(om.n_nodes, dtype=torch.float64, device="cuda")
+        gm.vcycle(_dev(b), x, "fp64", False)
+        xh = x.cpu().numpy()
+        assert np.linalg.norm(b - A @ xh) <= 1.5 * rtol * np.linalg.norm(b)
+        if rtol < 1e-9:
+            assert rel_err(xh, exact) < 1e-8
+        with pytest.raises(Exception):
+            gm.coarse_inverse()
+
+
+@pytest.mark.parametrize("i", [0, 1, 3])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_coarse_gmres_solver_forward_adjoint(i, precision):
+    """The paper's coarsest solve (Jacobi-GMRES to 1e-6) inside the V-cycle: FGMRES reaches
+    the same solution and adjoint as with the dense coarsest inverse."""
+    om, g = _case(i)
+    sol = O.forward(om, g, "uniform", 1.0)
+    lam = O.adjoint(sol.A, sol.f, O.dirichlet_mask(om), sol.lu)
+    gm = gpu_mesh(om, coarse_dof_cap=300, coarse_solver="gmres")
+    gm.set_design(g)
+    st = gm.solve_forward(rtol=parity_rtol(sol.A, sol.s, sol.f), precision=precision, max_it=400)
+    assert st["converged"]
+    tol = 1e-10 if precision == "fp64" else 1e-6
+    assert rel_err(gm.state("T"), sol.s) < tol
+    gm.solve_adjoint("compliance", rtol=parity_rtol(sol.A.T, lam, sol.f), precision=precision, max_it=400)
+    assert rel_err(gm.state("lambda"), lam) < tol
+
+
+def test_coarse_solver_switches_to_gmres_above_the_dense_cap():
+    """Odd element counts stop Algorithm 1 at once: the 46 x 46 x 18-node level cannot use
+    the dense inverse (more than 4096 nodes), so the default picks Jacobi-GMRES."""
+    om = O.Mesh((45, 45), 17, mat=MATS["unitcap"], bc="patch_left", bc_width=0.1)
+    g = np.random.default_rng(13).random((45, 45))
+    sol = O.forward(om, g, "uniform", 1.0)
+    gm = gpu_mesh(om)
+    assert len(gm.levels()) == 1 and om.n_nodes > 4096
+    gm.set_design(g)
+    for precision in ("fp64", "mixed"):
+        st = gm.solve_forward(rtol=parity_rtol(sol.A, sol.s, sol.f), precision=precision, max_it=400)
+        assert st["converged"]
+        assert rel_err(gm.state("T"), sol.s) < (1e-10 if precision == "fp64" else 1e-6)
+    with pytest.raises(Exception):
+        gpu_mesh(om, coarse_solver="dense")
