@@ -314,17 +314,21 @@ def serving_bench(args):
 def kernel_roofline(N, n_st_elems, apply_ms, apply_n, args):
     """Dominant kernel: the level-0 smoother operator apply w = A D^-1 u_j (20 launches per
     V-cycle), its launches timed with CUDA events on the mesh stream inside the timed steps.
-    Algorithmic bytes per launch: u_j and D^-1 read, w written (12 B per node in FP32), plus
-    the BF16 density (2 B per space-time element) on space-time designs; the per-spatial-node
-    stencils of time-constant designs are O(n_x n_y) and stay in L2."""
+    Algorithmic bytes per launch: on stencil levels (time-constant 2-D designs) u_j read and w
+    written (8 B per node in FP32; the Jacobi scaling is folded into the stencil, whose
+    O(n_x n_y) coefficients stay in L2); on element-block levels u_j and D^-1 read and w
+    written (12 B per node) plus the BF16 density (2 B per space-time element)."""
     peak, kind = _peaks()
     tsz = 4 if args.precision == "mixed" else 8
-    byts = 3.0 * tsz * N + (2.0 * n_st_elems if args.precision == "mixed" else 8.0 * n_st_elems)
+    if n_st_elems == 0:  # stencil level: u_j in, w out (Jacobi scaling folded into the stencil)
+        byts = 2.0 * tsz * N
+    else:                # element-block level 0: u_j and D^-1 in, w out, plus the density
+        byts = 3.0 * tsz * N + (2.0 * n_st_elems if args.precision == "mixed" else 8.0 * n_st_elems)
     if apply_n <= 0:
         return {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None, "traffic": None}
     t = apply_ms / 1e3 / apply_n
     ach = byts / t / 1e9
-    name = "km_sm_applyw" if n_st_elems == 0 else "k_sm_applyw"
+    name = "km_sm_applyw_sc" if n_st_elems == 0 else "k_sm_applyw"
     return {"kernel": f"{name} level 0 ({'FP32' if tsz == 4 else 'FP64'} smoother operator apply)",
             "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
             "traffic": TRAFFIC_PER_LAUNCH.get((name, args.workload, args.precision)),
@@ -334,7 +338,34 @@ def kernel_roofline(N, n_st_elems, apply_ms, apply_n, args):
 
 # DRAM read + write bytes of one launch, from an ncu capture of the current kernel version
 # (profiles/ names the capture); None when no capture of this version exists.
-TRAFFIC_PER_LAUNCH = {}
+TRAFFIC_PER_LAUNCH = {
+    # profiles/km_sm_applyw_sc_level0_c1_256x256x256.md: 98.04 MB read + 35.61 MB written
+    ("km_sm_applyw_sc", "c1_256x256x256_grf_extruded", "mixed"): 133647872,
+}
+
+
+def run_vcycles(args):
+    """Kernel-profiling mode: design set-up and K mixed-precision V-cycles on the workload
+    (no Krylov solve, so only the multigrid storage is resident: a few GB at 256^2 x 256)."""
+    import torch
+    from paper_2508_09589_gb300 import Mesh
+    w = W.WORKLOADS[args.workload]
+    mesh = Mesh(w.ns, w.nt, material=w.material, bc=w.bc, bc_width=w.bc_width, tau=w.tau)
+    mesh.set_design(W.make_design(w).reshape(-1), "extruded" if w.extruded else "spacetime")
+    N = mesh.n_nodes
+    g = torch.Generator(device="cuda").manual_seed(5)
+    b = torch.randn(N, dtype=torch.float32, device="cuda", generator=g)
+    x = torch.empty_like(b)
+    mesh.vcycle(b, x, "mixed")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.vcycles):
+        mesh.vcycle(b, x, "mixed")
+    torch.cuda.synchronize()
+    t = (time.perf_counter() - t0) / max(1, args.vcycles)
+    print(json.dumps({"mode": "vcycles", "workload": w.name, "vcycles": args.vcycles, "ms_per_vcycle": 1e3 * t,
+                      "device_gb": mesh.device_bytes / 1e9, "finite": bool(torch.isfinite(x).all())}), flush=True)
+    mesh.close()
 
 
 # ---------------------------------------------------------------------------- oracle (CPU) arm

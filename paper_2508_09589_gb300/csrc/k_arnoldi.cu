@@ -16,19 +16,6 @@
 
 namespace st {
 
-template <typename T>
-__device__ __forceinline__ void cp_async4(T* smem_dst, const T* gsrc, bool valid) {
-    static_assert(sizeof(T) == 4, "4-byte elements");
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-    const int sz = valid ? 4 : 0;  // 0 bytes read -> zero fill
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gsrc), "r"(sz) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
 constexpr int kArnPF = 2;  // planes in flight
 
 // Dynamic shared memory layout (floats): raw[kArnPF][NQ + 1][2][256] (slot 0: w_j,

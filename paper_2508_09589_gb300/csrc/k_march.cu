@@ -62,6 +62,43 @@ __global__ void k_stencil_build(OpL0<double> o0, OpLc<double> oc, double* __rest
         }
 }
 
+// Interior rows of a stencil level apply A D^-1 with D^-1 of interior planes, which is the
+// same on every interior plane: fold it into the interior-class stencil of both orientations.
+// Rows of prescribed spatial nodes become the identity row scaled by their own D^-1.
+template <typename T>
+__global__ void k_stencil_scale(Geom g, const T* __restrict__ st, const T* __restrict__ dinv,
+                                const unsigned char* __restrict__ dir, int nref, T* __restrict__ sc) {
+    const long long P = (long long)g.nx1 * g.ny1;
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const int i = (int)(p % g.nx1), j = (int)(p / g.nx1);
+    const bool pres = dir[p] != 0;
+    for (int o = 0; o < 2; ++o)
+        for (int k = 0; k < 27; ++k) {
+            const int dj = (k % 9) / 3, di = k % 3;
+            const int ii = i + di - 1, jn = j + dj - 1;
+            const bool ok = ii >= 0 && ii < g.nx1 && jn >= 0 && jn < g.ny1;
+            const T c = st[((long long)(o * 4 + 1) * 27 + k) * P + p];
+            const T d = ok ? dinv[(long long)nref * P + (long long)jn * g.nx1 + ii] : T(0);
+            T v = c * d;
+            if (pres) v = k == 13 ? dinv[(long long)nref * P + p] : T(0);
+            sc[((long long)o * 27 + k) * P + p] = v;
+        }
+}
+
+template <typename T>
+void launch_stencil_scale(const Geom& g, const T* st, const T* dinv, const unsigned char* dir, T* sc,
+                          cudaStream_t s) {
+    note_launch(s);
+    const long long P = (long long)g.nx1 * g.ny1;
+    const int nref = g.net < 2 ? g.net : 2;
+    k_stencil_scale<T><<<(int)((P + 127) / 128), 128, 0, s>>>(g, st, dinv, dir, nref, sc);
+}
+template void launch_stencil_scale<float>(const Geom&, const float*, const float*, const unsigned char*, float*,
+                                          cudaStream_t);
+template void launch_stencil_scale<double>(const Geom&, const double*, const double*, const unsigned char*, double*,
+                                           cudaStream_t);
+
 void launch_stencil_build(int lvl, const OpL0<double>& o0, const OpLc<double>& oc, double* st64, float* st32,
                           unsigned char* dir, cudaStream_t s) {
     note_launch(s);

@@ -489,6 +489,17 @@ __global__ void __launch_bounds__(256) km_sm_applyw(Geom g, const T* __restrict_
     march2d<T>(g, coef, dir, ld, chunk, [&](long long q, T v) { w[q] = v; });
 }
 
+// The same with the interior Jacobi scaling folded into the stencil (reads u_j only).
+template <typename T>
+__global__ void __launch_bounds__(256) km_sm_applyw_sc(Geom g, const T* __restrict__ sc, const T* __restrict__ coef,
+                                                       const unsigned char* __restrict__ dir, int chunk,
+                                                       const T* __restrict__ dinv, const T* __restrict__ uj,
+                                                       T* __restrict__ w, int j, const SmState* st) {
+    if (smt<T>(st)->stop || j >= smt<T>(st)->kdim) return;
+    constexpr int PF = sizeof(T) == 4 ? 8 : 4;  // planes in flight per block
+    march2d_scaled<T, PF>(g, sc, coef, dir, uj, dinv, chunk, [&](long long q, T v) { w[q] = v; });
+}
+
 template <int SD, typename T, int LV, bool TR>
 __global__ void __launch_bounds__(256) k_sm_applyw(OpL0<T> o0, OpLc<T> oc, const T* __restrict__ dinv,
                                                    const T* __restrict__ uj, T* __restrict__ w, int j,
@@ -647,7 +658,7 @@ constexpr long long kSplitNodes = 0;
 template <int SD, typename T, int LV, bool TR>
 static void smooth_impl(const OpL0<T>& o0, const OpLc<T>& oc, const T* b, T* x, const T* dinv, Basis<T> U, T* w,
                         T* w2, int steps, bool zero_init, SmState* st, RedBuf rb, cudaStream_t s,
-                        cudaEvent_t* ev) {
+                        cudaEvent_t* ev, const T* sc) {
     const Geom& g = LV == 0 ? o0.g : oc.g;
     const long long N = g.nnodes;
     const LaunchCfg c = node_cfg(g);
@@ -699,7 +710,10 @@ static void smooth_impl(const OpL0<T>& o0, const OpLc<T>& oc, const T* b, T* x, 
         if (split) {
             // optional timing events around the operator apply (event nodes when captured)
             if (ev) record_timing_event(ev[2 * j], s);
-            if (march)
+            if (march && sc)
+                km_sm_applyw_sc<T><<<mgrid, mblock, 0, s>>>(g, sc + (TR ? 27 * g.plane : 0), coef, dir, mg.chunk,
+                                                           dinv, U.u[j], w, j, st);
+            else if (march)
                 km_sm_applyw<T><<<mgrid, mblock, 0, s>>>(g, coef, dir, mg.chunk, dinv, U.u[j], w, j, st);
             else
                 k_sm_applyw<SD, T, LV, TR><<<c.grid, c.block, 0, s>>>(o0, oc, dinv, U.u[j], w, j, st);
@@ -718,13 +732,13 @@ static void smooth_impl(const OpL0<T>& o0, const OpLc<T>& oc, const T* b, T* x, 
 template <typename T>
 void launch_smooth(int sd, int lvl, const OpL0<T>& o0, const OpLc<T>& oc, bool tr, const T* b, T* x, const T* dinv,
                    Basis<T> U, T* w, T* w2, int steps, bool zero_init, SmState* st, RedBuf rb, cudaStream_t s,
-                   cudaEvent_t* ev) {
+                   cudaEvent_t* ev, const T* sc) {
     if (lvl == 0) {
-        ST_SD_DISPATCH(sd, if (tr) smooth_impl<SD, T, 0, true>(o0, oc, b, x, dinv, U, w, w2, steps, zero_init, st, rb, s, ev);
-                       else smooth_impl<SD, T, 0, false>(o0, oc, b, x, dinv, U, w, w2, steps, zero_init, st, rb, s, ev));
+        ST_SD_DISPATCH(sd, if (tr) smooth_impl<SD, T, 0, true>(o0, oc, b, x, dinv, U, w, w2, steps, zero_init, st, rb, s, ev, sc);
+                       else smooth_impl<SD, T, 0, false>(o0, oc, b, x, dinv, U, w, w2, steps, zero_init, st, rb, s, ev, sc));
     } else {
-        ST_SD_DISPATCH(sd, if (tr) smooth_impl<SD, T, 1, true>(o0, oc, b, x, dinv, U, w, w2, steps, zero_init, st, rb, s, ev);
-                       else smooth_impl<SD, T, 1, false>(o0, oc, b, x, dinv, U, w, w2, steps, zero_init, st, rb, s, ev));
+        ST_SD_DISPATCH(sd, if (tr) smooth_impl<SD, T, 1, true>(o0, oc, b, x, dinv, U, w, w2, steps, zero_init, st, rb, s, ev, sc);
+                       else smooth_impl<SD, T, 1, false>(o0, oc, b, x, dinv, U, w, w2, steps, zero_init, st, rb, s, ev, sc));
     }
 }
 
@@ -823,7 +837,7 @@ void launch_mask_copy(int sd, const Geom& g, const double* src, double* dst, cud
     template void launch_restrict<T>(const Geom&, const Geom&, int, int, const T*, T*, cudaStream_t);               \
     template void launch_prolong<T>(const Geom&, const Geom&, int, int, const T*, T*, cudaStream_t);                \
     template void launch_smooth<T>(int, int, const OpL0<T>&, const OpLc<T>&, bool, const T*, T*, const T*, Basis<T>, \
-                                   T*, T*, int, bool, SmState*, RedBuf, cudaStream_t, cudaEvent_t*);                \
+                                   T*, T*, int, bool, SmState*, RedBuf, cudaStream_t, cudaEvent_t*, const T*);      \
     template void launch_coarse_solve<T>(const double*, int, bool, const T*, T*, cudaStream_t);                     \
     template void launch_fg_apply_dots<T>(int, const OpL0<double>&, bool, const T*, T*, double*, double* const*,    \
                                           int, FgState*, RedBuf, cudaStream_t);                                      \

@@ -613,6 +613,15 @@ st_status Mesh::ensure_mg(int steps) {
             else
                 launch_diag_lc<T>(sd, opc<T>(l), W.dinv[l], true, stream);
         }
+        // stencil levels that smooth: interior stencils scaled by the Jacobi diagonal
+        W.sc.resize(L, nullptr);
+        for (int l = 0; l + 1 < L; ++l) {
+            if (!lv[l].sdir) continue;
+            const long long P = (long long)lv[l].g.nx1 * lv[l].g.ny1;
+            if (!W.sc[l]) CKS(alloc((void**)&W.sc[l], 2 * 27 * P * sizeof(T)));
+            const T* stl = std::is_same<T, float>::value ? (const T*)lv[l].st32 : (const T*)lv[l].st64;
+            launch_stencil_scale<T>(lv[l].g, stl, W.dinv[l], lv[l].sdir, W.sc[l], stream);
+        }
         W.dinv_version = design_version;
     }
     if (vt_first >= 0 && (W.vt_version != ws_version || W.steps_uploaded != steps)) CKS(upload_vtail<T>(steps));
@@ -702,8 +711,9 @@ void Mesh::smooth(int l, bool tr, bool zero_init, int steps) {
         ev = at_ev + (zero_init ? 0 : 2 * kMaxSmooth);
         at_steps = steps;
     }
+    const T* sc = (l < (int)W.sc.size() && lv[l].sdir) ? W.sc[l] : nullptr;
     launch_smooth<T>(sd, l, op0<T>(), opc<T>(l), tr, W.b[l], W.x[l], W.dinv[l], W.U[l], W.w[l], W.w2[l], steps,
-                     zero_init, d_sm, rb, stream, ev);
+                     zero_init, d_sm, rb, stream, ev, sc);
 }
 
 // One V-cycle on level l: pre-smoothing from zero, residual, restriction, coarse

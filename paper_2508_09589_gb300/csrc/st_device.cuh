@@ -505,6 +505,29 @@ __device__ __forceinline__ void fg_residual_finish(FgState* fs, double sum) {
 // Coefficients are stored [class][27][P] (structure of arrays over spatial nodes p) with
 // class 0: n = 1 < n_t, 1: interior, 2: n = n_t >= 2, 3: n_t == 1; prescribed rows (t = 0
 // plane, spatial sink flagged in dir) are the identity.
+// Asynchronous global -> shared copies of single elements (cp.async, 4 or 8 bytes); an
+// invalid source copies nothing and zero-fills the destination.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem_dst, const T* gsrc, bool valid) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    const int sz = valid ? (int)sizeof(T) : 0;
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gsrc), "r"(sz) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gsrc), "r"(sz) : "memory");
+}
+template <typename T>
+__device__ __forceinline__ void cp_async4(T* smem_dst, const T* gsrc, bool valid) {
+    static_assert(sizeof(T) == 4, "4-byte elements");
+    cp_async_elem<T>(smem_dst, gsrc, valid);
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 struct MarchGrid {
     int chunk;  // planes per block
 };
@@ -641,6 +664,156 @@ __device__ __forceinline__ void march2d(const Geom& g, const T* __restrict__ coe
         if (m + 1 <= me) step(m + 1, s1, tile_[1], B, Cc, A, E1, E2);
         if (m + 2 <= me) step(m + 2, s2, tile_[2], Cc, A, B, E2, E0);
     }
+}
+
+
+// Smoother operator apply w = A D^-1 u on a stencil level.  The rows of interior planes read
+// only interior-plane neighbours, whose Jacobi scaling is time invariant, so it is folded
+// into the interior-class stencil once per design (sc[k][p] = c_k(p) d(q_k); prescribed
+// spatial nodes get the identity row d(p) at the own-plane centre).  Interior rows then need
+// the raw u alone, which is staged plane by plane into a ring of PF + 1 shared buffers by
+// cp.async, PF planes ahead, without passing through registers.  Planes whose three rows
+// are all interior and inside this block's range take a lean path (no class, range or
+// boundary tests); the others use the unscaled class stencils, the scaled neighbours u d
+// and the identity rows explicitly.  Rows are accumulated as in march2d.
+template <typename T, int PF, typename EMIT>
+__device__ __forceinline__ void march2d_scaled(const Geom& g, const T* __restrict__ sc, const T* __restrict__ coef,
+                                               const unsigned char* __restrict__ dir, const T* __restrict__ u,
+                                               const T* __restrict__ dinv, int chunk, EMIT&& emit) {
+    constexpr int NB = PF + 1;
+    __shared__ __align__(16) T tile_[NB * 340];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 8;
+    const int i = i0 + tx, jj = j0 + ty;
+    const int nt = g.net;
+    const int n0 = blockIdx.z * chunk;
+    const int n1 = min(n0 + chunk, nt + 1);
+    const int ms = n0 > 0 ? n0 - 1 : 0;
+    const int me = n1 <= nt ? n1 : nt;
+    // lean planes: rows m - 1, m, m + 1 interior and row m - 1 (written here) in range with all
+    // three of its parts (planes m - 2 .. m) taken from the scaled interior stencil
+    const int ml = max(n0 + 1, 5), mh = min(me, nt - 2);
+    const long long P = (long long)g.nx1 * g.ny1;
+    const bool in = i < g.nx1 && jj < g.ny1;
+    const long long p = in ? (long long)jj * g.nx1 + i : 0;
+    const T* src[2];
+    bool cell_ok[2], cell_st[2];
+    int cell_sm[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int cidx = tid + r * 256;
+        src[r] = u;
+        cell_ok[r] = false;
+        cell_st[r] = cidx < 340;
+        cell_sm[r] = cidx < 340 ? cidx : 0;
+        if (cidx < 340) {
+            const int cy = cidx / 34, cx = cidx - cy * 34;
+            const int gi = i0 - 1 + cx, gj = j0 - 1 + cy;
+            if (gi >= 0 && gi < g.nx1 && gj >= 0 && gj < g.ny1) {
+                src[r] = u + (long long)gj * g.nx1 + gi;
+                cell_ok[r] = true;
+            }
+        }
+    }
+    const int rd = ty * 34 + tx;
+    T c[27];
+#pragma unroll
+    for (int q = 0; q < 27; ++q) c[q] = in ? sc[(long long)q * P + p] : T(0);
+    const bool dirp = in ? (dir[p] != 0) : true;
+    // copies of plane m into its ring buffer; every call commits one group (possibly empty)
+    auto issue = [&](int m) {
+        if (m <= me) {
+            T* buf = tile_ + ((m - ms) % NB) * 340;
+            const long long off = (long long)m * P;
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+                if (cell_st[r]) cp_async_elem<T>(buf + cell_sm[r], src[r] + off, cell_ok[r]);
+        }
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int q = 0; q < PF; ++q) issue(ms + q);
+    auto step = [&](int m, T& a_prev, T& a_cur, T& a_next, T& c_prev, T& c_cur) {
+        cp_async_wait<PF - 1>();  // this thread's copies of plane m have landed
+        __syncthreads();          // everyone's have; plane m - 1's buffer is free again
+        const T* buf = tile_ + ((m - ms) % NB) * 340;
+        T v[9];
+#pragma unroll
+        for (int dj = 0; dj < 3; ++dj)
+#pragma unroll
+            for (int di = 0; di < 3; ++di) v[dj * 3 + di] = buf[rd + dj * 34 + di];
+        issue(m + PF);
+        c_cur = v[4];
+        if (m >= ml && m <= mh) {
+            T s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                s0 += c[k] * v[k];
+                s1 += c[9 + k] * v[k];
+                s2 += c[18 + k] * v[k];
+            }
+            a_next = s0;
+            a_cur += s1;
+            a_prev += s2;
+            if (in) emit((long long)(m - 1) * P + p, a_prev);
+            return;
+        }
+        const bool fast = m >= 3 && m + 2 <= nt;
+        if (fast) {
+            T s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                s0 += c[k] * v[k];
+                s1 += c[9 + k] * v[k];
+                s2 += c[18 + k] * v[k];
+            }
+            a_next = s0;
+            a_cur += s1;
+            a_prev += s2;
+        } else {
+            const T* dm = dinv + (long long)m * P;
+#pragma unroll
+            for (int dj = 0; dj < 3; ++dj)
+#pragma unroll
+                for (int di = 0; di < 3; ++di) {
+                    const int ii = i + di - 1, jn = jj + dj - 1;
+                    const bool ok = in && ii >= 0 && ii < g.nx1 && jn >= 0 && jn < g.ny1;
+                    v[dj * 3 + di] *= ok ? dm[(long long)jn * g.nx1 + ii] : T(0);
+                }
+#pragma unroll
+            for (int part = 0; part < 3; ++part) {
+                const int r = m + 1 - part;
+                T sum = 0;
+                if (r >= 1 && r <= nt) {
+                    const int cl = (r == 1) ? (nt == 1 ? 3 : 0) : (r == nt ? 2 : 1);
+                    const T* cc = coef + (long long)(cl * 27 + part * 9) * P + p;
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) sum += cc[(long long)k * P] * v[k];
+                }
+                if (part == 0)
+                    a_next = sum;
+                else if (part == 1)
+                    a_cur += sum;
+                else
+                    a_prev += sum;
+            }
+        }
+        if (in && m - 1 >= n0 && m - 1 < n1) {
+            const long long q = (long long)(m - 1) * P + p;
+            emit(q, (m - 1 == 0 || dirp) ? c_prev * dinv[q] : a_prev);
+        }
+        if (in && m == nt && nt >= n0 && nt < n1) {
+            const long long q = (long long)nt * P + p;
+            emit(q, dirp ? c_cur * dinv[q] : a_cur);
+        }
+    };
+    T A = 0, B = 0, Cc = 0, E0 = 0, E1 = 0, E2 = 0;
+    for (int m = ms; m <= me; m += 3) {
+        step(m, A, B, Cc, E0, E1);
+        if (m + 1 <= me) step(m + 1, B, Cc, A, E1, E2);
+        if (m + 2 <= me) step(m + 2, Cc, A, B, E2, E0);
+    }
+    cp_async_wait<0>();
 }
 
 }  // namespace st

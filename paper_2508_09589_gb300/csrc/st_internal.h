@@ -171,7 +171,13 @@ void launch_prolong(const Geom& gf, const Geom& gc, int kind, int sd, const T* x
 template <typename T>
 void launch_smooth(int sd, int lvl, const OpL0<T>& o0, const OpLc<T>& oc, bool tr, const T* b, T* x,
                    const T* dinv, Basis<T> U, T* w, T* w2, int steps, bool zero_init, SmState* st, RedBuf rb,
-                   cudaStream_t s, cudaEvent_t* apply_ev = nullptr);
+                   cudaStream_t s, cudaEvent_t* apply_ev = nullptr, const T* scaled_stencil = nullptr);
+// Interior-class stencils of a stencil level with the Jacobi scaling of the neighbour folded
+// in: sc[o][k][p] = st[o][1][k][p] dinv(n_ref, q_k(p)), identity rows d(p) at prescribed
+// spatial nodes (k_march.cu).
+template <typename T>
+void launch_stencil_scale(const Geom& g, const T* st, const T* dinv, const unsigned char* dir, T* sc,
+                          cudaStream_t s);
 // Fused FP32 Arnoldi step j -> j+1 on a stencil level (k_arnoldi.cu).
 void launch_arnoldi(const Geom& g, const float* coef, const unsigned char* dir, const float* dinv,
                     const Ptrs<float>& U, const float* w_in, float* w_out, int j, SmState* st, RedBuf rb,

@@ -33,6 +33,7 @@ struct MGWork {
     int nbasis = 0;
     long long dinv_version = -1;
     std::vector<T*> b, x, r, w, w2, dinv;
+    std::vector<T*> sc;            // stencil levels: interior stencils with the Jacobi scaling folded in
     std::vector<Basis<T>> U;
 };
 
