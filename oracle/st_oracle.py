@@ -320,6 +320,40 @@ def assemble_source(m: Mesh, Q: Callable, nq: int = 2, constrained: bool = True)
     return f
 
 
+def source_rows(m: Mesh, Q: Callable, rows: np.ndarray, nq: int = 2) -> np.ndarray:
+    """f_i of assemble_source for the listed nodes only, element by element (for meshes too
+    large to assemble): the sum over the elements containing node i of the nq-point Gauss
+    integral of N_i Q; prescribed nodes are 0."""
+    sd = m.sd
+    shape = m.node_shape
+    dm = dirichlet_mask(m)
+    gp, gw = gauss_1d(nq)
+    sizes = list(m.h) + [m.dt]
+    out = np.zeros(len(rows))
+    for r, node in enumerate(np.asarray(rows)):
+        if dm[node]:
+            continue
+        idx = np.unravel_index(node, shape)  # (t, [z], y, x)
+        acc = 0.0
+        for e_off in itertools.product((0, 1), repeat=sd + 1):
+            e = tuple(i - 1 + o for i, o in zip(idx, e_off))
+            if any(v < 0 or v >= n for v, n in zip(e, m.elem_shape)):
+                continue
+            loc = [i - v for i, v in zip(idx, e)]  # local coordinate bits, (t, [z], y, x)
+            for q in itertools.product(range(nq), repeat=sd + 1):  # q[d]: axis d of (x, y, [z], t)
+                wq = np.prod([gw[qi] * sizes[d] for d, qi in enumerate(q)])
+                t = (e[0] + gp[q[sd]]) * m.dt
+                xs = [(e[len(shape) - 1 - d] + gp[q[d]]) * m.h[d] for d in range(sd)]
+                Na = 1.0
+                for d in range(sd):
+                    bit = loc[len(shape) - 1 - d]
+                    Na *= (1.0 - gp[q[d]]) if bit == 0 else gp[q[d]]
+                Na *= (1.0 - gp[q[sd]]) if loc[0] == 0 else gp[q[sd]]
+                acc += wq * Na * float(Q(np.array(t), *reversed([np.array(v) for v in xs])))
+        out[r] = acc
+    return out
+
+
 # ----------------------------------------------------------------------------
 # Direct solves (the plain definition of what the FGMRES + multigrid solve reaches)
 # ----------------------------------------------------------------------------

@@ -547,3 +547,14 @@ def test_apply_rows_matches_assembled_operator():
         x = rng.random(m.n_nodes)
         rows = np.arange(m.n_nodes)
         np.testing.assert_allclose(O.apply_rows(m, g, x, rows), A @ x, rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("ns,nt,kind", [((5, 4), 6, "sin_t"), ((3, 2, 4), 3, "uniform")])
+def test_source_rows_match_assembled_source(ns, nt, kind):
+    """The row-by-row source (used where the mesh is too large to assemble) equals the
+    assembled source vector on every node."""
+    m = O.Mesh(ns, nt, bc="patch_left", bc_width=0.5)
+    Q = O.source_fn(kind, 1.0, 1.0, 0.5, 4.0)
+    f = O.assemble_source(m, Q)
+    rows = np.arange(m.n_nodes)
+    np.testing.assert_allclose(O.source_rows(m, Q, rows), f, rtol=1e-13, atol=1e-16)
