@@ -115,10 +115,12 @@ def test_fullsize_solves_residual_duality_and_directional_derivative(name):
     assert abs(float(f @ s) - float(lam @ f)) <= 1e-6 * abs(phi)
     np.testing.assert_allclose(phi, float(f @ s), rtol=1e-12)
     # directional derivative along v = gamma (1 - gamma) (smooth, zero at the bounds) by
-    # central differences of tightly solved compliances, against g^T v
-    tight = dict(rtol=1e-12, max_it=400)
-    gm.solve_forward(**tight, **src)
-    gm.solve_adjoint("compliance", **tight)
+    # central differences of tightly solved compliances, against g^T v.  At these sizes the
+    # FP64 residual floor is near 1e-12, so the solves aim at 1e-11 and must reach 1e-10:
+    # with h = 1e-4 the compliance changes by about 1e-5 relative, far above that noise.
+    tight = dict(rtol=1e-11, max_it=300, allow_not_converged=True)
+    assert gm.solve_forward(**tight, **src)["rel_res"] < 1e-10
+    assert gm.solve_adjoint("compliance", **tight)[1]["rel_res"] < 1e-10
     grad = gm.sensitivities()
     v = (g * (1.0 - g)).reshape(-1)
     gv = float(grad @ v)
@@ -126,7 +128,7 @@ def test_fullsize_solves_residual_duality_and_directional_derivative(name):
     phis = []
     for sgn in (1.0, -1.0):
         gm.set_design((g.reshape(-1) + sgn * h * v), layout)
-        gm.solve_forward(**tight, **src)
+        assert gm.solve_forward(**tight, **src)["rel_res"] < 1e-10
         fs = gm.state("rhs")
         phis.append(float(fs @ gm.state("T")))
     fd = (phis[0] - phis[1]) / (2 * h)
