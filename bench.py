@@ -339,8 +339,8 @@ def kernel_roofline(N, n_st_elems, apply_ms, apply_n, args):
 # DRAM read + write bytes of one launch, from an ncu capture of the current kernel version
 # (profiles/ names the capture); None when no capture of this version exists.
 TRAFFIC_PER_LAUNCH = {
-    # profiles/km_sm_applyw_sc_level0_c1_256x256x256.md: 98.04 MB read + 35.61 MB written
-    ("km_sm_applyw_sc", "c1_256x256x256_grf_extruded", "mixed"): 133647872,
+    # profiles/km_sm_applyw_sc_level0_c1_256x256x256.md: 99.22 MB read + 31.94 MB written
+    ("km_sm_applyw_sc", "c1_256x256x256_grf_extruded", "mixed"): 131153664,
 }
 
 

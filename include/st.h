@@ -93,7 +93,8 @@ typedef struct {
     int coarse_max_it;       /* Jacobi-GMRES iterations on the coarsest level (0: 200) */
     double coarse_rtol;      /* its relative residual target (0: 1e-6) */
     int march_blocks;        /* tuning: thread-block budget of the time-marching stencil kernels
-                                (0: 4096); a smaller budget gives each block a longer time chunk */
+                                (0: 912, two waves on 152 SMs; at most 4096); a smaller budget
+                                gives each block a longer time chunk */
 } st_mesh_desc;
 
 typedef struct {

@@ -532,10 +532,16 @@ struct MarchGrid {
     int chunk;  // planes per block
 };
 
+// Default thread-block budget of the time-marching kernels: about two waves of 3 resident
+// 256-thread blocks on each of 152 SMs, so that every block marches a long time chunk and
+// its set-up (coefficients, halo cells, staging prologue) is amortised (measured on the
+// 256^2 x 256 fine level: 912 blocks beat 1824 and 4096).
+constexpr long long kMarchBlocks = 2 * 3 * 152;
+
 inline __host__ MarchGrid march_grid(const Geom& g, dim3& grid, dim3& block) {
     block = dim3(32, 8, 1);
     const int gx = (g.nx1 + 31) / 32, gy = (g.ny1 + 7) / 8;
-    const long long budget = g.march_blocks > 0 && g.march_blocks < kMaxBlocks ? g.march_blocks : kMaxBlocks;
+    const long long budget = g.march_blocks > 0 && g.march_blocks < kMaxBlocks ? g.march_blocks : kMarchBlocks;
     long long gz = budget / ((long long)gx * gy);
     if (gz < 1) gz = 1;
     if (gz > g.nt1) gz = g.nt1;
@@ -681,6 +687,7 @@ __device__ __forceinline__ void march2d_scaled(const Geom& g, const T* __restric
                                                const unsigned char* __restrict__ dir, const T* __restrict__ u,
                                                const T* __restrict__ dinv, int chunk, EMIT&& emit) {
     constexpr int NB = PF + 1;
+    static_assert((NB & (NB - 1)) == 0, "ring length must be a power of two");
     __shared__ __align__(16) T tile_[NB * 340];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
     const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 8;
@@ -720,23 +727,28 @@ __device__ __forceinline__ void march2d_scaled(const Geom& g, const T* __restric
 #pragma unroll
     for (int q = 0; q < 27; ++q) c[q] = in ? sc[(long long)q * P + p] : T(0);
     const bool dirp = in ? (dir[p] != 0) : true;
-    // copies of plane m into its ring buffer; every call commits one group (possibly empty)
+    // copies of plane m into its ring buffer; every call commits one group (possibly empty).
+    // Planes are issued in order, so the cell sources advance by one plane per call.
+#pragma unroll
+    for (int r = 0; r < 2; ++r) src[r] += (long long)ms * P;
     auto issue = [&](int m) {
         if (m <= me) {
-            T* buf = tile_ + ((m - ms) % NB) * 340;
-            const long long off = (long long)m * P;
+            T* buf = tile_ + ((m - ms) & (NB - 1)) * 340;
 #pragma unroll
             for (int r = 0; r < 2; ++r)
-                if (cell_st[r]) cp_async_elem<T>(buf + cell_sm[r], src[r] + off, cell_ok[r]);
+                if (cell_st[r]) cp_async_elem<T>(buf + cell_sm[r], src[r], cell_ok[r]);
         }
+#pragma unroll
+        for (int r = 0; r < 2; ++r) src[r] += P;
         cp_async_commit();
     };
 #pragma unroll
     for (int q = 0; q < PF; ++q) issue(ms + q);
+    long long qrow = (long long)(ms - 1) * P + p;  // node index of row m - 1 at step m
     auto step = [&](int m, T& a_prev, T& a_cur, T& a_next, T& c_prev, T& c_cur) {
         cp_async_wait<PF - 1>();  // this thread's copies of plane m have landed
         __syncthreads();          // everyone's have; plane m - 1's buffer is free again
-        const T* buf = tile_ + ((m - ms) % NB) * 340;
+        const T* buf = tile_ + ((m - ms) & (NB - 1)) * 340;
         T v[9];
 #pragma unroll
         for (int dj = 0; dj < 3; ++dj)
@@ -755,7 +767,8 @@ __device__ __forceinline__ void march2d_scaled(const Geom& g, const T* __restric
             a_next = s0;
             a_cur += s1;
             a_prev += s2;
-            if (in) emit((long long)(m - 1) * P + p, a_prev);
+            if (in) emit(qrow, a_prev);
+            qrow += P;
             return;
         }
         const bool fast = m >= 3 && m + 2 <= nt;
@@ -798,14 +811,9 @@ __device__ __forceinline__ void march2d_scaled(const Geom& g, const T* __restric
                     a_prev += sum;
             }
         }
-        if (in && m - 1 >= n0 && m - 1 < n1) {
-            const long long q = (long long)(m - 1) * P + p;
-            emit(q, (m - 1 == 0 || dirp) ? c_prev * dinv[q] : a_prev);
-        }
-        if (in && m == nt && nt >= n0 && nt < n1) {
-            const long long q = (long long)nt * P + p;
-            emit(q, dirp ? c_cur * dinv[q] : a_cur);
-        }
+        if (in && m - 1 >= n0 && m - 1 < n1) emit(qrow, (m - 1 == 0 || dirp) ? c_prev * dinv[qrow] : a_prev);
+        if (in && m == nt && nt >= n0 && nt < n1) emit(qrow + P, dirp ? c_cur * dinv[qrow + P] : a_cur);
+        qrow += P;
     };
     T A = 0, B = 0, Cc = 0, E0 = 0, E1 = 0, E2 = 0;
     for (int m = ms; m <= me; m += 3) {
