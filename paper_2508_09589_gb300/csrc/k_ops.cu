@@ -496,7 +496,7 @@ __global__ void __launch_bounds__(256) km_sm_applyw_sc(Geom g, const T* __restri
                                                        const T* __restrict__ dinv, const T* __restrict__ uj,
                                                        T* __restrict__ w, int j, const SmState* st) {
     if (smt<T>(st)->stop || j >= smt<T>(st)->kdim) return;
-    constexpr int PF = sizeof(T) == 4 ? 7 : 3;  // planes in flight per block (ring of PF + 1)
+    constexpr int PF = sizeof(T) == 4 ? 13 : 5;  // planes in flight per block (ring of PF + 3)
     march2d_scaled<T, PF>(g, sc, coef, dir, uj, dinv, chunk, [&](long long q, T v) { w[q] = v; });
 }
 

@@ -532,6 +532,34 @@ struct MarchGrid {
     int chunk;  // planes per block
 };
 
+// Sum of c[k] v[k] over the 9 points of one plane.  FP32 pairs the terms for the packed
+// two-lane FMA of sm_100+ (fma.rn.f32x2): ((c0 v0 + c2 v2 + c4 v4 + c6 v6) + (c1 v1 + ... +
+// c7 v7)) + c8 v8, four instructions instead of eight; FP64 sums in order.
+__device__ __forceinline__ void ffma2(float& d0, float& d1, float a0, float a1, float b0, float b1) {
+    asm("{\n\t.reg .b64 pa, pb, pd;\n\t"
+        "mov.b64 pa, {%2, %3};\n\t"
+        "mov.b64 pb, {%4, %5};\n\t"
+        "mov.b64 pd, {%0, %1};\n\t"
+        "fma.rn.f32x2 pd, pa, pb, pd;\n\t"
+        "mov.b64 {%0, %1}, pd;\n\t}"
+        : "+f"(d0), "+f"(d1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+template <typename T>
+__device__ __forceinline__ T dot9(const T* c, const T (&v)[9]) {
+    if constexpr (std::is_same<T, float>::value) {
+        float e = 0.f, o = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; k += 2) ffma2(e, o, c[k], c[k + 1], v[k], v[k + 1]);
+        return (e + o) + c[8] * v[8];
+    } else {
+        T s = 0;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) s += c[k] * v[k];
+        return s;
+    }
+}
+
 // Default thread-block budget of the time-marching kernels: about two waves of 3 resident
 // 256-thread blocks on each of 152 SMs, so that every block marches a long time chunk and
 // its set-up (coefficients, halo cells, staging prologue) is amortised (measured on the
@@ -686,7 +714,7 @@ template <typename T, int PF, typename EMIT>
 __device__ __forceinline__ void march2d_scaled(const Geom& g, const T* __restrict__ sc, const T* __restrict__ coef,
                                                const unsigned char* __restrict__ dir, const T* __restrict__ u,
                                                const T* __restrict__ dinv, int chunk, EMIT&& emit) {
-    constexpr int NB = PF + 1;
+    constexpr int NB = PF + 3;
     static_assert((NB & (NB - 1)) == 0, "ring length must be a power of two");
     __shared__ __align__(16) T tile_[NB * 340];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
@@ -757,16 +785,9 @@ __device__ __forceinline__ void march2d_scaled(const Geom& g, const T* __restric
         issue(m + PF);
         c_cur = v[4];
         if (m >= ml && m <= mh) {
-            T s0 = 0, s1 = 0, s2 = 0;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                s0 += c[k] * v[k];
-                s1 += c[9 + k] * v[k];
-                s2 += c[18 + k] * v[k];
-            }
-            a_next = s0;
-            a_cur += s1;
-            a_prev += s2;
+            a_next = dot9(c, v);
+            a_cur += dot9(c + 9, v);
+            a_prev += dot9(c + 18, v);
             if (in) emit(qrow, a_prev);
             qrow += P;
             return;
@@ -815,8 +836,35 @@ __device__ __forceinline__ void march2d_scaled(const Geom& g, const T* __restric
         if (in && m == nt && nt >= n0 && nt < n1) emit(qrow + P, dirp ? c_cur * dinv[qrow + P] : a_cur);
         qrow += P;
     };
+    // three lean planes behind one wait and one barrier: the copies issued afterwards go to
+    // the buffers of planes m - 3 .. m - 1 (ring of PF + 3), which every thread has finished
+    auto lean_one = [&](int m, T& a_prev, T& a_cur, T& a_next, T& c_cur) {
+        const T* buf = tile_ + ((m - ms) & (NB - 1)) * 340;
+        T v[9];
+#pragma unroll
+        for (int dj = 0; dj < 3; ++dj)
+#pragma unroll
+            for (int di = 0; di < 3; ++di) v[dj * 3 + di] = buf[rd + dj * 34 + di];
+        c_cur = v[4];
+        a_next = dot9(c, v);
+        a_cur += dot9(c + 9, v);
+        a_prev += dot9(c + 18, v);
+        if (in) emit(qrow, a_prev);
+        qrow += P;
+    };
     T A = 0, B = 0, Cc = 0, E0 = 0, E1 = 0, E2 = 0;
     for (int m = ms; m <= me; m += 3) {
+        if (m >= ml && m + 2 <= mh) {
+            cp_async_wait<PF - 3>();
+            __syncthreads();
+            lean_one(m, A, B, Cc, E1);
+            lean_one(m + 1, B, Cc, A, E2);
+            lean_one(m + 2, Cc, A, B, E0);
+            issue(m + PF);
+            issue(m + PF + 1);
+            issue(m + PF + 2);
+            continue;
+        }
         step(m, A, B, Cc, E0, E1);
         if (m + 1 <= me) step(m + 1, B, Cc, A, E1, E2);
         if (m + 2 <= me) step(m + 2, Cc, A, B, E2, E0);
