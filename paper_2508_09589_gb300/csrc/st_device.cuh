@@ -545,6 +545,15 @@ __device__ __forceinline__ void ffma2(float& d0, float& d1, float a0, float a1, 
         : "+f"(d0), "+f"(d1)
         : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
 }
+// The same with operands already held as register pairs: cp[i] = (c_{2i}, c_{2i+1}),
+// vp[i] = (v_{2i}, v_{2i+1}) for i < 4, and the ninth term apart.
+__device__ __forceinline__ float dot9p(const float2 (&cp)[4], float c8, const float2 (&vp)[4], float v8) {
+    float e = 0.f, o = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) ffma2(e, o, cp[k].x, cp[k].y, vp[k].x, vp[k].y);
+    return (e + o) + c8 * v8;
+}
+
 template <typename T>
 __device__ __forceinline__ T dot9(const T* c, const T (&v)[9]) {
     if constexpr (std::is_same<T, float>::value) {
@@ -838,17 +847,44 @@ __device__ __forceinline__ void march2d_scaled(const Geom& g, const T* __restric
     };
     // three lean planes behind one wait and one barrier: the copies issued afterwards go to
     // the buffers of planes m - 3 .. m - 1 (ring of PF + 3), which every thread has finished
+    // FP32: the interior stencil again as register pairs for the packed FMA
+    float2 cp[3][4];
+    float c8[3];
+    if constexpr (std::is_same<T, float>::value) {
+#pragma unroll
+        for (int part = 0; part < 3; ++part) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) cp[part][k] = make_float2(c[part * 9 + 2 * k], c[part * 9 + 2 * k + 1]);
+            c8[part] = c[part * 9 + 8];
+        }
+    }
     auto lean_one = [&](int m, T& a_prev, T& a_cur, T& a_next, T& c_cur) {
         const T* buf = tile_ + ((m - ms) & (NB - 1)) * 340;
-        T v[9];
+        if constexpr (std::is_same<T, float>::value) {
+            float2 vp[4];
+            float v8;
 #pragma unroll
-        for (int dj = 0; dj < 3; ++dj)
+            for (int k = 0; k < 4; ++k) {
+                const int k0 = 2 * k, k1 = 2 * k + 1;
+                vp[k].x = buf[rd + (k0 / 3) * 34 + k0 % 3];
+                vp[k].y = buf[rd + (k1 / 3) * 34 + k1 % 3];
+            }
+            v8 = buf[rd + 2 * 34 + 2];
+            c_cur = vp[2].x;  // k = 4: the centre
+            a_next = dot9p(cp[0], c8[0], vp, v8);
+            a_cur += dot9p(cp[1], c8[1], vp, v8);
+            a_prev += dot9p(cp[2], c8[2], vp, v8);
+        } else {
+            T v[9];
 #pragma unroll
-            for (int di = 0; di < 3; ++di) v[dj * 3 + di] = buf[rd + dj * 34 + di];
-        c_cur = v[4];
-        a_next = dot9(c, v);
-        a_cur += dot9(c + 9, v);
-        a_prev += dot9(c + 18, v);
+            for (int dj = 0; dj < 3; ++dj)
+#pragma unroll
+                for (int di = 0; di < 3; ++di) v[dj * 3 + di] = buf[rd + dj * 34 + di];
+            c_cur = v[4];
+            a_next = dot9(c, v);
+            a_cur += dot9(c + 9, v);
+            a_prev += dot9(c + 18, v);
+        }
         if (in) emit(qrow, a_prev);
         qrow += P;
     };
