@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(256) km_arnoldi(Geom g, const float* __restric
                                                   const float* __restrict__ dinv, Ptrs<float> U,
                                                   const float* __restrict__ w_in, float* __restrict__ w_out, int j,
                                                   SmState* st_, RedBuf rb) {
+    pdl_enter();
     const SmStateT<float>* st = smt<float>((const SmState*)st_);
     if (st->stop || j >= st->kdim) return;
     extern __shared__ float sm[];
@@ -242,7 +243,7 @@ static void launch_arnoldi_nq(const Geom& g, const float* coef, const unsigned c
         cudaFuncSetAttribute(km_arnoldi<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         attr = true;
     }
-    km_arnoldi<NQ><<<grid, block, bytes, s>>>(g, coef, dir, mg.chunk, dinv, U, w_in, w_out, j, st, rb);
+    launch_pdl(km_arnoldi<NQ>, grid, block, bytes, s, g, coef, dir, mg.chunk, dinv, U, w_in, w_out, j, st, rb);
 }
 
 // One fused Arnoldi step j -> j+1 (requires j + 2 <= 16).

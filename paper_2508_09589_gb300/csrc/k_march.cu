@@ -15,6 +15,7 @@ namespace st {
 template <int LV>
 __global__ void k_stencil_build(OpL0<double> o0, OpLc<double> oc, double* __restrict__ out64,
                                 float* __restrict__ out32, unsigned char* __restrict__ dir) {
+    pdl_enter();
     constexpr int NS = 4, NSYM = 10, NV = 40;
     const Geom& g = LV == 0 ? o0.g : oc.g;
     const long long P = (long long)g.nx1 * g.ny1;
@@ -68,6 +69,7 @@ __global__ void k_stencil_build(OpL0<double> o0, OpLc<double> oc, double* __rest
 template <typename T>
 __global__ void k_stencil_scale(Geom g, const T* __restrict__ st, const T* __restrict__ dinv,
                                 const unsigned char* __restrict__ dir, int nref, T* __restrict__ sc) {
+    pdl_enter();
     const long long P = (long long)g.nx1 * g.ny1;
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= P) return;
@@ -92,7 +94,7 @@ void launch_stencil_scale(const Geom& g, const T* st, const T* dinv, const unsig
     note_launch(s);
     const long long P = (long long)g.nx1 * g.ny1;
     const int nref = g.net < 2 ? g.net : 2;
-    k_stencil_scale<T><<<(int)((P + 127) / 128), 128, 0, s>>>(g, st, dinv, dir, nref, sc);
+    launch_pdl(k_stencil_scale<T>, (int)((P + 127) / 128), 128, 0, s, g, st, dinv, dir, nref, sc);
 }
 template void launch_stencil_scale<float>(const Geom&, const float*, const float*, const unsigned char*, float*,
                                           cudaStream_t);
@@ -106,9 +108,9 @@ void launch_stencil_build(int lvl, const OpL0<double>& o0, const OpLc<double>& o
     const long long P = (long long)g.nx1 * g.ny1;
     const int blocks = (int)((P + 127) / 128);
     if (lvl == 0)
-        k_stencil_build<0><<<blocks, 128, 0, s>>>(o0, oc, st64, st32, dir);
+        launch_pdl(k_stencil_build<0>, blocks, 128, 0, s, o0, oc, st64, st32, dir);
     else
-        k_stencil_build<1><<<blocks, 128, 0, s>>>(o0, oc, st64, st32, dir);
+        launch_pdl(k_stencil_build<1>, blocks, 128, 0, s, o0, oc, st64, st32, dir);
 }
 
 }  // namespace st

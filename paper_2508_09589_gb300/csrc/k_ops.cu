@@ -2,6 +2,7 @@
 // transfers, the Jacobi-GMRES smoother, the coarsest solve and the FP64 flexible
 // GMRES kernels (arXiv 2508.09589, Sec. 3.2).
 #include <math.h>
+#include <stdlib.h>
 
 #include <atomic>
 
@@ -10,6 +11,10 @@
 namespace st {
 
 static std::atomic<long long> g_launches{0};
+bool g_pdl = [] {
+    const char* e = getenv("ST_PDL");
+    return !(e && atoi(e) == 0);
+}();
 
 void note_launch(cudaStream_t s, long long n) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -36,6 +41,7 @@ LaunchCfg node_cfg(const Geom& g) {
 // ---------------------------------------------------------------- applies
 template <int SD, typename T, int LV, bool TR>
 __global__ void __launch_bounds__(256) k_apply(OpL0<T> o0, OpLc<T> oc, const T* __restrict__ x, T* __restrict__ y) {
+    pdl_enter();
     const Geom& g = LV == 0 ? o0.g : oc.g;
     LoadPlain<T, T> ld{x};
     ST_NODE_LOOP_BEGIN(g)
@@ -50,6 +56,7 @@ __global__ void __launch_bounds__(256) k_apply(OpL0<T> o0, OpLc<T> oc, const T* 
 
 template <int SD, typename T, int LV>
 __global__ void __launch_bounds__(256) k_diag(OpL0<T> o0, OpLc<T> oc, T* __restrict__ d, int invert) {
+    pdl_enter();
     const Geom& g = LV == 0 ? o0.g : oc.g;
     ST_NODE_LOOP_BEGIN(g)
     T v = T(1);
@@ -66,6 +73,7 @@ __global__ void __launch_bounds__(256) k_diag(OpL0<T> o0, OpLc<T> oc, T* __restr
 template <int SD, typename T, int LV, bool TR>
 __global__ void __launch_bounds__(256) k_residual(OpL0<T> o0, OpLc<T> oc, const T* __restrict__ b,
                                                   const T* __restrict__ x, T* __restrict__ r) {
+    pdl_enter();
     const Geom& g = LV == 0 ? o0.g : oc.g;
     LoadPlain<T, T> ld{x};
     ST_NODE_LOOP_BEGIN(g)
@@ -84,6 +92,7 @@ __global__ void __launch_bounds__(256) k_residual(OpL0<T> o0, OpLc<T> oc, const 
 template <int SD, typename T>
 __global__ void __launch_bounds__(256) k_restrict(Geom gf, Geom gc, int kind, const T* __restrict__ rf,
                                                   T* __restrict__ rc) {
+    pdl_enter();
     ST_NODE_LOOP_BEGIN(gc)
     rc[idx_] = restrict_node<SD, T>(gf, gc, kind, rf, i_, j_, k_, n_);
     ST_NODE_LOOP_END
@@ -93,6 +102,7 @@ __global__ void __launch_bounds__(256) k_restrict(Geom gf, Geom gc, int kind, co
 template <int SD, typename T>
 __global__ void __launch_bounds__(256) k_prolong(Geom gf, Geom gc, int kind, const T* __restrict__ xc,
                                                  T* __restrict__ xf) {
+    pdl_enter();
     ST_NODE_LOOP_BEGIN(gf)
     if (is_free<SD>(gf, i_, j_, k_, n_)) xf[idx_] += prolong_node<SD, T>(gf, gc, kind, xc, i_, j_, k_, n_);
     ST_NODE_LOOP_END
@@ -106,6 +116,7 @@ template <int SD, typename T, int LV, bool TR, bool ZERO>
 __global__ void __launch_bounds__(256) k_sm_start(OpL0<T> o0, OpLc<T> oc, const T* __restrict__ b,
                                                   const T* __restrict__ x, T* __restrict__ u0, int steps,
                                                   SmState* st, RedBuf rb) {
+    pdl_enter();
     const Geom& g = LV == 0 ? o0.g : oc.g;
     LoadPlain<T, T> ld{x};
     double acc[1] = {0.0};
@@ -135,6 +146,7 @@ template <int SD, typename T, int LV, bool TR>
 __global__ void __launch_bounds__(256) k_sm_apply(OpL0<T> o0, OpLc<T> oc, const T* __restrict__ dinv,
                                                   Basis<T> U, T* __restrict__ w, int j, SmState* st,
                                                   RedBuf rb) {
+    pdl_enter();
     if (smt<T>(st)->stop || j >= smt<T>(st)->kdim) return;
     const Geom& g = LV == 0 ? o0.g : oc.g;
     LoadScaled<T> ld{U.u[j], dinv};
@@ -161,6 +173,7 @@ __global__ void __launch_bounds__(256) k_sm_apply(OpL0<T> o0, OpLc<T> oc, const 
 // ---------------------------------------------------------------- coarsest solve
 template <typename T>
 __global__ void k_coarse_gemv(const double* __restrict__ Ainv, int n, const T* __restrict__ b, T* __restrict__ x) {
+    pdl_enter();
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= n) return;
     const double* row = Ainv + (long long)warp * n;
@@ -173,6 +186,7 @@ __global__ void k_coarse_gemv(const double* __restrict__ Ainv, int n, const T* _
 
 template <typename T>
 __global__ void k_coarse_gemv_t(const double* __restrict__ Ainv, int n, const T* __restrict__ b, T* __restrict__ x) {
+    pdl_enter();
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     double a = 0;
@@ -216,6 +230,7 @@ template <int SD, typename TZ, bool TR>
 __global__ void __launch_bounds__(256) k_fg_apply_dots(OpL0<double> op, const TZ* __restrict__ z,
                                                        TZ* __restrict__ zstore, double* __restrict__ w, VPtrs V,
                                                        int j, FgState* fs, RedBuf rb) {
+    pdl_enter();
     const Geom& g = op.g;
     LoadPlain<double, TZ> ld{z};
     double dots[32] = {0.0};  // j + 1 <= kMaxRestart = 32 dots in one pass
@@ -241,6 +256,7 @@ __global__ void __launch_bounds__(256) k_fg_apply_dots(OpL0<double> op, const TZ
 // pass 1: w -= sum h1_q v_q, norm; H column completed, Givens applied.
 __global__ void __launch_bounds__(256) k_fg_update(Geom g, double* __restrict__ w, VPtrs V, int j, int pass,
                                                    FgState* fs, RedBuf rb) {
+    pdl_enter();
     __shared__ double cf[32];
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     if (tid <= j) cf[tid] = fs->h1[tid];
@@ -285,6 +301,7 @@ template <typename TZ>
 __global__ void __launch_bounds__(256) k_fg_normalize(Geom g, const double* __restrict__ w,
                                                       double* __restrict__ vn, TZ* __restrict__ bmg,
                                                       const FgState* fs) {
+    pdl_enter();
     const double h = fs->nrm;
     const double inv = h > 0 ? 1.0 / h : 0.0;
     ST_NODE_LOOP_BEGIN(g)
@@ -295,6 +312,7 @@ __global__ void __launch_bounds__(256) k_fg_normalize(Geom g, const double* __re
 }
 
 __global__ void k_fg_backsolve(FgState* fs, int k) {
+    pdl_enter();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     for (int q = k - 1; q >= 0; --q) {
         double a = fs->g[q];
@@ -307,6 +325,7 @@ __global__ void k_fg_backsolve(FgState* fs, int k) {
 template <typename TZ>
 __global__ void __launch_bounds__(256) k_fg_update_x(Geom g, double* __restrict__ x, ZPtrs<TZ> Z, int k,
                                                      const FgState* fs) {
+    pdl_enter();
     __shared__ double y[kMaxRestart];
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     if (tid < k) y[tid] = fs->h1[tid];
@@ -322,6 +341,7 @@ template <int SD, bool TR>
 __global__ void __launch_bounds__(256) k_fg_residual(OpL0<double> op, const double* __restrict__ f,
                                                      const double* __restrict__ x, double* __restrict__ r,
                                                      FgState* fs, RedBuf rb) {
+    pdl_enter();
     const Geom& g = op.g;
     LoadPlain<double, double> ld{x};
     double acc[1] = {0.0};
@@ -343,6 +363,7 @@ __global__ void __launch_bounds__(256) k_fg_residual(OpL0<double> op, const doub
 template <typename TZ>
 __global__ void __launch_bounds__(256) k_fg_start(Geom g, double* __restrict__ v0, TZ* __restrict__ bmg,
                                                   FgState* fs) {
+    pdl_enter();
     const double beta = fs->beta;
     const double inv = beta > 0 ? 1.0 / beta : 0.0;
     if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
@@ -360,6 +381,7 @@ __global__ void __launch_bounds__(256) k_fg_start(Geom g, double* __restrict__ v
 
 __global__ void __launch_bounds__(256) k_dot64(Geom g, const double* __restrict__ a, const double* __restrict__ b,
                                                double* out_d, RedBuf rb) {
+    pdl_enter();
     double acc[1] = {0.0};
     ST_NODE_LOOP_BEGIN(g)
     acc[0] += a[idx_] * b[idx_];
@@ -372,6 +394,7 @@ __global__ void __launch_bounds__(256) k_dot64(Geom g, const double* __restrict_
 
 template <int SD>
 __global__ void __launch_bounds__(256) k_mask_copy(Geom g, const double* __restrict__ src, double* __restrict__ dst) {
+    pdl_enter();
     ST_NODE_LOOP_BEGIN(g)
     dst[idx_] = is_free<SD>(g, i_, j_, k_, n_) ? src[idx_] : 0.0;
     ST_NODE_LOOP_END
@@ -383,6 +406,7 @@ __global__ void __launch_bounds__(256) k_mask_copy(Geom g, const double* __restr
 template <typename T>
 __global__ void __launch_bounds__(256) km_apply(Geom g, const T* __restrict__ coef, const unsigned char* __restrict__ dir,
                                                 int chunk, const T* __restrict__ x, T* __restrict__ y) {
+    pdl_enter();
     LoadPlain<T, T> ld{x};
     march2d<T>(g, coef, dir, ld, chunk, [&](long long q, T v) { y[q] = v; });
 }
@@ -392,6 +416,7 @@ __global__ void __launch_bounds__(256) km_residual(Geom g, const T* __restrict__
                                                    const unsigned char* __restrict__ dir, int chunk,
                                                    const T* __restrict__ b, const T* __restrict__ x,
                                                    T* __restrict__ r) {
+    pdl_enter();
     LoadPlain<T, T> ld{x};
     march2d<T>(g, coef, dir, ld, chunk, [&](long long q, T v) { r[q] = b[q] - v; });
 }
@@ -401,6 +426,7 @@ __global__ void __launch_bounds__(256) km_sm_start(Geom g, const T* __restrict__
                                                    const unsigned char* __restrict__ dir, int chunk,
                                                    const T* __restrict__ b, const T* __restrict__ x,
                                                    T* __restrict__ u0, int steps, SmState* st, RedBuf rb) {
+    pdl_enter();
     LoadPlain<T, T> ld{x};
     T accT = T(0);
     march2d<T>(g, coef, dir, ld, chunk, [&](long long q, T v) {
@@ -420,6 +446,7 @@ __global__ void __launch_bounds__(256) km_sm_apply(Geom g, const T* __restrict__
                                                    const unsigned char* __restrict__ dir, int chunk,
                                                    const T* __restrict__ dinv, Basis<T> U, T* __restrict__ w, int j,
                                                    SmState* st, RedBuf rb) {
+    pdl_enter();
     if (smt<T>(st)->stop || j >= smt<T>(st)->kdim) return;
     LoadScaled<T> ld{U.u[j], dinv};
     T accT[kMaxSmooth];
@@ -443,6 +470,7 @@ __global__ void __launch_bounds__(256) km_fg_apply_dots(Geom g, const double* __
                                                         const TZ* __restrict__ z, TZ* __restrict__ zstore,
                                                         double* __restrict__ w, VPtrs V, int j, FgState* fs,
                                                         RedBuf rb) {
+    pdl_enter();
     LoadPlain<double, TZ> ld{z};
     double dots[32];
 #pragma unroll
@@ -464,6 +492,7 @@ __global__ void __launch_bounds__(256) km_fg_residual(Geom g, const double* __re
                                                       const unsigned char* __restrict__ dir, int chunk,
                                                       const double* __restrict__ f, const double* __restrict__ x,
                                                       double* __restrict__ r, FgState* fs, RedBuf rb) {
+    pdl_enter();
     LoadPlain<double, double> ld{x};
     double acc[1] = {0.0};
     march2d<double>(g, coef, dir, ld, chunk, [&](long long q, double v) {
@@ -484,6 +513,7 @@ __global__ void __launch_bounds__(256) km_sm_applyw(Geom g, const T* __restrict_
                                                     const unsigned char* __restrict__ dir, int chunk,
                                                     const T* __restrict__ dinv, const T* __restrict__ uj,
                                                     T* __restrict__ w, int j, const SmState* st) {
+    pdl_enter();
     if (smt<T>(st)->stop || j >= smt<T>(st)->kdim) return;
     LoadScaled<T> ld{uj, dinv};
     march2d<T>(g, coef, dir, ld, chunk, [&](long long q, T v) { w[q] = v; });
@@ -495,6 +525,7 @@ __global__ void __launch_bounds__(256) km_sm_applyw_sc(Geom g, const T* __restri
                                                        const unsigned char* __restrict__ dir, int chunk,
                                                        const T* __restrict__ dinv, const T* __restrict__ uj,
                                                        T* __restrict__ w, int j, const SmState* st) {
+    pdl_enter();
     if (smt<T>(st)->stop || j >= smt<T>(st)->kdim) return;
     constexpr int PF = sizeof(T) == 4 ? 13 : 5;  // planes in flight per block (ring of PF + 3)
     march2d_scaled<T, PF>(g, sc, coef, dir, uj, dinv, chunk, [&](long long q, T v) { w[q] = v; });
@@ -504,6 +535,7 @@ template <int SD, typename T, int LV, bool TR>
 __global__ void __launch_bounds__(256) k_sm_applyw(OpL0<T> o0, OpLc<T> oc, const T* __restrict__ dinv,
                                                    const T* __restrict__ uj, T* __restrict__ w, int j,
                                                    const SmState* st) {
+    pdl_enter();
     if (smt<T>(st)->stop || j >= smt<T>(st)->kdim) return;
     const Geom& g = LV == 0 ? o0.g : oc.g;
     LoadScaled<T> ld{uj, dinv};
@@ -518,6 +550,7 @@ __global__ void __launch_bounds__(256) km_fg_apply(Geom g, const double* __restr
                                                    const unsigned char* __restrict__ dir, int chunk,
                                                    const TZ* __restrict__ z, TZ* __restrict__ zstore,
                                                    double* __restrict__ w) {
+    pdl_enter();
     LoadPlain<double, TZ> ld{z};
     march2d<double>(g, coef, dir, ld, chunk, [&](long long q, double v) {
         w[q] = v;
@@ -528,6 +561,7 @@ __global__ void __launch_bounds__(256) km_fg_apply(Geom g, const double* __restr
 template <int SD, typename TZ, bool TR>
 __global__ void __launch_bounds__(256) k_fg_apply(OpL0<double> op, const TZ* __restrict__ z, TZ* __restrict__ zstore,
                                                   double* __restrict__ w) {
+    pdl_enter();
     const Geom& g = op.g;
     LoadPlain<double, TZ> ld{z};
     ST_NODE_LOOP_BEGIN(g)
@@ -567,13 +601,13 @@ void launch_apply_l0(int sd, const OpL0<T>& op, bool tr, const T* x, T* y, cudaS
     if (sd == 2 && op.st_dir) {
         dim3 grid, block;
         const MarchGrid mg = march_grid(op.g, grid, block);
-        km_apply<T><<<grid, block, 0, s>>>(op.g, op.st_coef[tr ? 1 : 0], op.st_dir, mg.chunk, x, y);
+        launch_pdl(km_apply<T>, grid, block, 0, s, op.g, op.st_coef[tr ? 1 : 0], op.st_dir, mg.chunk, x, y);
         return;
     }
     const LaunchCfg c = node_cfg(op.g);
     const OpLc<T> oc = dummy_lc<T>(op.g);
-    ST_SD_DISPATCH(sd, if (tr) k_apply<SD, T, 0, true><<<c.grid, c.block, 0, s>>>(op, oc, x, y);
-                   else k_apply<SD, T, 0, false><<<c.grid, c.block, 0, s>>>(op, oc, x, y));
+    ST_SD_DISPATCH(sd, if (tr) launch_pdl(k_apply<SD, T, 0, true>, c.grid, c.block, 0, s, op, oc, x, y);
+                   else launch_pdl(k_apply<SD, T, 0, false>, c.grid, c.block, 0, s, op, oc, x, y));
 }
 template <typename T>
 void launch_apply_lc(int sd, const OpLc<T>& op, bool tr, const T* x, T* y, cudaStream_t s) {
@@ -581,27 +615,27 @@ void launch_apply_lc(int sd, const OpLc<T>& op, bool tr, const T* x, T* y, cudaS
     if (sd == 2 && op.st_dir) {
         dim3 grid, block;
         const MarchGrid mg = march_grid(op.g, grid, block);
-        km_apply<T><<<grid, block, 0, s>>>(op.g, op.st_coef[tr ? 1 : 0], op.st_dir, mg.chunk, x, y);
+        launch_pdl(km_apply<T>, grid, block, 0, s, op.g, op.st_coef[tr ? 1 : 0], op.st_dir, mg.chunk, x, y);
         return;
     }
     const LaunchCfg c = node_cfg(op.g);
     const OpL0<T> o0 = dummy_l0<T>(op.g);
-    ST_SD_DISPATCH(sd, if (tr) k_apply<SD, T, 1, true><<<c.grid, c.block, 0, s>>>(o0, op, x, y);
-                   else k_apply<SD, T, 1, false><<<c.grid, c.block, 0, s>>>(o0, op, x, y));
+    ST_SD_DISPATCH(sd, if (tr) launch_pdl(k_apply<SD, T, 1, true>, c.grid, c.block, 0, s, o0, op, x, y);
+                   else launch_pdl(k_apply<SD, T, 1, false>, c.grid, c.block, 0, s, o0, op, x, y));
 }
 template <typename T>
 void launch_diag_l0(int sd, const OpL0<T>& op, T* d, bool invert, cudaStream_t s) {
     note_launch(s);
     const LaunchCfg c = node_cfg(op.g);
     const OpLc<T> oc = dummy_lc<T>(op.g);
-    ST_SD_DISPATCH(sd, k_diag<SD, T, 0><<<c.grid, c.block, 0, s>>>(op, oc, d, invert ? 1 : 0));
+    ST_SD_DISPATCH(sd, launch_pdl(k_diag<SD, T, 0>, c.grid, c.block, 0, s, op, oc, d, invert ? 1 : 0));
 }
 template <typename T>
 void launch_diag_lc(int sd, const OpLc<T>& op, T* d, bool invert, cudaStream_t s) {
     note_launch(s);
     const LaunchCfg c = node_cfg(op.g);
     const OpL0<T> o0 = dummy_l0<T>(op.g);
-    ST_SD_DISPATCH(sd, k_diag<SD, T, 1><<<c.grid, c.block, 0, s>>>(o0, op, d, invert ? 1 : 0));
+    ST_SD_DISPATCH(sd, launch_pdl(k_diag<SD, T, 1>, c.grid, c.block, 0, s, o0, op, d, invert ? 1 : 0));
 }
 template <typename T>
 void launch_residual(int sd, int lvl, const OpL0<T>& o0, const OpLc<T>& oc, bool tr, const T* b, const T* x, T* r,
@@ -614,30 +648,30 @@ void launch_residual(int sd, int lvl, const OpL0<T>& o0, const OpLc<T>& oc, bool
             const T* coef = lvl == 0 ? o0.st_coef[tr ? 1 : 0] : oc.st_coef[tr ? 1 : 0];
             dim3 grid, block;
             const MarchGrid mg = march_grid(g, grid, block);
-            km_residual<T><<<grid, block, 0, s>>>(g, coef, dir, mg.chunk, b, x, r);
+            launch_pdl(km_residual<T>, grid, block, 0, s, g, coef, dir, mg.chunk, b, x, r);
             return;
         }
     }
     const LaunchCfg c = node_cfg(lvl == 0 ? o0.g : oc.g);
     if (lvl == 0) {
-        ST_SD_DISPATCH(sd, if (tr) k_residual<SD, T, 0, true><<<c.grid, c.block, 0, s>>>(o0, oc, b, x, r);
-                       else k_residual<SD, T, 0, false><<<c.grid, c.block, 0, s>>>(o0, oc, b, x, r));
+        ST_SD_DISPATCH(sd, if (tr) launch_pdl(k_residual<SD, T, 0, true>, c.grid, c.block, 0, s, o0, oc, b, x, r);
+                       else launch_pdl(k_residual<SD, T, 0, false>, c.grid, c.block, 0, s, o0, oc, b, x, r));
     } else {
-        ST_SD_DISPATCH(sd, if (tr) k_residual<SD, T, 1, true><<<c.grid, c.block, 0, s>>>(o0, oc, b, x, r);
-                       else k_residual<SD, T, 1, false><<<c.grid, c.block, 0, s>>>(o0, oc, b, x, r));
+        ST_SD_DISPATCH(sd, if (tr) launch_pdl(k_residual<SD, T, 1, true>, c.grid, c.block, 0, s, o0, oc, b, x, r);
+                       else launch_pdl(k_residual<SD, T, 1, false>, c.grid, c.block, 0, s, o0, oc, b, x, r));
     }
 }
 template <typename T>
 void launch_restrict(const Geom& gf, const Geom& gc, int kind, int sd, const T* rf, T* rc, cudaStream_t s) {
     note_launch(s);
     const LaunchCfg c = node_cfg(gc);
-    ST_SD_DISPATCH(sd, k_restrict<SD, T><<<c.grid, c.block, 0, s>>>(gf, gc, kind, rf, rc));
+    ST_SD_DISPATCH(sd, launch_pdl(k_restrict<SD, T>, c.grid, c.block, 0, s, gf, gc, kind, rf, rc));
 }
 template <typename T>
 void launch_prolong(const Geom& gf, const Geom& gc, int kind, int sd, const T* xc, T* xf, cudaStream_t s) {
     note_launch(s);
     const LaunchCfg c = node_cfg(gf);
-    ST_SD_DISPATCH(sd, k_prolong<SD, T><<<c.grid, c.block, 0, s>>>(gf, gc, kind, xc, xf));
+    ST_SD_DISPATCH(sd, launch_pdl(k_prolong<SD, T>, c.grid, c.block, 0, s, gf, gc, kind, xc, xf));
 }
 
 // Timing event on stream s: an event node when the stream is being captured into a graph,
@@ -681,16 +715,16 @@ static void smooth_impl(const OpL0<T>& o0, const OpLc<T>& oc, const T* b, T* x, 
     } else {
         note_launch(s);
         if (march)
-            km_sm_start<T><<<mgrid, mblock, 0, s>>>(g, coef, dir, mg.chunk, b, x, U.u[0], steps, st, rb);
+            launch_pdl(km_sm_start<T>, mgrid, mblock, 0, s, g, coef, dir, mg.chunk, b, x, U.u[0], steps, st, rb);
         else
-            k_sm_start<SD, T, LV, TR, false><<<c.grid, c.block, 0, s>>>(o0, oc, b, x, U.u[0], steps, st, rb);
+            launch_pdl(k_sm_start<SD, T, LV, TR, false>, c.grid, c.block, 0, s, o0, oc, b, x, U.u[0], steps, st, rb);
     }
     if (fused) {
         if constexpr (std::is_same<T, float>::value) {
             // step 0: w = A D^{-1} u_0 and (w, u_0); then fused steps j -> j+1; the last
             // update only closes the Hessenberg matrix (norm of u_m) before the combination.
             note_launch(s);
-            km_sm_applyw<T><<<mgrid, mblock, 0, s>>>(g, coef, dir, mg.chunk, dinv, U.u[0], w, 0, st);
+            launch_pdl(km_sm_applyw<T>, mgrid, mblock, 0, s, g, coef, dir, mg.chunk, dinv, U.u[0], w, 0, st);
             launch_dots<T>(N, w, P, 1, 0, 0, st, rb, s);
             T* wc = w;
             T* wn = w2;
@@ -711,18 +745,18 @@ static void smooth_impl(const OpL0<T>& o0, const OpLc<T>& oc, const T* b, T* x, 
             // optional timing events around the operator apply (event nodes when captured)
             if (ev) record_timing_event(ev[2 * j], s);
             if (march && sc)
-                km_sm_applyw_sc<T><<<mgrid, mblock, 0, s>>>(g, sc + (TR ? 27 * g.plane : 0), coef, dir, mg.chunk,
+                launch_pdl(km_sm_applyw_sc<T>, mgrid, mblock, 0, s, g, sc + (TR ? 27 * g.plane : 0), coef, dir, mg.chunk,
                                                            dinv, U.u[j], w, j, st);
             else if (march)
-                km_sm_applyw<T><<<mgrid, mblock, 0, s>>>(g, coef, dir, mg.chunk, dinv, U.u[j], w, j, st);
+                launch_pdl(km_sm_applyw<T>, mgrid, mblock, 0, s, g, coef, dir, mg.chunk, dinv, U.u[j], w, j, st);
             else
-                k_sm_applyw<SD, T, LV, TR><<<c.grid, c.block, 0, s>>>(o0, oc, dinv, U.u[j], w, j, st);
+                launch_pdl(k_sm_applyw<SD, T, LV, TR>, c.grid, c.block, 0, s, o0, oc, dinv, U.u[j], w, j, st);
             if (ev) record_timing_event(ev[2 * j + 1], s);
             launch_dots<T>(N, w, P, j + 1, j, 0, st, rb, s);
         } else if (march) {
-            km_sm_apply<T><<<mgrid, mblock, 0, s>>>(g, coef, dir, mg.chunk, dinv, U, w, j, st, rb);
+            launch_pdl(km_sm_apply<T>, mgrid, mblock, 0, s, g, coef, dir, mg.chunk, dinv, U, w, j, st, rb);
         } else {
-            k_sm_apply<SD, T, LV, TR><<<c.grid, c.block, 0, s>>>(o0, oc, dinv, U, w, j, st, rb);
+            launch_pdl(k_sm_apply<SD, T, LV, TR>, c.grid, c.block, 0, s, o0, oc, dinv, U, w, j, st, rb);
         }
         launch_update<T>(N, w, U.u[j + 1], P, j, steps, 0, st, rb, s);
     }
@@ -746,9 +780,9 @@ template <typename T>
 void launch_coarse_solve(const double* Ainv, int n, bool tr, const T* b, T* x, cudaStream_t s) {
     note_launch(s);
     if (tr)
-        k_coarse_gemv_t<T><<<(n + 127) / 128, 128, 0, s>>>(Ainv, n, b, x);
+        launch_pdl(k_coarse_gemv_t<T>, (n + 127) / 128, 128, 0, s, Ainv, n, b, x);
     else
-        k_coarse_gemv<T><<<(n * 32 + 255) / 256, 256, 0, s>>>(Ainv, n, b, x);
+        launch_pdl(k_coarse_gemv<T>, (n * 32 + 255) / 256, 256, 0, s, Ainv, n, b, x);
 }
 
 template <typename TZ>
@@ -758,11 +792,11 @@ void launch_fg_apply_dots(int sd, const OpL0<double>& op, bool tr, const TZ* z, 
     if (sd == 2 && op.st_dir) {
         dim3 grid, block;
         const MarchGrid mg = march_grid(op.g, grid, block);
-        km_fg_apply<TZ><<<grid, block, 0, s>>>(op.g, op.st_coef[tr ? 1 : 0], op.st_dir, mg.chunk, z, zstore, w);
+        launch_pdl(km_fg_apply<TZ>, grid, block, 0, s, op.g, op.st_coef[tr ? 1 : 0], op.st_dir, mg.chunk, z, zstore, w);
     } else {
         const LaunchCfg c = node_cfg(op.g);
-        ST_SD_DISPATCH(sd, if (tr) k_fg_apply<SD, TZ, true><<<c.grid, c.block, 0, s>>>(op, z, zstore, w);
-                       else k_fg_apply<SD, TZ, false><<<c.grid, c.block, 0, s>>>(op, z, zstore, w));
+        ST_SD_DISPATCH(sd, if (tr) launch_pdl(k_fg_apply<SD, TZ, true>, c.grid, c.block, 0, s, op, z, zstore, w);
+                       else launch_pdl(k_fg_apply<SD, TZ, false>, c.grid, c.block, 0, s, op, z, zstore, w));
     }
     Ptrs<double> P{};
     for (int q = 0; q <= j; ++q) P.p[q] = V[q];
@@ -781,14 +815,14 @@ void launch_fg_normalize(const Geom& g, const double* w, double* vnext, TZ* bmg,
     note_launch(s);
     (void)j;
     const LaunchCfg c = node_cfg(g);
-    k_fg_normalize<TZ><<<c.grid, c.block, 0, s>>>(g, w, vnext, bmg, fs);
+    launch_pdl(k_fg_normalize<TZ>, c.grid, c.block, 0, s, g, w, vnext, bmg, fs);
 }
 
 template <typename TZ>
 void launch_fg_update_x(const Geom& g, double* x, TZ* const* Z, int k, FgState* fs, cudaStream_t s) {
     if (k <= 0) return;
     note_launch(s);
-    k_fg_backsolve<<<1, 32, 0, s>>>(fs, k);
+    launch_pdl(k_fg_backsolve, 1, 32, 0, s, fs, k);
     Ptrs<TZ> P{};
     for (int q = 0; q < k; ++q) P.p[q] = Z[q];
     launch_fg_combine<TZ>(g.nnodes, x, P, k, fs, s);
@@ -800,31 +834,31 @@ void launch_fg_residual(int sd, const OpL0<double>& op, bool tr, const double* f
     if (sd == 2 && op.st_dir) {
         dim3 grid, block;
         const MarchGrid mg = march_grid(op.g, grid, block);
-        km_fg_residual<<<grid, block, 0, s>>>(op.g, op.st_coef[tr ? 1 : 0], op.st_dir, mg.chunk, f, x, r, fs, rb);
+        launch_pdl(km_fg_residual, grid, block, 0, s, op.g, op.st_coef[tr ? 1 : 0], op.st_dir, mg.chunk, f, x, r, fs, rb);
         return;
     }
     const LaunchCfg c = node_cfg(op.g);
-    ST_SD_DISPATCH(sd, if (tr) k_fg_residual<SD, true><<<c.grid, c.block, 0, s>>>(op, f, x, r, fs, rb);
-                   else k_fg_residual<SD, false><<<c.grid, c.block, 0, s>>>(op, f, x, r, fs, rb));
+    ST_SD_DISPATCH(sd, if (tr) launch_pdl(k_fg_residual<SD, true>, c.grid, c.block, 0, s, op, f, x, r, fs, rb);
+                   else launch_pdl(k_fg_residual<SD, false>, c.grid, c.block, 0, s, op, f, x, r, fs, rb));
 }
 
 template <typename TZ>
 void launch_fg_start(const Geom& g, double* v0, TZ* bmg, FgState* fs, cudaStream_t s) {
     note_launch(s);
     const LaunchCfg c = node_cfg(g);
-    k_fg_start<TZ><<<c.grid, c.block, 0, s>>>(g, v0, bmg, fs);
+    launch_pdl(k_fg_start<TZ>, c.grid, c.block, 0, s, g, v0, bmg, fs);
 }
 
 void launch_dot64(const Geom& g, const double* a, const double* b, double* out, RedBuf rb, cudaStream_t s) {
     note_launch(s);
     const LaunchCfg c = node_cfg(g);
-    k_dot64<<<c.grid, c.block, 0, s>>>(g, a, b, out, rb);
+    launch_pdl(k_dot64, c.grid, c.block, 0, s, g, a, b, out, rb);
 }
 
 void launch_mask_copy(int sd, const Geom& g, const double* src, double* dst, cudaStream_t s) {
     note_launch(s);
     const LaunchCfg c = node_cfg(g);
-    ST_SD_DISPATCH(sd, k_mask_copy<SD><<<c.grid, c.block, 0, s>>>(g, src, dst));
+    ST_SD_DISPATCH(sd, launch_pdl(k_mask_copy<SD>, c.grid, c.block, 0, s, g, src, dst));
 }
 
 #define ST_INST_T(T)                                                                                                \

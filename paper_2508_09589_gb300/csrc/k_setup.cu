@@ -21,6 +21,7 @@ namespace st {
 
 __global__ void k_design_cast(const double* __restrict__ in, double* __restrict__ g64,
                               __nv_bfloat16* __restrict__ g16, long long n) {
+    pdl_enter();
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
         double v = in[q];
         v = v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
@@ -31,6 +32,7 @@ __global__ void k_design_cast(const double* __restrict__ in, double* __restrict_
 }
 
 __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, long long n) {
+    pdl_enter();
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
         out[q] = (float)in[q];
 }
@@ -38,6 +40,7 @@ __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ ou
 // One coarse element: A_E = M_E (sum_children Q_c^T A_c Q_c) M_E with Q_c = Q_t (x) Q_s.
 template <int SD, int LV>
 __global__ void k_build(OpL0<double> f0, OpLc<double> fc, Geom gc, int kind, int tc, double* __restrict__ out) {
+    pdl_enter();
     constexpr int NS = 1 << SD, NSYM = NS * (NS + 1) / 2, NV = 4 * NSYM;
     const Geom& gf = LV == 0 ? f0.g : fc.g;
     const long long nstore = tc ? 2 * gc.sp_elems : (long long)gc.net * gc.sp_elems;
@@ -123,6 +126,7 @@ __global__ void k_build(OpL0<double> f0, OpLc<double> fc, Geom gc, int kind, int
 // ---------------------------------------------------------------- dense coarsest operator
 template <int SD, int LV>
 __global__ void k_dense_assemble(OpL0<double> o0, OpLc<double> oc, double* __restrict__ A) {
+    pdl_enter();
     constexpr int NS = 1 << SD, NSYM = NS * (NS + 1) / 2, NV = 4 * NSYM;
     const Geom& g = LV == 0 ? o0.g : oc.g;
     const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -171,6 +175,7 @@ __global__ void k_dense_assemble(OpL0<double> o0, OpLc<double> oc, double* __res
 // pinv[kp] holds 1 / pivot of this step; the thread that writes the next pivot stores its
 // reciprocal, so each step needs one division in total.
 __global__ void k_gj_first(const double* __restrict__ A, double* __restrict__ pinv, int* err) {
+    pdl_enter();
     const double p = A[0];
     if (!(fabs(p) > 1e-300) || !isfinite(p)) *err = 1;
     pinv[0] = (fabs(p) > 1e-300 && isfinite(p)) ? 1.0 / p : 1.0;
@@ -178,6 +183,7 @@ __global__ void k_gj_first(const double* __restrict__ A, double* __restrict__ pi
 
 __global__ void k_gj_step(const double* __restrict__ src, double* __restrict__ dst, int n, int kp,
                           double* __restrict__ pinv, int* err) {
+    pdl_enter();
     const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (q >= (long long)n * n) return;
     const int i = (int)(q / n), j = (int)(q % n);
@@ -205,6 +211,7 @@ __global__ void k_gj_step(const double* __restrict__ src, double* __restrict__ d
 // Gauss (exact for uniform q).
 template <int SD>
 __global__ void k_rhs(Geom g, int kind, double q0, double a, double b, double f, double* __restrict__ out) {
+    pdl_enter();
     ST_NODE_LOOP_BEGIN(g)
     double v = 0.0;
     if (is_free<SD>(g, i_, j_, k_, n_)) {
@@ -252,6 +259,7 @@ __device__ __forceinline__ double elem_avg(const Geom& g, const double* s, int s
 template <int SD>
 __global__ void __launch_bounds__(256) k_pnorm_theta(Geom g, const double* __restrict__ s, int P, double* theta,
                                                      RedBuf rb) {
+    pdl_enter();
     // element loop: (ex, ey) from the thread grid, (slab, ez) from the plane loop
     double acc[1] = {0.0};
     const int ex = blockIdx.x * blockDim.x + threadIdx.x, ey = blockIdx.y * blockDim.y + threadIdx.y;
@@ -272,6 +280,7 @@ __global__ void __launch_bounds__(256) k_pnorm_theta(Geom g, const double* __res
 template <int SD>
 __global__ void __launch_bounds__(256) k_pnorm_rhs(Geom g, const double* __restrict__ s, int P,
                                                    const double* theta, double* __restrict__ rhs, double* phi) {
+    pdl_enter();
     constexpr int NS = 1 << SD;
     const double th = *theta;
     const double sc = pow(th, (1.0 - P) / (double)P) / (2 * NS);
@@ -302,6 +311,7 @@ __global__ void __launch_bounds__(256) k_pnorm_rhs(Geom g, const double* __restr
 template <int SD>
 __global__ void k_sens(OpL0<double> op, const double* __restrict__ s, const double* __restrict__ lam,
                        double* __restrict__ out) {
+    pdl_enter();
     constexpr int NS = 1 << SD;
     const Geom& g = op.g;
     const long long nout = op.tc ? g.sp_elems : (long long)g.net * g.sp_elems;
@@ -350,13 +360,13 @@ __global__ void k_sens(OpL0<double> op, const double* __restrict__ s, const doub
 void launch_design_cast(const double* in, double* g64, __nv_bfloat16* g16, long long n, cudaStream_t s) {
     note_launch(s);
     const int blocks = (int)((n + 255) / 256 < 65536 ? (n + 255) / 256 : 65536);
-    k_design_cast<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(in, g64, g16, n);
+    launch_pdl(k_design_cast, blocks > 0 ? blocks : 1, 256, 0, s, in, g64, g16, n);
 }
 
 void launch_to_float(const double* in, float* out, long long n, cudaStream_t s) {
     note_launch(s);
     const int blocks = (int)((n + 255) / 256 < 65536 ? (n + 255) / 256 : 65536);
-    k_to_float<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(in, out, n);
+    launch_pdl(k_to_float, blocks > 0 ? blocks : 1, 256, 0, s, in, out, n);
 }
 
 void launch_build_from_l0(int sd, const OpL0<double>& f0, const Geom& gc, int kind, int tc, double* elem_c,
@@ -365,7 +375,7 @@ void launch_build_from_l0(int sd, const OpL0<double>& f0, const Geom& gc, int ki
     const long long nstore = tc ? 2 * gc.sp_elems : (long long)gc.net * gc.sp_elems;
     const int blocks = (int)((nstore + 127) / 128);
     OpLc<double> dummy{};
-    ST_SD_DISPATCH(sd, k_build<SD, 0><<<blocks, 128, 0, s>>>(f0, dummy, gc, kind, tc, elem_c));
+    ST_SD_DISPATCH(sd, launch_pdl(k_build<SD, 0>, blocks, 128, 0, s, f0, dummy, gc, kind, tc, elem_c));
 }
 
 void launch_build_from_lc(int sd, const OpLc<double>& fc, const Geom& gc, int kind, double* elem_c, cudaStream_t s) {
@@ -373,7 +383,7 @@ void launch_build_from_lc(int sd, const OpLc<double>& fc, const Geom& gc, int ki
     const long long nstore = fc.tc ? 2 * gc.sp_elems : (long long)gc.net * gc.sp_elems;
     const int blocks = (int)((nstore + 127) / 128);
     OpL0<double> dummy{};
-    ST_SD_DISPATCH(sd, k_build<SD, 1><<<blocks, 128, 0, s>>>(dummy, fc, gc, kind, fc.tc, elem_c));
+    ST_SD_DISPATCH(sd, launch_pdl(k_build<SD, 1>, blocks, 128, 0, s, dummy, fc, gc, kind, fc.tc, elem_c));
 }
 
 void launch_dense_assemble(int sd, int lvl, const OpL0<double>& o0, const OpLc<double>& oc, double* A,
@@ -383,9 +393,9 @@ void launch_dense_assemble(int sd, int lvl, const OpL0<double>& o0, const OpLc<d
     cudaMemsetAsync(A, 0, sizeof(double) * g.nnodes * g.nnodes, s);
     const int blocks = (int)((g.nnodes + 127) / 128);
     if (lvl == 0) {
-        ST_SD_DISPATCH(sd, k_dense_assemble<SD, 0><<<blocks, 128, 0, s>>>(o0, oc, A));
+        ST_SD_DISPATCH(sd, launch_pdl(k_dense_assemble<SD, 0>, blocks, 128, 0, s, o0, oc, A));
     } else {
-        ST_SD_DISPATCH(sd, k_dense_assemble<SD, 1><<<blocks, 128, 0, s>>>(o0, oc, A));
+        ST_SD_DISPATCH(sd, launch_pdl(k_dense_assemble<SD, 1>, blocks, 128, 0, s, o0, oc, A));
     }
 }
 
@@ -395,9 +405,9 @@ void launch_gauss_jordan(double* A, double* B, double* pinv, int n, int* err, cu
     const int blocks = (int)((nn + 255) / 256);
     double* src = A;
     double* dst = B;
-    k_gj_first<<<1, 1, 0, s>>>(A, pinv, err);
+    launch_pdl(k_gj_first, 1, 1, 0, s, A, pinv, err);
     for (int kp = 0; kp < n; ++kp) {
-        k_gj_step<<<blocks, 256, 0, s>>>(src, dst, n, kp, pinv, err);
+        launch_pdl(k_gj_step, blocks, 256, 0, s, src, dst, n, kp, pinv, err);
         double* t = src;
         src = dst;
         dst = t;
@@ -409,7 +419,7 @@ void launch_rhs(int sd, const Geom& g, int kind, double q0, double a, double b, 
                 cudaStream_t s) {
     note_launch(s);
     const LaunchCfg c = node_cfg(g);
-    ST_SD_DISPATCH(sd, k_rhs<SD><<<c.grid, c.block, 0, s>>>(g, kind, q0, a, b, f, out));
+    ST_SD_DISPATCH(sd, launch_pdl(k_rhs<SD>, c.grid, c.block, 0, s, g, kind, q0, a, b, f, out));
 }
 
 void launch_pnorm(int sd, const Geom& g, const double* s, int P, double* rhs, double* phi, RedBuf rb,
@@ -422,16 +432,16 @@ void launch_pnorm(int sd, const Geom& g, const double* s, int P, double* rhs, do
     if (gz < 1) gz = 1;
     if (gz > planes) gz = planes;
     dim3 grid(gx, gy, (unsigned)gz);
-    ST_SD_DISPATCH(sd, k_pnorm_theta<SD><<<grid, block, 0, st>>>(g, s, P, scratch, rb));
+    ST_SD_DISPATCH(sd, launch_pdl(k_pnorm_theta<SD>, grid, block, 0, st, g, s, P, scratch, rb));
     const LaunchCfg c = node_cfg(g);
-    ST_SD_DISPATCH(sd, k_pnorm_rhs<SD><<<c.grid, c.block, 0, st>>>(g, s, P, scratch, rhs, phi));
+    ST_SD_DISPATCH(sd, launch_pdl(k_pnorm_rhs<SD>, c.grid, c.block, 0, st, g, s, P, scratch, rhs, phi));
 }
 
 void launch_sens(int sd, const OpL0<double>& op, const double* s, const double* lam, double* out, cudaStream_t st) {
     note_launch(st);
     const long long nout = op.tc ? op.g.sp_elems : (long long)op.g.net * op.g.sp_elems;
     const int blocks = (int)((nout + 127) / 128);
-    ST_SD_DISPATCH(sd, k_sens<SD><<<blocks, 128, 0, st>>>(op, s, lam, out));
+    ST_SD_DISPATCH(sd, launch_pdl(k_sens<SD>, blocks, 128, 0, st, op, s, lam, out));
 }
 
 }  // namespace st

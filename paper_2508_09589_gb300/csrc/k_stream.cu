@@ -12,6 +12,7 @@ namespace st {
 template <typename T, int NQ, int FIN>
 __global__ void __launch_bounds__(256) k_dots(long long n, const T* __restrict__ w, Ptrs<T> U, int nq, int j,
                                               void* state, RedBuf rb) {
+    pdl_enter();
     if (FIN == 0) {
         const SmStateT<T>* st = smt<T>((const SmState*)state);
         if (st->stop || j >= st->kdim) return;
@@ -57,6 +58,7 @@ __global__ void __launch_bounds__(256) k_dots(long long n, const T* __restrict__
 template <typename T, int NQ, int MODE>
 __global__ void __launch_bounds__(256) k_update(long long n, T* __restrict__ w, T* __restrict__ y, Ptrs<T> U, int j,
                                                 int steps, void* state, RedBuf rb) {
+    pdl_enter();
     constexpr int W = Vec16<T>::W;
     __shared__ T cf[NQ];
     __shared__ double cfd[NQ];
@@ -139,6 +141,7 @@ __global__ void __launch_bounds__(256) k_update(long long n, T* __restrict__ w, 
 template <typename T, int NQ>
 __global__ void __launch_bounds__(256) k_sm_combine(long long n, T* __restrict__ x, const T* __restrict__ dinv,
                                                     Ptrs<T> U, int zero_init, const SmState* st_) {
+    pdl_enter();
     constexpr int W = Vec16<T>::W;
     const SmStateT<T>* st = smt<T>(st_);
     __shared__ T cf[NQ];
@@ -179,6 +182,7 @@ __global__ void __launch_bounds__(256) k_sm_combine(long long n, T* __restrict__
 template <typename T>
 __global__ void __launch_bounds__(256) k_sm_norm(long long n, const T* __restrict__ b, int steps, SmState* st,
                                                  RedBuf rb) {
+    pdl_enter();
     constexpr int W = Vec16<T>::W;
     T acc = T(0);
     stream_loop<T>(n, [&](long long v, bool full) {
@@ -202,6 +206,7 @@ __global__ void __launch_bounds__(256) k_sm_norm(long long n, const T* __restric
 template <typename TZ, int NQ>
 __global__ void __launch_bounds__(256) k_fg_combine(long long n, double* __restrict__ x, Ptrs<TZ> Z, int k,
                                                     const FgState* fs) {
+    pdl_enter();
     __shared__ double y[NQ];
     if (threadIdx.x < NQ) y[threadIdx.x] = threadIdx.x < k ? fs->h1[threadIdx.x] : 0.0;
     __syncthreads();
@@ -253,9 +258,9 @@ void launch_dots(long long n, const T* w, const Ptrs<T>& U, int nq, int j, int f
     nq_dispatch(nq, [&](auto NQc) {
         constexpr int NQ = decltype(NQc)::value;
         if (fin == 0)
-            k_dots<T, NQ, 0><<<blocks, 256, 0, s>>>(n, w, U, nq, j, state, rb);
+            launch_pdl(k_dots<T, NQ, 0>, blocks, 256, 0, s, n, w, U, nq, j, state, rb);
         else
-            k_dots<T, NQ, 1><<<blocks, 256, 0, s>>>(n, w, U, nq, j, state, rb);
+            launch_pdl(k_dots<T, NQ, 1>, blocks, 256, 0, s, n, w, U, nq, j, state, rb);
     });
 }
 
@@ -267,11 +272,11 @@ void launch_update(long long n, T* w, T* y, const Ptrs<T>& U, int j, int steps, 
     nq_dispatch(j + 1, [&](auto NQc) {
         constexpr int NQ = decltype(NQc)::value;
         if (mode == 0)
-            k_update<T, NQ, 0><<<blocks, 256, 0, s>>>(n, w, y, U, j, steps, state, rb);
+            launch_pdl(k_update<T, NQ, 0>, blocks, 256, 0, s, n, w, y, U, j, steps, state, rb);
         else if (mode == 1)
-            k_update<T, NQ, 1><<<blocks, 256, 0, s>>>(n, w, y, U, j, steps, state, rb);
+            launch_pdl(k_update<T, NQ, 1>, blocks, 256, 0, s, n, w, y, U, j, steps, state, rb);
         else
-            k_update<T, NQ, 2><<<blocks, 256, 0, s>>>(n, w, y, U, j, steps, state, rb);
+            launch_pdl(k_update<T, NQ, 2>, blocks, 256, 0, s, n, w, y, U, j, steps, state, rb);
     });
 }
 
@@ -282,12 +287,13 @@ void launch_sm_combine(long long n, T* x, const T* dinv, const Ptrs<T>& U, int s
     const int blocks = stream_blocks(n, Vec16<T>::W);
     nq_dispatch(steps, [&](auto NQc) {
         constexpr int NQ = decltype(NQc)::value;
-        k_sm_combine<T, NQ><<<blocks, 256, 0, s>>>(n, x, dinv, U, zero_init ? 1 : 0, st);
+        launch_pdl(k_sm_combine<T, NQ>, blocks, 256, 0, s, n, x, dinv, U, zero_init ? 1 : 0, st);
     });
 }
 
 template <typename T>
 __global__ void k_cg_begin(SmState* st, T rtol) {
+    pdl_enter();
     SmStateT<T>* t = smt<T>(st);
     t->rtol_rel = rtol;
     t->atol = T(-1);
@@ -295,6 +301,7 @@ __global__ void k_cg_begin(SmState* st, T rtol) {
 
 template <typename TI, typename TO>
 __global__ void __launch_bounds__(256) k_convert(const TI* __restrict__ in, TO* __restrict__ out, long long n) {
+    pdl_enter();
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
         out[q] = (TO)in[q];
 }
@@ -302,13 +309,13 @@ __global__ void __launch_bounds__(256) k_convert(const TI* __restrict__ in, TO* 
 template <typename T>
 void launch_cg_begin(SmState* st, double rtol, cudaStream_t s) {
     note_launch(s);
-    k_cg_begin<T><<<1, 1, 0, s>>>(st, (T)rtol);
+    launch_pdl(k_cg_begin<T>, 1, 1, 0, s, st, (T)rtol);
 }
 
 template <typename TI, typename TO>
 void launch_convert(const TI* in, TO* out, long long n, cudaStream_t s) {
     note_launch(s);
-    k_convert<TI, TO><<<stream_blocks(n, 1), 256, 0, s>>>(in, out, n);
+    launch_pdl(k_convert<TI, TO>, stream_blocks(n, 1), 256, 0, s, in, out, n);
 }
 
 template void launch_cg_begin<double>(SmState*, double, cudaStream_t);
@@ -318,7 +325,7 @@ template void launch_convert<double, float>(const double*, float*, long long, cu
 template <typename T>
 void launch_sm_norm(long long n, const T* b, int steps, SmState* st, RedBuf rb, cudaStream_t s) {
     note_launch(s);
-    k_sm_norm<T><<<stream_blocks(n, Vec16<T>::W), 256, 0, s>>>(n, b, steps, st, rb);
+    launch_pdl(k_sm_norm<T>, stream_blocks(n, Vec16<T>::W), 256, 0, s, n, b, steps, st, rb);
 }
 
 template <typename TZ>
@@ -327,7 +334,7 @@ void launch_fg_combine(long long n, double* x, const Ptrs<TZ>& Z, int k, const F
     const int blocks = stream_blocks(n, 2);
     nq_dispatch(k, [&](auto NQc) {
         constexpr int NQ = decltype(NQc)::value;
-        k_fg_combine<TZ, NQ><<<blocks, 256, 0, s>>>(n, x, Z, k, fs);
+        launch_pdl(k_fg_combine<TZ, NQ>, blocks, 256, 0, s, n, x, Z, k, fs);
     });
 }
 

@@ -17,6 +17,35 @@
 
 namespace st {
 
+// Programmatic dependent launch.  Every kernel of the library starts with pdl_enter(): it
+// waits until the previous kernel in the stream has completed and its memory is visible, then
+// lets the next kernel be scheduled.  Launched through launch_pdl, the next kernel's launch and
+// block set-up overlap the tail of the current one (also inside captured graphs); launched
+// without the attribute, both instructions return at once.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+#endif
+
+extern bool g_pdl;  // environment ST_PDL=0 turns the launch attribute off
+
+template <typename... KP, typename... A>
+inline void launch_pdl(void (*k)(KP...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A&&... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = g_pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, k, static_cast<A&&>(args)...);
+}
+
 constexpr int kMaxLevels = 40;
 constexpr int kMaxSmooth = 16;     // Jacobi-GMRES steps per smoothing call
 constexpr int kMaxRestart = 32;    // FGMRES restart length
