@@ -338,7 +338,10 @@ def kernel_roofline(N, n_st_elems, apply_ms, apply_n, args):
 
 # DRAM read + write bytes of one launch, from an ncu capture of the current kernel version
 # (profiles/ names the capture); None when no capture of this version exists.
-TRAFFIC_PER_LAUNCH = {}
+TRAFFIC_PER_LAUNCH = {
+    # profiles/km_sm_applyw_sc_level0_c1_256x256x256.md: 99.23 MB read + 30.94 MB written
+    ("km_sm_applyw_sc", "c1_256x256x256_grf_extruded", "mixed"): 130173184,
+}
 
 
 def run_vcycles(args):
