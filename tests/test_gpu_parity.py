@@ -410,3 +410,34 @@ def test_coarse_solver_switches_to_gmres_above_the_dense_cap():
         assert rel_err(gm.state("T"), sol.s) < (1e-10 if precision == "fp64" else 1e-6)
     with pytest.raises(Exception):
         gpu_mesh(om, coarse_solver="dense")
+
+
+@pytest.mark.parametrize("nt", [1, 2, 3, 4, 5, 6])
+def test_few_time_planes_smoother_and_solve(nt):
+    """Time-constant 2-D designs with 1..6 time elements: every plane of the smoothing level
+    is a first, second, last or second-to-last plane, so the stencil smoother runs on its
+    boundary-plane path only (and n_t = 1 uses the single-slab class); the fine level has more
+    than 15,000 nodes, so FP32 smoothing uses the scaled stencil kernel as well."""
+    om = O.Mesh((180, 48), nt, mat=MATS["unitcap"], bc="patch_left", bc_width=0.2)
+    g = np.random.default_rng(30 + nt).random((48, 180))
+    gm = gpu_mesh(om, coarse_dof_cap=600)
+    gm.set_design(g)
+    levels = gm.levels()
+    assert len(levels) >= 2
+    A = O.assemble(om, g)
+    b = np.random.default_rng(31).standard_normal(om.n_nodes)
+    b[O.dirichlet_mask(om)] = 0
+    for tr in (False, True):
+        At = A.T.tocsr() if tr else A
+        ref = O.gmres_jacobi(At, b, np.zeros_like(b), 10)
+        x = torch.zeros(om.n_nodes, dtype=torch.float64, device="cuda")
+        gm.smooth(0, _dev(b), x, 10, True, "fp64", tr)
+        assert rel_err(x.cpu().numpy(), ref) < 1e-9
+        x32 = torch.zeros(om.n_nodes, dtype=torch.float32, device="cuda")
+        gm.smooth(0, _dev(b, torch.float32), x32, 10, True, "mixed", tr)
+        assert rel_err(x32.cpu().numpy(), ref) < 5e-3
+    sol = O.forward(om, g, "uniform", 1.0)
+    for precision in ("fp64", "mixed"):
+        st = gm.solve_forward(rtol=parity_rtol(sol.A, sol.s, sol.f), precision=precision, max_it=400)
+        assert st["converged"]
+        assert rel_err(gm.state("T"), sol.s) < 1e-10
