@@ -142,34 +142,6 @@ __global__ void __launch_bounds__(256) k_sm_start(OpL0<T> o0, OpLc<T> oc, const 
     }
 }
 
-template <int SD, typename T, int LV, bool TR>
-__global__ void __launch_bounds__(256) k_sm_apply(OpL0<T> o0, OpLc<T> oc, const T* __restrict__ dinv,
-                                                  Basis<T> U, T* __restrict__ w, int j, SmState* st,
-                                                  RedBuf rb) {
-    pdl_enter();
-    if (smt<T>(st)->stop || j >= smt<T>(st)->kdim) return;
-    const Geom& g = LV == 0 ? o0.g : oc.g;
-    LoadScaled<T> ld{U.u[j], dinv};
-    T accT[kMaxSmooth];
-#pragma unroll
-    for (int q = 0; q < kMaxSmooth; ++q) accT[q] = T(0);
-    ST_NODE_LOOP_BEGIN(g)
-    T v;
-    if (is_free<SD>(g, i_, j_, k_, n_))
-        v = op_row<SD, T, LV, TR>(o0, oc, i_, j_, k_, n_, ld);
-    else
-        v = ld(idx_);
-    w[idx_] = v;
-#pragma unroll
-    for (int q = 0; q < kMaxSmooth; ++q)
-        if (q <= j) accT[q] += v * U.u[q][idx_];
-    ST_NODE_LOOP_END
-    __shared__ double out[kMaxSmooth];
-    if (reduce_publish_t<T, kMaxSmooth>(accT, j + 1, rb, out)) {
-        if (threadIdx.x == 0 && threadIdx.y == 0) sm_apply_finish<T>(st, out, j);
-    }
-}
-
 // ---------------------------------------------------------------- coarsest solve
 template <typename T>
 __global__ void k_coarse_gemv(const double* __restrict__ Ainv, int n, const T* __restrict__ b, T* __restrict__ x) {
@@ -226,77 +198,6 @@ __device__ void fg_givens_column(FgState* fs, int j) {
 
 static_assert(kRedQ >= kMaxRestart && kRedQ >= kMaxSmooth, "partial-sum stride too small");
 
-template <int SD, typename TZ, bool TR>
-__global__ void __launch_bounds__(256) k_fg_apply_dots(OpL0<double> op, const TZ* __restrict__ z,
-                                                       TZ* __restrict__ zstore, double* __restrict__ w, VPtrs V,
-                                                       int j, FgState* fs, RedBuf rb) {
-    pdl_enter();
-    const Geom& g = op.g;
-    LoadPlain<double, TZ> ld{z};
-    double dots[32] = {0.0};  // j + 1 <= kMaxRestart = 32 dots in one pass
-    ST_NODE_LOOP_BEGIN(g)
-    double v;
-    if (is_free<SD>(g, i_, j_, k_, n_))
-        v = row_l0<SD, double, TR>(op, i_, j_, k_, n_, ld);
-    else
-        v = (double)z[idx_];
-    w[idx_] = v;
-    zstore[idx_] = z[idx_];
-#pragma unroll
-    for (int q = 0; q < 32; ++q)
-        if (q <= j) dots[q] += v * V.v[q][idx_];
-    ST_NODE_LOOP_END
-    __shared__ double out[32];
-    if (reduce_publish<32>(dots, j + 1, rb, out)) {
-        if (threadIdx.x == 0 && threadIdx.y == 0) fg_apply_finish(fs, out, j);
-    }
-}
-
-// pass 0: w -= sum h1_q v_q, new dots -> h1 (first projection kept in H)
-// pass 1: w -= sum h1_q v_q, norm; H column completed, Givens applied.
-__global__ void __launch_bounds__(256) k_fg_update(Geom g, double* __restrict__ w, VPtrs V, int j, int pass,
-                                                   FgState* fs, RedBuf rb) {
-    pdl_enter();
-    __shared__ double cf[32];
-    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    if (tid <= j) cf[tid] = fs->h1[tid];
-    __syncthreads();
-    double dots[32] = {0.0};
-    ST_NODE_LOOP_BEGIN(g)
-    double v = w[idx_];
-#pragma unroll
-    for (int q = 0; q < 32; ++q)
-        if (q <= j) v -= cf[q] * V.v[q][idx_];
-    w[idx_] = v;
-    if (pass == 0) {
-#pragma unroll
-        for (int q = 0; q < 32; ++q)
-            if (q <= j) dots[q] += v * V.v[q][idx_];
-    } else {
-        dots[0] += v * v;
-    }
-    ST_NODE_LOOP_END
-    __shared__ double out[32];
-    if (reduce_publish<32>(dots, pass == 0 ? j + 1 : 1, rb, out)) {
-        if (tid == 0) {
-            if (pass == 0) {
-                for (int q = 0; q <= j; ++q) {
-                    fs->H[q * kMaxRestart + j] = cf[q];
-                    fs->h1[q] = out[q];
-                }
-            } else {
-                for (int q = 0; q <= j; ++q) fs->H[q * kMaxRestart + j] += cf[q];
-                const double h = sqrt(out[0]);
-                fs->H[(j + 1) * kMaxRestart + j] = h;
-                fs->nrm = h;
-                fg_givens_column(fs, j);
-                fs->breakdown = !(h > 0.0);
-                fs->bad = !isfinite(h) || !isfinite(fs->res_est);
-            }
-        }
-    }
-}
-
 template <typename TZ>
 __global__ void __launch_bounds__(256) k_fg_normalize(Geom g, const double* __restrict__ w,
                                                       double* __restrict__ vn, TZ* __restrict__ bmg,
@@ -320,21 +221,6 @@ __global__ void k_fg_backsolve(FgState* fs, int k) {
         const double d = fs->H[q * kMaxRestart + q];
         fs->h1[q] = d != 0 ? a / d : 0.0;  // y stored in h1
     }
-}
-
-template <typename TZ>
-__global__ void __launch_bounds__(256) k_fg_update_x(Geom g, double* __restrict__ x, ZPtrs<TZ> Z, int k,
-                                                     const FgState* fs) {
-    pdl_enter();
-    __shared__ double y[kMaxRestart];
-    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    if (tid < k) y[tid] = fs->h1[tid];
-    __syncthreads();
-    ST_NODE_LOOP_BEGIN(g)
-    double v = x[idx_];
-    for (int q = 0; q < k; ++q) v += y[q] * (double)Z.z[q][idx_];
-    x[idx_] = v;
-    ST_NODE_LOOP_END
 }
 
 template <int SD, bool TR>
@@ -438,53 +324,6 @@ __global__ void __launch_bounds__(256) km_sm_start(Geom g, const T* __restrict__
     __shared__ double out[1];
     if (reduce_publish_t<T, 1>(acc, 1, rb, out)) {
         if (threadIdx.x == 0 && threadIdx.y == 0) sm_start_finish<T>(st, out[0], steps);
-    }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) km_sm_apply(Geom g, const T* __restrict__ coef,
-                                                   const unsigned char* __restrict__ dir, int chunk,
-                                                   const T* __restrict__ dinv, Basis<T> U, T* __restrict__ w, int j,
-                                                   SmState* st, RedBuf rb) {
-    pdl_enter();
-    if (smt<T>(st)->stop || j >= smt<T>(st)->kdim) return;
-    LoadScaled<T> ld{U.u[j], dinv};
-    T accT[kMaxSmooth];
-#pragma unroll
-    for (int q = 0; q < kMaxSmooth; ++q) accT[q] = T(0);
-    march2d<T>(g, coef, dir, ld, chunk, [&](long long q, T v) {
-        w[q] = v;
-#pragma unroll
-        for (int s = 0; s < kMaxSmooth; ++s)
-            if (s <= j) accT[s] += v * U.u[s][q];
-    });
-    __shared__ double out[kMaxSmooth];
-    if (reduce_publish_t<T, kMaxSmooth>(accT, j + 1, rb, out)) {
-        if (threadIdx.x == 0 && threadIdx.y == 0) sm_apply_finish<T>(st, out, j);
-    }
-}
-
-template <typename TZ>
-__global__ void __launch_bounds__(256) km_fg_apply_dots(Geom g, const double* __restrict__ coef,
-                                                        const unsigned char* __restrict__ dir, int chunk,
-                                                        const TZ* __restrict__ z, TZ* __restrict__ zstore,
-                                                        double* __restrict__ w, VPtrs V, int j, FgState* fs,
-                                                        RedBuf rb) {
-    pdl_enter();
-    LoadPlain<double, TZ> ld{z};
-    double dots[32];
-#pragma unroll
-    for (int q = 0; q < 32; ++q) dots[q] = 0.0;
-    march2d<double>(g, coef, dir, ld, chunk, [&](long long q, double v) {
-        w[q] = v;
-        zstore[q] = z[q];
-#pragma unroll
-        for (int s = 0; s < 32; ++s)
-            if (s <= j) dots[s] += v * V.v[s][q];
-    });
-    __shared__ double out[32];
-    if (reduce_publish<32>(dots, j + 1, rb, out)) {
-        if (threadIdx.x == 0 && threadIdx.y == 0) fg_apply_finish(fs, out, j);
     }
 }
 
@@ -684,11 +523,6 @@ static void record_timing_event(cudaEvent_t e, cudaStream_t s) {
     if (cudaEventRecordWithFlags(e, s, flags) != cudaSuccess) cudaGetLastError();
 }
 
-// Below this many nodes a level's Arnoldi step is latency bound: the fused stencil + dots
-// kernel (one launch fewer) is used; above it the apply, dots and update run as separate
-// bandwidth-efficient kernels.
-constexpr long long kSplitNodes = 0;
-
 template <int SD, typename T, int LV, bool TR>
 static void smooth_impl(const OpL0<T>& o0, const OpLc<T>& oc, const T* b, T* x, const T* dinv, Basis<T> U, T* w,
                         T* w2, int steps, bool zero_init, SmState* st, RedBuf rb, cudaStream_t s,
@@ -704,7 +538,6 @@ static void smooth_impl(const OpL0<T>& o0, const OpLc<T>& oc, const T* b, T* x, 
     if (zero_init) U.u[0] = const_cast<T*>(b);
     Ptrs<T> P{};
     for (int q = 0; q <= steps; ++q) P.p[q] = U.u[q];
-    const bool split = N >= kSplitNodes;
     // The fused Arnoldi step (one pass per step, halo recomputed) only pays on tiny, latency
     // bound levels; on large levels the split apply / dots / update kernels stream faster.
     constexpr long long kFusedMaxNodes = 15000;
@@ -739,25 +572,21 @@ static void smooth_impl(const OpL0<T>& o0, const OpLc<T>& oc, const T* b, T* x, 
             return;
         }
     }
+    // Arnoldi step j: w = A D^-1 u_j (stencil kernel), the dots (w, u_q), then the update
+    // u_{j+1} = w - sum h_q u_q with its norm, each a separate bandwidth-efficient kernel
     for (int j = 0; j < steps; ++j) {
         note_launch(s);
-        if (split) {
-            // optional timing events around the operator apply (event nodes when captured)
-            if (ev) record_timing_event(ev[2 * j], s);
-            if (march && sc)
-                launch_pdl(km_sm_applyw_sc<T>, mgrid, mblock, 0, s, g, sc + (TR ? 27 * g.plane : 0), coef, dir, mg.chunk,
-                                                           dinv, U.u[j], w, j, st);
-            else if (march)
-                launch_pdl(km_sm_applyw<T>, mgrid, mblock, 0, s, g, coef, dir, mg.chunk, dinv, U.u[j], w, j, st);
-            else
-                launch_pdl(k_sm_applyw<SD, T, LV, TR>, c.grid, c.block, 0, s, o0, oc, dinv, U.u[j], w, j, st);
-            if (ev) record_timing_event(ev[2 * j + 1], s);
-            launch_dots<T>(N, w, P, j + 1, j, 0, st, rb, s);
-        } else if (march) {
-            launch_pdl(km_sm_apply<T>, mgrid, mblock, 0, s, g, coef, dir, mg.chunk, dinv, U, w, j, st, rb);
-        } else {
-            launch_pdl(k_sm_apply<SD, T, LV, TR>, c.grid, c.block, 0, s, o0, oc, dinv, U, w, j, st, rb);
-        }
+        // optional timing events around the operator apply (event nodes when captured)
+        if (ev) record_timing_event(ev[2 * j], s);
+        if (march && sc)
+            launch_pdl(km_sm_applyw_sc<T>, mgrid, mblock, 0, s, g, sc + (TR ? 27 * g.plane : 0), coef, dir, mg.chunk,
+                       dinv, U.u[j], w, j, st);
+        else if (march)
+            launch_pdl(km_sm_applyw<T>, mgrid, mblock, 0, s, g, coef, dir, mg.chunk, dinv, U.u[j], w, j, st);
+        else
+            launch_pdl(k_sm_applyw<SD, T, LV, TR>, c.grid, c.block, 0, s, o0, oc, dinv, U.u[j], w, j, st);
+        if (ev) record_timing_event(ev[2 * j + 1], s);
+        launch_dots<T>(N, w, P, j + 1, j, 0, st, rb, s);
         launch_update<T>(N, w, U.u[j + 1], P, j, steps, 0, st, rb, s);
     }
     launch_sm_combine<T>(N, x, dinv, P, steps, zero_init, st, s);
