@@ -166,7 +166,8 @@ st_status st_synchronize(st_mesh* m);
 /* Set the density design (Sec. 2.2.1).  layout ST_DESIGN_EXTRUDED: count = nx*ny(*nz),
  * constant along time (Sec. 3.4.1); ST_DESIGN_SPACETIME: count = number of elements.
  * Values are clipped to [0, 1].  Builds the Galerkin coarse operators (J_{l+1} = P^T J_l P,
- * Sec. 3.2), the Jacobi diagonals and the inverse of the coarsest operator. */
+ * Sec. 3.2), the 27-point stencils of time-constant 2-D designs and, for the dense coarsest
+ * solve, the inverse of the coarsest operator; the Jacobi diagonals follow at the next solve. */
 st_status st_set_design(st_mesh* m, const double* gamma, int layout, size_t count, int mem);
 
 /* Forward solve J s = f (Sec. 3.1.2) with f from `q` (2-point Gauss in time per element).
@@ -189,8 +190,9 @@ st_status st_get_state(st_mesh* m, int which, double* out, size_t count, int mem
 st_status st_set_state(st_mesh* m, const double* s, size_t count, int mem);
 
 /* ---- Component entry points (used by the parity tests; same kernels as the solve) ----
- * precision selects the multigrid copy: ST_PREC_MIXED -> float vectors (level 0 applies
- * with the BF16 design), ST_PREC_FP64 -> double vectors.  level 0 with precision
+ * precision selects the multigrid copy: ST_PREC_MIXED -> float vectors (level 0 applies with
+ * FP32 stencils built from the FP64 design on time-constant 2-D designs, else with the BF16
+ * design), ST_PREC_FP64 -> double vectors.  level 0 with precision
  * ST_PREC_FP64 is also the FP64 operator of the outer Krylov solver.  All vectors are
  * device pointers of the level's node count. */
 st_status st_op_apply(st_mesh* m, int level, int precision, int transpose, const void* x, void* y);

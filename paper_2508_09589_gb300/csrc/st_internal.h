@@ -66,7 +66,7 @@ struct Geom {
     int bc;                        // ST_BC_*
     int face;                      // patch face axis (0: x = 0, 1: y = 0)
     int plo[3], phi[3];            // patch node range per spatial axis (inclusive)
-    int march_blocks;              // thread-block budget of the time-marching kernels (<= 0: kMaxBlocks)
+    int march_blocks;              // thread-block budget of the time-marching kernels (<= 0: the default, 912)
 };
 
 // Modified SIMP parameters (C = C_ins + dC g^p_c, k = k_ins + dk g^p_k).
