@@ -244,10 +244,17 @@ def run_native(args):
         }
     mesh.close()
     if rank == 0:
+        # the device-timed line is printed even if one of the auxiliary legs fails
         if args.serve_requests > 0:
-            line["serving"] = serving_bench(args)
+            try:
+                line["serving"] = serving_bench(args)
+            except Exception as e:  # noqa: BLE001
+                line["serving"] = {"error": f"{type(e).__name__}: {e}"}
         if args.cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(args.cpu_sample)
+            try:
+                line["cpu_baseline"] = cpu_baseline(args.cpu_sample)
+            except Exception as e:  # noqa: BLE001
+                line["cpu_baseline"] = {"error": f"{type(e).__name__}: {e}", "kind": "oracle"}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
