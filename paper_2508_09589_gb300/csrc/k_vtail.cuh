@@ -1,3 +1,4 @@
+#pragma once
 // Persistent coarse tail of the V-cycle (Sec. 3.2): the smoothing, residual, restriction,
 // coarsest solve and prolongation of every level from `first` down to the coarsest run in
 // ONE cooperative kernel, with grid-wide barriers between phases instead of separate
@@ -398,26 +399,24 @@ static int vtail_grid() {
     return cached;
 }
 
-template <typename T>
-int launch_vtail(int sd, bool tr, const VTail<T>* dev_pv, unsigned* bar, cudaStream_t s) {
+// One (dimension, precision) pair of the launcher; the four pairs are instantiated in four
+// translation units (k_vtail_2f.cu, k_vtail_2d.cu, k_vtail_3f.cu, k_vtail_3d.cu) so that the
+// large tail kernels compile in parallel.
+template <int SD, typename T>
+int launch_vtail_sd(bool tr, const VTail<T>* dev_pv, unsigned* bar, cudaStream_t s) {
     note_launch(s);
     cudaMemsetAsync(bar, 0, sizeof(unsigned), s);
     void* args[] = {(void*)&dev_pv};
     int nb = 0;
     cudaError_t e = cudaSuccess;
-    ST_SD_DISPATCH2(sd, {
-        if (tr) {
-            nb = vtail_grid<SD, T, true>();
-            e = cudaLaunchCooperativeKernel((const void*)k_vtail<SD, T, true>, dim3(nb), dim3(256), args, 0, s);
-        } else {
-            nb = vtail_grid<SD, T, false>();
-            e = cudaLaunchCooperativeKernel((const void*)k_vtail<SD, T, false>, dim3(nb), dim3(256), args, 0, s);
-        }
-    });
+    if (tr) {
+        nb = vtail_grid<SD, T, true>();
+        e = cudaLaunchCooperativeKernel((const void*)k_vtail<SD, T, true>, dim3(nb), dim3(256), args, 0, s);
+    } else {
+        nb = vtail_grid<SD, T, false>();
+        e = cudaLaunchCooperativeKernel((const void*)k_vtail<SD, T, false>, dim3(nb), dim3(256), args, 0, s);
+    }
     return e == cudaSuccess ? nb : -1;
 }
-
-template int launch_vtail<float>(int, bool, const VTail<float>*, unsigned*, cudaStream_t);
-template int launch_vtail<double>(int, bool, const VTail<double>*, unsigned*, cudaStream_t);
 
 }  // namespace st

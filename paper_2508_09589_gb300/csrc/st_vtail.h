@@ -38,8 +38,12 @@ struct VTail {
     VLevel<T> lv[kMaxLevels];
 };
 
+template <int SD, typename T>
+int launch_vtail_sd(bool tr, const VTail<T>* dev_pv, unsigned* bar, cudaStream_t s);
 template <typename T>
-int launch_vtail(int sd, bool tr, const VTail<T>* dev_pv, unsigned* bar, cudaStream_t s);
+inline int launch_vtail(int sd, bool tr, const VTail<T>* dev_pv, unsigned* bar, cudaStream_t s) {
+    return sd == 2 ? launch_vtail_sd<2, T>(tr, dev_pv, bar, s) : launch_vtail_sd<3, T>(tr, dev_pv, bar, s);
+}
 
 }  // namespace st
 
