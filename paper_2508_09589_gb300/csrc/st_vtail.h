@@ -1,4 +1,4 @@
-// Descriptor of the persistent coarse tail of the V-cycle (k_vtail.cu), kept in device memory.
+// Descriptor of the persistent coarse tail of the V-cycle (k_vtail.cuh, instantiated in k_vtail_*.cu), kept in device memory.
 #pragma once
 
 #include "st_internal.h"
