@@ -427,7 +427,7 @@ def main():
     ap.add_argument("--workload", default=W.C1.name, choices=sorted(W.WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=1)
-    ap.add_argument("--cpu-sample", default="24")
+    ap.add_argument("--cpu-sample", default="34", help="oracle sample n (n^3 mesh, about 10-15 s of CPU work)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--serve-requests", type=int, default=48, help="serving leg size (0 skips it)")
     ap.add_argument("--serve-slots", type=int, default=4, help="concurrent solves in the server")
