@@ -601,17 +601,26 @@ def build_mg(m: Mesh, gamma: np.ndarray, levels: List[Level]) -> List[MGLevel]:
 # from the current iterate; the coarsest level is solved directly.
 # ----------------------------------------------------------------------------
 def gmres_jacobi(A: sp.spmatrix, b: np.ndarray, x0: np.ndarray, m: int = 10,
-                 breakdown_tol: float = 0.0) -> np.ndarray:
+                 breakdown_tol: float = 0.0, dtype=np.float64) -> np.ndarray:
     """m steps of GMRES on A D^{-1} y = b - A x0, x = x0 + D^{-1} y (Arnoldi with
-    modified Gram-Schmidt, least squares by numpy.linalg.lstsq)."""
-    dinv = 1.0 / A.diagonal()
+    modified Gram-Schmidt, least squares by numpy.linalg.lstsq).
+
+    dtype selects the arithmetic: float64 (the oracle proper) or float32, which runs the
+    same algorithm with every vector operation in IEEE single precision (matrix entries,
+    D^{-1}, matrix-vector products, dot products, norms and updates all float32; the
+    (m+1) x m least-squares problem is solved by numpy in float64 and rounded back), to
+    measure how far a single-precision smoother lands from the float64 one."""
+    A = sp.csr_matrix(A).astype(dtype)
+    b = np.asarray(b).astype(dtype)
+    x0 = np.asarray(x0).astype(dtype)
+    dinv = (dtype(1.0) / A.diagonal()).astype(dtype)
     r = b - A @ x0
     beta = np.linalg.norm(r)
     if beta == 0.0:
         return x0.copy()
     n = b.size
-    V = np.zeros((m + 1, n))
-    H = np.zeros((m + 1, m))
+    V = np.zeros((m + 1, n), dtype=dtype)
+    H = np.zeros((m + 1, m), dtype=dtype)
     V[0] = r / beta
     k = m
     for j in range(m):
@@ -624,34 +633,64 @@ def gmres_jacobi(A: sp.spmatrix, b: np.ndarray, x0: np.ndarray, m: int = 10,
             k = j + 1
             break
         V[j + 1] = w / H[j + 1, j]
-    e1 = np.zeros(k + 1)
+    e1 = np.zeros(k + 1, dtype=dtype)
     e1[0] = beta
-    y = np.linalg.lstsq(H[: k + 1, :k], e1, rcond=None)[0]
+    y = np.linalg.lstsq(H[: k + 1, :k], e1, rcond=None)[0].astype(dtype)
     return x0 + dinv * (V[:k].T @ y)
 
 
 def vcycle(mg: List[MGLevel], b: np.ndarray, l: int = 0, nsmooth: int = 10,
-           transpose: bool = False) -> np.ndarray:
+           transpose: bool = False, dtype=np.float64) -> np.ndarray:
     """One V-cycle for A_l x = b (A_l^T for transpose=True, which uses the same
-    hierarchy since (P^T A P)^T = P^T A^T P)."""
+    hierarchy since (P^T A P)^T = P^T A^T P).
+
+    dtype = float32 runs the smoothing, residuals and transfers in single precision and
+    keeps the coarsest solve in float64 (its result rounded to float32), the precision
+    split of a mixed-precision multigrid; float64 is the oracle proper."""
     A = mg[l].A.T.tocsr() if transpose else mg[l].A
+    b = np.asarray(b).astype(dtype)
     if l == len(mg) - 1:
-        return np.linalg.solve(A.toarray(), b)
-    x = gmres_jacobi(A, b, np.zeros_like(b), nsmooth)
+        return np.linalg.solve(A.toarray(), b.astype(np.float64)).astype(dtype)
+    A = sp.csr_matrix(A).astype(dtype)
+    x = gmres_jacobi(A, b, np.zeros_like(b), nsmooth, dtype=dtype)
     r = b - A @ x
-    Pt = mg[l].Pt
-    xc = vcycle(mg, Pt.T @ r, l + 1, nsmooth, transpose)
+    Pt = mg[l].Pt.astype(dtype)
+    xc = vcycle(mg, Pt.T @ r, l + 1, nsmooth, transpose, dtype)
     x = x + Pt @ xc
-    return gmres_jacobi(A, b, x, nsmooth)
+    return gmres_jacobi(A, b, x, nsmooth, dtype=dtype)
+
+
+def abs_operator(m: Mesh, gamma: np.ndarray, ngauss: int = 3) -> sp.csr_matrix:
+    """Element-wise absolute operator |J|_elem = sum_e |C_e Jc| + |k_e Jk| (entry-wise
+    absolute values of each element's capacity and conductivity parts, summed without
+    cancellation), with the identity on prescribed rows and columns as in assemble().
+    It bounds the rounding error of any evaluation of J x that forms the element terms
+    and adds them: |fl(J x) - J x| <= c u |J|_elem |x| (componentwise, c a small multiple
+    of the number of terms, u the unit roundoff)."""
+    ge = element_gamma(m, gamma)
+    C = np.abs(simp_C(m.mat, ge))
+    k = np.abs(simp_k(m.mat, ge))
+    Jc, Jk = element_matrices(m.h, m.dt, ngauss)
+    conn = element_connectivity(m)
+    nv = m.nv
+    rows = np.repeat(conn, nv, axis=1).reshape(-1)
+    cols = np.tile(conn, (1, nv)).reshape(-1)
+    vals = (C[:, None, None] * np.abs(Jc)[None] + k[:, None, None] * np.abs(Jk)[None]).reshape(-1)
+    B = sp.csr_matrix((vals, (rows, cols)), shape=(m.n_nodes, m.n_nodes))
+    return constrain(B, dirichlet_mask(m))
 
 
 # ----------------------------------------------------------------------------
 # Single rows of the constrained system, for checks on meshes too large to assemble.
 # ----------------------------------------------------------------------------
-def apply_rows(m: Mesh, gamma: np.ndarray, x: np.ndarray, rows: np.ndarray) -> np.ndarray:
+def apply_rows(m: Mesh, gamma: np.ndarray, x: np.ndarray, rows: np.ndarray,
+               absolute: bool = False) -> np.ndarray:
     """(A x)_i for the listed nodes i, element by element: the sum over the elements that
     contain node i of row a(i) of C_e Jc + k_e Jk applied to the element's (masked) values;
-    prescribed rows are the identity."""
+    prescribed rows are the identity.  absolute=True gives the same rows of abs_operator
+    applied to |x| instead (|C_e Jc| + |k_e Jk| per element, no cancellation)."""
+    if absolute:
+        x = np.abs(x)
     sd = m.sd
     shape = m.node_shape
     dm = dirichlet_mask(m)
@@ -686,6 +725,9 @@ def apply_rows(m: Mesh, gamma: np.ndarray, x: np.ndarray, rows: np.ndarray) -> n
                 q = np.ravel_multi_index(tuple(bi), shape)
                 if dm[q]:
                     continue
-                acc += (C * Jc[a, b] + k * Jk[a, b]) * x[q]
+                if absolute:
+                    acc += (abs(C * Jc[a, b]) + abs(k * Jk[a, b])) * x[q]
+                else:
+                    acc += (C * Jc[a, b] + k * Jk[a, b]) * x[q]
         out[r] = acc
     return out

@@ -547,6 +547,9 @@ def test_apply_rows_matches_assembled_operator():
         x = rng.random(m.n_nodes)
         rows = np.arange(m.n_nodes)
         np.testing.assert_allclose(O.apply_rows(m, g, x, rows), A @ x, rtol=1e-13, atol=1e-15)
+        xs = x - 0.5  # both signs
+        np.testing.assert_allclose(O.apply_rows(m, g, xs, rows, absolute=True),
+                                   O.abs_operator(m, g) @ np.abs(xs), rtol=1e-13, atol=1e-15)
 
 
 @pytest.mark.parametrize("ns,nt,kind", [((5, 4), 6, "sin_t"), ((3, 2, 4), 3, "uniform")])
@@ -558,3 +561,150 @@ def test_source_rows_match_assembled_source(ns, nt, kind):
     f = O.assemble_source(m, Q)
     rows = np.arange(m.n_nodes)
     np.testing.assert_allclose(O.source_rows(m, Q, rows), f, rtol=1e-13, atol=1e-16)
+
+
+# ---------------------------------------------------------------- V-cycle structure (Sec. 3.2)
+def _minres_smooth(A, b, x0, m):
+    """Independent statement of m GMRES steps with right Jacobi preconditioning: the x0 + D^-1 K y
+    of least residual norm over the Krylov space K = span{r0, (A D^-1) r0, ..., (A D^-1)^(m-1) r0}
+    (dense, power basis orthonormalised by a QR factorisation, then numpy least squares)."""
+    A = np.asarray(A.toarray() if sp.issparse(A) else A)
+    dinv = 1.0 / np.diag(A)
+    r0 = b - A @ x0
+    K = [r0]
+    for _ in range(m - 1):
+        K.append(A @ (dinv * K[-1]))
+    Q, _ = np.linalg.qr(np.array(K).T)
+    y = np.linalg.lstsq(A @ (dinv[:, None] * Q), r0, rcond=None)[0]
+    return x0 + dinv * (Q @ y)
+
+
+def _two_level_hand(A, Ac, Pt, b, m):
+    """The two-level cycle written out step by step from Sec. 3.2: pre-smoothing from zero,
+    residual, restriction by Pt^T, exact coarse solve, prolongation by Pt, post-smoothing from
+    the corrected iterate."""
+    A = A.toarray()
+    x = _minres_smooth(A, b, np.zeros_like(b), m)
+    r = b - A @ x
+    ec = np.linalg.solve(Ac.toarray(), Pt.toarray().T @ r)
+    x = x + Pt.toarray() @ ec
+    return _minres_smooth(A, b, x, m)
+
+
+@pytest.mark.parametrize("transpose", [False, True])
+def test_vcycle_two_level_equals_hand_composition(transpose):
+    """A two-level V-cycle on a 4x4x4 mesh equals the cycle composed by hand from an
+    independently computed minimal-residual smoother.  Post-smoothing started from zero
+    instead of the corrected iterate, a missing post-smoothing, a sign error in the coarse
+    correction, or an adjoint cycle that transposes only the fine level all change the result
+    far beyond the tolerance (each was planted in a copy of the cycle and fails here)."""
+    mat = O.Material(C_ins=1.0, C_con=1.0, k_ins=1e-3, k_con=1.0, p_c=1, p_k=3)
+    m = O.Mesh((4, 4), 4, mat=mat, bc="patch_left", bc_width=0.5)
+    g = np.random.default_rng(21).random((4, 4))
+    levels = O.hierarchy(m, n_levels=2)
+    assert len(levels) == 2
+    mg = O.build_mg(m, g, levels)
+    b = np.random.default_rng(22).standard_normal(m.n_nodes)
+    b[mg[0].mask] = 0
+    A = mg[0].A.T.tocsr() if transpose else mg[0].A
+    Ac = mg[1].A.T.tocsr() if transpose else mg[1].A
+    for nsm, tol in ((2, 1e-11), (3, 1e-10)):
+        ref = _two_level_hand(A, Ac, mg[0].Pt, b, nsm)
+        got = O.vcycle(mg, b, nsmooth=nsm, transpose=transpose)
+        assert np.abs(got - ref).max() <= tol * np.abs(ref).max(), nsm
+    # the transposed cycle differs from the forward one (the operator is not symmetric)
+    if transpose:
+        fwd = O.vcycle(mg, b, nsmooth=2)
+        assert np.abs(fwd - O.vcycle(mg, b, nsmooth=2, transpose=True)).max() > 1e-6 * np.abs(fwd).max()
+
+
+def test_vcycle_transposed_one_level_is_the_transposed_solve():
+    """On a one-level hierarchy the transposed V-cycle is the coarsest solve with A^T."""
+    m = O.Mesh((5, 4), 6, mat=O.Material(), bc="patch_bottom", bc_width=0.4)
+    g = np.random.default_rng(23).random((4, 5))
+    one = O.build_mg(m, g, O.hierarchy(m)[:1])
+    b = np.random.default_rng(24).standard_normal(m.n_nodes)
+    A = one[0].A
+    ref = np.linalg.solve(A.toarray().T, b)
+    np.testing.assert_allclose(O.vcycle(one, b, transpose=True), ref, rtol=1e-10, atol=1e-13 * np.abs(ref).max())
+    assert np.abs(O.vcycle(one, b) - ref).max() > 1e-6 * np.abs(ref).max()
+
+
+def test_transposed_vcycle_contracts_on_the_transposed_operator():
+    """Preconditioned Richardson with the transposed cycle converges on A^T lambda = b (the
+    adjoint system of Sec. 3.3.3): at least 2x residual reduction per cycle."""
+    mat = O.Material(C_ins=1.0, C_con=1.0, k_ins=1e-3, k_con=1.0, p_c=1, p_k=3)
+    m = O.Mesh((16, 16), 16, mat=mat)
+    g = np.random.default_rng(6).random((16, 16))
+    mg = O.build_mg(m, g, O.hierarchy(m, coarse_cap=400))
+    At = mg[0].A.T.tocsr()
+    b = O.assemble_source(m, O.source_fn("uniform"))
+    x = np.zeros_like(b)
+    res = [np.linalg.norm(b)]
+    for _ in range(4):
+        x = x + O.vcycle(mg, b - At @ x, transpose=True)
+        res.append(np.linalg.norm(b - At @ x))
+    assert all(res[i + 1] < 0.5 * res[i] for i in range(4)), res
+
+
+# ---------------------------------------------------------------- single-precision runs
+def test_float32_smoother_runs_in_single_precision_and_tracks_float64():
+    """The float32 variant of the smoother returns float32 values that differ from the
+    float64 run by more than float64 rounding (so it really computes in single precision)
+    but by no more than a few hundred float32 unit roundoffs (so it is the same algorithm)."""
+    m = O.Mesh((6, 6), 6, mat=O.Material(), bc="patch_left", bc_width=0.4)
+    A = O.assemble(m, np.random.default_rng(4).random((6, 6)))
+    rng = np.random.default_rng(9)
+    b = rng.standard_normal(m.n_nodes); b[O.dirichlet_mask(m)] = 0
+    x0 = rng.standard_normal(m.n_nodes) * 0.1
+    x64 = O.gmres_jacobi(A, b, x0, 6)
+    x32 = O.gmres_jacobi(A, b, x0, 6, dtype=np.float32)
+    assert x32.dtype == np.float32
+    err = np.abs(x32.astype(np.float64) - x64).max() / np.abs(x64).max()
+    assert 1e-10 < err < 300 * 2.0 ** -24, err
+    # the single-precision V-cycle keeps the same structure and contracts as well
+    mat = O.Material(C_ins=1.0, C_con=1.0, k_ins=1e-3, k_con=1.0, p_c=1, p_k=3)
+    mm = O.Mesh((16, 16), 16, mat=mat)
+    mg = O.build_mg(mm, np.random.default_rng(6).random((16, 16)), O.hierarchy(mm, coarse_cap=400))
+    f = O.assemble_source(mm, O.source_fn("uniform"))
+    v64 = O.vcycle(mg, f)
+    v32 = O.vcycle(mg, f, dtype=np.float32)
+    assert v32.dtype == np.float32
+    e = np.abs(v32.astype(np.float64) - v64).max() / np.abs(v64).max()
+    assert 1e-10 < e < 1e-3, e
+    r0 = np.linalg.norm(f)
+    assert np.linalg.norm(f - mg[0].A @ v32.astype(np.float64)) < 0.5 * r0
+
+
+def test_abs_operator_bounds_the_operator_and_is_exact_on_one_element():
+    """|J|_elem >= |J| entry by entry, with equality on one element when only the capacity part
+    or only the conductivity part is present (nothing is summed), and it bounds the float32
+    evaluation error of the element-by-element product."""
+    mat = O.Material()
+    g1 = np.array([[0.37]])
+    for part in (O.Material(C_ins=0.5, C_con=1.0, k_ins=0.0, k_con=0.0), O.Material(C_ins=0.0, C_con=0.0)):
+        one = O.Mesh((1, 1), 1, mat=part, bc="none", ext=(0.3, 0.7))
+        np.testing.assert_allclose(O.abs_operator(one, g1).toarray(), np.abs(O.assemble(one, g1).toarray()),
+                                   rtol=1e-15, atol=0)
+    m = O.Mesh((5, 4), 3, mat=mat, bc="patch_left", bc_width=0.5)
+    g = np.random.default_rng(25).random((3, 4, 5))
+    A = O.assemble(m, g).toarray()
+    B = O.abs_operator(m, g).toarray()
+    assert np.all(B >= np.abs(A) - 1e-15 * np.abs(A).max())
+    assert (B > np.abs(A) + 1e-12 * np.abs(A).max()).any()  # cancellation exists between elements
+    # a float32 element-by-element product stays within 16 u32 |J|_elem |x| per row
+    x = np.random.default_rng(26).standard_normal(m.n_nodes)
+    ge = O.element_gamma(m, g)
+    Jc, Jk = O.element_matrices(m.h, m.dt)
+    conn = O.element_connectivity(m)
+    dm = O.dirichlet_mask(m)
+    xm = np.where(dm, 0.0, x).astype(np.float32)
+    y = np.zeros(m.n_nodes, dtype=np.float32)
+    Cs = O.simp_C(mat, ge).astype(np.float32)
+    ks = O.simp_k(mat, ge).astype(np.float32)
+    for e in range(m.n_elem):
+        Ee = Cs[e] * Jc.astype(np.float32) + ks[e] * Jk.astype(np.float32)
+        np.add.at(y, conn[e], (Ee @ xm[conn[e]]).astype(np.float32))
+    y = np.where(dm, x.astype(np.float32), y).astype(np.float64)
+    err = np.abs(y - A @ x)
+    assert np.all(err <= 16 * 2.0 ** -24 * (B @ np.abs(x)) + 1e-30)
