@@ -51,6 +51,7 @@ typedef int st_status;
 #define ST_ERR_BUSY (-7)           /* request refused by admission control */
 #define ST_ERR_STATE (-8)          /* call out of order (e.g. solve before set_design) */
 #define ST_ERR_NOT_FOUND (-9)      /* unknown ticket */
+#define ST_ERR_CANCELLED (-10)     /* the request was cancelled before it was admitted */
 
 enum { ST_BC_PATCH_LEFT = 0, ST_BC_PATCH_BOTTOM = 1, ST_BC_ALL_WALLS = 2, ST_BC_NONE = 3 };
 enum { ST_DESIGN_EXTRUDED = 0, ST_DESIGN_SPACETIME = 1 };
@@ -165,13 +166,17 @@ st_status st_synchronize(st_mesh* m);
 
 /* Set the density design (Sec. 2.2.1).  layout ST_DESIGN_EXTRUDED: count = nx*ny(*nz),
  * constant along time (Sec. 3.4.1); ST_DESIGN_SPACETIME: count = number of elements.
- * Values are clipped to [0, 1].  Builds the Galerkin coarse operators (J_{l+1} = P^T J_l P,
+ * Values are clipped to [0, 1]; a NaN or infinite value returns ST_ERR_NUMERIC and leaves the
+ * mesh without a design (solves return ST_ERR_STATE until a valid design is set).  Builds the Galerkin coarse operators (J_{l+1} = P^T J_l P,
  * Sec. 3.2), the 27-point stencils of time-constant 2-D designs and, for the dense coarsest
  * solve, the inverse of the coarsest operator; the Jacobi diagonals follow at the next solve. */
 st_status st_set_design(st_mesh* m, const double* gamma, int layout, size_t count, int mem);
 
 /* Forward solve J s = f (Sec. 3.1.2) with f from `q` (2-point Gauss in time per element).
- * ST_ERR_NOT_CONVERGED keeps the best iterate and fills stats. */
+ * ST_ERR_NOT_CONVERGED keeps the best iterate and fills stats.  Non-finite source parameters
+ * return ST_ERR_ARG; a NaN or Inf that reaches the residual (for example from a warm-start
+ * state) returns ST_ERR_NUMERIC.  ST_ERR_TIMEOUT: a bounded grid-barrier wait of the opt-in
+ * persistent coarse V-cycle tail gave up (the result is then not to be trusted). */
 st_status st_solve_forward(st_mesh* m, const st_source* q, const st_options* o, st_stats* stats);
 
 /* Objective phi (*phi_out) from the stored state and the adjoint solve J^T Lambda =
@@ -265,6 +270,11 @@ st_status st_submit(st_server* s, const st_request* r, uint64_t* ticket);
  * sensitivities if requested (count = design size).  A finished ticket is released by the
  * first st_poll that returns done = 1. */
 st_status st_poll(st_server* s, uint64_t ticket, st_result* out, double* grad, size_t count, int* done);
+/* Cancel a request that is still queued (not yet admitted to a slot).  Returns ST_OK and
+ * marks it finished with result status ST_ERR_CANCELLED (release it with st_poll as usual);
+ * ST_ERR_BUSY if it is already running on the device (it then runs to completion),
+ * ST_ERR_STATE if it has finished, ST_ERR_NOT_FOUND for an unknown or released ticket. */
+st_status st_cancel(st_server* s, uint64_t ticket);
 /* Number of kernels this library has launched in the process so far (kernels inside
  * replayed CUDA graphs included); a diagnostic for benchmarks. */
 long long st_kernel_launches(void);

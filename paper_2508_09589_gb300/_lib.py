@@ -13,7 +13,8 @@ LIB_PATH = os.path.join(HERE, "libst.so")
 
 ST_OK = 0
 STATUS = {0: "ST_OK", -1: "ST_ERR_ARG", -2: "ST_ERR_OOM", -3: "ST_ERR_NOT_CONVERGED", -4: "ST_ERR_NUMERIC",
-          -5: "ST_ERR_TIMEOUT", -6: "ST_ERR_CUDA", -7: "ST_ERR_BUSY", -8: "ST_ERR_STATE", -9: "ST_ERR_NOT_FOUND"}
+          -5: "ST_ERR_TIMEOUT", -6: "ST_ERR_CUDA", -7: "ST_ERR_BUSY", -8: "ST_ERR_STATE", -9: "ST_ERR_NOT_FOUND",
+          -10: "ST_ERR_CANCELLED"}
 BC = {"patch_left": 0, "patch_bottom": 1, "all_walls": 2, "none": 3}
 LAYOUT = {"extruded": 0, "spacetime": 1}
 MEM_HOST, MEM_DEVICE = 0, 1
@@ -118,6 +119,7 @@ SIGNATURES = {
     "st_server_create": (C.c_int, [C.POINTER(ServerDesc), C.POINTER(C.c_void_p)]),
     "st_server_destroy": (C.c_int, [C.c_void_p]),
     "st_submit": (C.c_int, [C.c_void_p, C.POINTER(Request), C.POINTER(C.c_uint64)]),
+    "st_cancel": (C.c_int, [C.c_void_p, C.c_uint64]),
     "st_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(Result), C.c_void_p, C.c_size_t, C.POINTER(C.c_int)]),
     "st_footprint_bytes": (C.c_longlong, [C.POINTER(MeshDesc), C.c_int, C.c_int]),
     "st_kernel_launches": (C.c_longlong, []),

@@ -330,6 +330,12 @@ class Server:
         self._keep[t.value] = arr.size
         return t.value
 
+    def cancel(self, ticket: int) -> int:
+        """Cancel a queued request (st_cancel).  Returns 0 when it was removed from the queue
+        (its result then carries status ST_ERR_CANCELLED), else the library's status code:
+        -7 running, -8 finished, -9 unknown."""
+        return int(L.lib().st_cancel(self._h, C.c_uint64(ticket)))
+
     def poll(self, ticket: int):
         """(done, result dict or None, gradient or None)."""
         res = L.Result()

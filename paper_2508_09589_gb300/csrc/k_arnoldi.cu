@@ -12,6 +12,8 @@
 // staged itself, so the ring needs no block barrier.
 #include <math.h>
 
+#include <mutex>
+
 #include "st_device.cuh"
 
 namespace st {
@@ -238,11 +240,11 @@ static void launch_arnoldi_nq(const Geom& g, const float* coef, const unsigned c
     dim3 grid, block;
     const MarchGrid mg = march_grid(g, grid, block);
     const size_t bytes = sizeof(float) * ArnSmem<NQ>::floats;
-    static bool attr = false;
-    if (!attr) {
+    // once per process (the server's slot threads reach this concurrently)
+    static std::once_flag attr;
+    std::call_once(attr, [&] {
         cudaFuncSetAttribute(km_arnoldi<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        attr = true;
-    }
+    });
     launch_pdl(km_arnoldi<NQ>, grid, block, bytes, s, g, coef, dir, mg.chunk, dinv, U, w_in, w_out, j, st, rb);
 }
 

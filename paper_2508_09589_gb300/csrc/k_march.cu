@@ -63,6 +63,41 @@ __global__ void k_stencil_build(OpL0<double> o0, OpLc<double> oc, double* __rest
         }
 }
 
+// Jacobi diagonal of a stencil level: the centre coefficient (k = 13) of the row's plane class,
+// 1 on prescribed rows.  Taken from the stencil itself, so that D is the diagonal of exactly
+// the operator the time-marching kernels apply (in FP32 that operator comes from the FP64
+// design, not from the BF16 copy the element-wise FP32 rows read).
+template <typename T>
+__global__ void __launch_bounds__(256) k_stencil_diag(Geom g, const T* __restrict__ coef,
+                                                      const unsigned char* __restrict__ dir, T* __restrict__ d,
+                                                      int invert) {
+    pdl_enter();
+    const long long P = (long long)g.nx1 * g.ny1;
+    const int nt = g.net;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.nnodes;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int n = (int)(q / P);
+        const long long p = q - (long long)n * P;
+        T v = T(1);
+        if (n > 0 && !dir[p]) {
+            const int cls = (n == 1) ? (nt == 1 ? 3 : 0) : (n == nt ? 2 : 1);
+            v = coef[((long long)cls * 27 + 13) * P + p];
+        }
+        d[q] = invert ? T(1) / v : v;
+    }
+}
+
+template <typename T>
+void launch_stencil_diag(const Geom& g, const T* coef, const unsigned char* dir, T* d, bool invert, cudaStream_t s) {
+    note_launch(s);
+    long long blocks = (g.nnodes + 255) / 256;
+    if (blocks > 4 * 1216) blocks = 4 * 1216;
+    launch_pdl(k_stencil_diag<T>, (int)(blocks > 0 ? blocks : 1), 256, 0, s, g, coef, dir, d, invert ? 1 : 0);
+}
+template void launch_stencil_diag<float>(const Geom&, const float*, const unsigned char*, float*, bool, cudaStream_t);
+template void launch_stencil_diag<double>(const Geom&, const double*, const unsigned char*, double*, bool,
+                                          cudaStream_t);
+
 // Interior rows of a stencil level apply A D^-1 with D^-1 of interior planes, which is the
 // same on every interior plane: fold it into the interior-class stencil of both orientations.
 // Rows of prescribed spatial nodes become the identity row scaled by their own D^-1.

@@ -464,6 +464,10 @@ void launch_apply_lc(int sd, const OpLc<T>& op, bool tr, const T* x, T* y, cudaS
 }
 template <typename T>
 void launch_diag_l0(int sd, const OpL0<T>& op, T* d, bool invert, cudaStream_t s) {
+    if (sd == 2 && op.st_dir) {
+        launch_stencil_diag<T>(op.g, op.st_coef[0], op.st_dir, d, invert, s);
+        return;
+    }
     note_launch(s);
     const LaunchCfg c = node_cfg(op.g);
     const OpLc<T> oc = dummy_lc<T>(op.g);
@@ -471,6 +475,10 @@ void launch_diag_l0(int sd, const OpL0<T>& op, T* d, bool invert, cudaStream_t s
 }
 template <typename T>
 void launch_diag_lc(int sd, const OpLc<T>& op, T* d, bool invert, cudaStream_t s) {
+    if (sd == 2 && op.st_dir) {
+        launch_stencil_diag<T>(op.g, op.st_coef[0], op.st_dir, d, invert, s);
+        return;
+    }
     note_launch(s);
     const LaunchCfg c = node_cfg(op.g);
     const OpL0<T> o0 = dummy_l0<T>(op.g);

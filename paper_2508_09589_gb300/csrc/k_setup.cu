@@ -19,13 +19,18 @@ namespace st {
         }                         \
     } while (0)
 
+// Clip the design to [0, 1] and keep FP64 and BF16 copies; a NaN or infinite value sets
+// *bad (the caller rejects the design) and is stored as 0.
 __global__ void k_design_cast(const double* __restrict__ in, double* __restrict__ g64,
-                              __nv_bfloat16* __restrict__ g16, long long n) {
+                              __nv_bfloat16* __restrict__ g16, long long n, int* __restrict__ bad) {
     pdl_enter();
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
         double v = in[q];
+        if (!isfinite(v)) {
+            *bad = 1;
+            v = 0.0;
+        }
         v = v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
-        if (!(v == v)) v = 0.0;
         g64[q] = v;
         g16[q] = __double2bfloat16(v);
     }
@@ -357,10 +362,10 @@ __global__ void k_sens(OpL0<double> op, const double* __restrict__ s, const doub
 }
 
 // ---------------------------------------------------------------- wrappers
-void launch_design_cast(const double* in, double* g64, __nv_bfloat16* g16, long long n, cudaStream_t s) {
+void launch_design_cast(const double* in, double* g64, __nv_bfloat16* g16, long long n, int* bad, cudaStream_t s) {
     note_launch(s);
     const int blocks = (int)((n + 255) / 256 < 65536 ? (n + 255) / 256 : 65536);
-    launch_pdl(k_design_cast, blocks > 0 ? blocks : 1, 256, 0, s, in, g64, g16, n);
+    launch_pdl(k_design_cast, blocks > 0 ? blocks : 1, 256, 0, s, in, g64, g16, n, bad);
 }
 
 void launch_to_float(const double* in, float* out, long long n, cudaStream_t s) {

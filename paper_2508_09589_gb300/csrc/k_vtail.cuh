@@ -11,6 +11,8 @@
 #include <math.h>
 #include <stddef.h>
 
+#include <mutex>
+
 #include "st_device.cuh"
 #include "st_vtail.h"
 
@@ -23,6 +25,7 @@ struct GBar {
     int* err;
     unsigned long long* trace;
     int trace_cap;
+    unsigned spin_limit;           // polls before a barrier wait gives up
 };
 
 __device__ __forceinline__ void gbar(GBar& b) {
@@ -36,7 +39,7 @@ __device__ __forceinline__ void gbar(GBar& b) {
         for (;;) {
             const unsigned v = *((volatile unsigned*)b.ctr);
             if (v >= target) break;
-            if (++spins > (1u << 24)) {  // about a second: give up, report, continue
+            if (++spins > b.spin_limit) {  // default 2^24 polls, about a second: give up, report, continue
                 atomicExch(b.err, 1);
                 break;
             }
@@ -313,7 +316,7 @@ __global__ void __launch_bounds__(256) k_vtail(const VTail<T>* __restrict__ pvp)
         __syncthreads();
     };
     __syncthreads();
-    GBar bar{pv.bar, gridDim.x, 0u, pv.err, pv.trace, pv.trace_cap};
+    GBar bar{pv.bar, gridDim.x, 0u, pv.err, pv.trace, pv.trace_cap, pv.spin_limit};
     if (pv.trace && blockIdx.x == 0 && threadIdx.x == 0) {
         unsigned long long t;
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -385,17 +388,21 @@ __global__ void __launch_bounds__(256) k_vtail(const VTail<T>* __restrict__ pvp)
 
 template <int SD, typename T, bool TR>
 static int vtail_grid() {
-    static int cached = 0;  // blocks of one full co-resident wave (device 0 of this process)
-    if (cached) return cached;
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_vtail<SD, T, TR>, 256, 0);
-    if (per < 1) per = 1;
-    if (per > 2) per = 2;
-    long long nb = (long long)sms * per;
-    if (nb > kMaxBlocks) nb = kMaxBlocks;
-    cached = (int)nb;
+    // blocks of one full co-resident wave (the first device that asks; computed once per
+    // process, also when several server slot threads reach it together)
+    static std::once_flag once;
+    static int cached = 0;
+    std::call_once(once, [] {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_vtail<SD, T, TR>, 256, 0);
+        if (per < 1) per = 1;
+        if (per > 2) per = 2;
+        long long nb = (long long)sms * per;
+        if (nb > kMaxBlocks) nb = kMaxBlocks;
+        cached = (int)nb;
+    });
     return cached;
 }
 

@@ -28,8 +28,38 @@ double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+// Pool key of a mesh description: its fields one by one (the struct's padding bytes, which
+// a C caller may leave uninitialised, take no part).
+template <typename V>
+void put(std::string& k, const V& v) {
+    k.append(reinterpret_cast<const char*>(&v), sizeof(v));
+}
+
 std::string desc_key(const st_mesh_desc& d) {
-    return std::string(reinterpret_cast<const char*>(&d), sizeof(d));
+    std::string k;
+    put(k, d.ndim_space);
+    for (int q = 0; q < 3; ++q) put(k, d.n[q]);
+    put(k, d.n_t);
+    for (int q = 0; q < 3; ++q) put(k, d.ext[q]);
+    put(k, d.tau);
+    put(k, d.mat.C_ins);
+    put(k, d.mat.C_con);
+    put(k, d.mat.k_ins);
+    put(k, d.mat.k_con);
+    put(k, d.mat.p_c);
+    put(k, d.mat.p_k);
+    put(k, d.bc);
+    put(k, d.bc_width);
+    put(k, d.lambda_crit);
+    put(k, d.coarse_dof_cap);
+    put(k, d.max_levels);
+    put(k, d.coarsening);
+    put(k, d.device);
+    put(k, d.coarse_solver);
+    put(k, d.coarse_max_it);
+    put(k, d.coarse_rtol);
+    put(k, d.march_blocks);
+    return k;
 }
 
 struct Job {
@@ -63,15 +93,17 @@ struct st_server {
     bool stopping = false;
     std::vector<std::thread> workers;
 
-    // Release idle meshes (least recently used first) until `need` more bytes fit.
-    void evict_for(long long need) {
+    // Take idle meshes (least recently used first) out of the pool until `need` more bytes
+    // fit; the caller destroys them after releasing the lock (st_destroy_mesh frees device
+    // memory, which synchronises the device, and must not stall the other slots' admission).
+    void evict_for(long long need, std::vector<st_mesh*>& doomed) {
         while (in_use + idle_bytes + need > desc.hbm_budget && !idle_lru.empty()) {
             const std::string key = idle_lru.front();
             idle_lru.pop_front();
             auto it = idle.find(key);
             if (it == idle.end()) continue;
             idle_bytes -= it->second.bytes;
-            st_destroy_mesh(it->second.mesh);
+            doomed.push_back(it->second.mesh);
             idle.erase(it);
         }
     }
@@ -84,6 +116,7 @@ struct st_server {
         for (;;) {
             std::shared_ptr<Job> job;
             st_mesh* mesh = nullptr;
+            std::vector<st_mesh*> doomed;
             {
                 std::unique_lock<std::mutex> lk(mu);
                 for (;;) {
@@ -106,7 +139,7 @@ struct st_server {
                             queue.pop_front();
                             break;
                         }
-                        evict_for(head->footprint);
+                        evict_for(head->footprint, doomed);
                         if (in_use + idle_bytes + head->footprint <= desc.hbm_budget) {
                             in_use += head->footprint;
                             job = head;
@@ -114,10 +147,15 @@ struct st_server {
                             break;
                         }
                     }
+                    if (!doomed.empty()) break;  // free them unlocked, then look again
                     cv_work.wait(lk);
                 }
             }
-            if (!job) break;
+            for (st_mesh* d : doomed) st_destroy_mesh(d);
+            if (!job) {
+                if (!doomed.empty()) continue;
+                break;
+            }
             job->t_admit = now_s();
             run(job.get(), mesh, stream);
             {
@@ -160,15 +198,18 @@ struct st_server {
             st_set_stream(mesh, nullptr);
             st_mesh_info info{};
             st_mesh_info_get(mesh, &info);
-            std::lock_guard<std::mutex> lk(mu);
-            const std::string key = desc_key(job->req.mesh);
-            if (!stopping && info.device_bytes <= desc.hbm_budget) {
-                idle.insert({key, Pooled{mesh, info.device_bytes}});
-                idle_lru.push_back(key);
-                idle_bytes += info.device_bytes;
-            } else {
-                st_destroy_mesh(mesh);
+            bool pooled = false;
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                const std::string key = desc_key(job->req.mesh);
+                if (!stopping && info.device_bytes <= desc.hbm_budget) {
+                    idle.insert({key, Pooled{mesh, info.device_bytes}});
+                    idle_lru.push_back(key);
+                    idle_bytes += info.device_bytes;
+                    pooled = true;
+                }
             }
+            if (!pooled) st_destroy_mesh(mesh);
         }
     }
 };
@@ -275,6 +316,32 @@ st_status st_submit(st_server* s, const st_request* r, uint64_t* ticket) {
         *ticket = job->ticket;
     }
     s->cv_work.notify_all();
+    return ST_OK;
+}
+
+st_status st_cancel(st_server* s, uint64_t ticket) {
+    if (!s) return ST_ERR_ARG;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->jobs.find(ticket);
+        if (it == s->jobs.end()) return ST_ERR_NOT_FOUND;
+        std::shared_ptr<Job> job = it->second;
+        if (job->done) return ST_ERR_STATE;  // finished: poll it instead
+        bool queued = false;
+        for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
+            if (q->get() == job.get()) {
+                s->queue.erase(q);
+                queued = true;
+                break;
+            }
+        if (!queued) return ST_ERR_BUSY;  // admitted and running on the device
+        memset(&job->res, 0, sizeof(job->res));
+        job->res.status = ST_ERR_CANCELLED;
+        job->res.latency_s = now_s() - job->t_submit;
+        job->res.queue_s = job->res.latency_s;
+        job->done = true;
+    }
+    s->cv_done.notify_all();
     return ST_OK;
 }
 

@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <string>
 #include <vector>
@@ -378,6 +379,10 @@ st_status create_mesh(const st_mesh_desc* d, Mesh** out) {
     m->own_stream = true;
     m->stream = m->own;
     if (const char* e = getenv("ST_VTAIL_NODES")) m->vt_max_nodes = atoll(e);
+    if (const char* e = getenv("ST_VTAIL_SPIN_LIMIT")) {
+        const long long v = atoll(e);  // a test shortens the barrier waits to make them give up
+        if (v >= 1 && v <= (1LL << 24)) m->vt_spin_limit = (unsigned)v;
+    }
     if (const char* e = getenv("ST_LEVEL_TIMING")) m->level_timing = atoi(e) != 0;
     if (const char* e = getenv("ST_VTAIL_TRACE"))
         if (atoi(e) != 0) cudaMalloc((void**)&m->vt_trace, 4096 * sizeof(unsigned long long));
@@ -515,7 +520,8 @@ st_status set_design(Mesh* m, const double* gamma, int layout, size_t count, int
     cudaStream_t s = m->stream;
     CK(cudaMemcpyAsync(m->gin, gamma, want * sizeof(double),
                        mem == ST_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-    launch_design_cast(m->gin, m->g64, m->g16, want, s);
+    CK(cudaMemsetAsync(m->d_err + 2, 0, sizeof(int), s));
+    launch_design_cast(m->gin, m->g64, m->g16, want, m->d_err + 2, s);
     // Galerkin coarse operators, level by level, in FP64; FP32 copies for the mixed V-cycle.
     const int L = (int)m->lv.size();
     for (int l = 1; l < L; ++l) {
@@ -545,9 +551,18 @@ st_status set_design(Mesh* m, const double* gamma, int layout, size_t count, int
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(&herr, m->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     }
+    int gbad = 0;
+    CK(cudaMemcpyAsync(&gbad, m->d_err + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (herr) return fail(ST_ERR_NUMERIC, "zero pivot in the coarsest-level inverse");
     m->design_version++;
+    if (gbad || herr) {
+        // the operators now hold a rejected design: no solve until a valid one is set
+        m->have_design = false;
+        m->have_state = false;
+        m->have_adjoint = false;
+        return fail(ST_ERR_NUMERIC, gbad ? "the design holds a NaN or infinite value"
+                                         : "zero pivot in the coarsest-level inverse");
+    }
     m->have_design = true;
     m->have_state = false;
     m->have_adjoint = false;
@@ -642,6 +657,7 @@ st_status Mesh::upload_vtail(int steps) {
     h->part = vt_part;
     h->bar = d_bar;
     h->err = d_err + 1;
+    h->spin_limit = vt_spin_limit;
     if (vt_trace) {
         h->trace = vt_trace;
         h->trace_cap = 4096;
@@ -733,9 +749,17 @@ void Mesh::vcycle_rec(int l, bool tr, int steps) {
     auto mark = [&](int k) {
         if (timing) cudaEventRecord(tev[l * 4 + k], stream);
     };
-    if (l == vt_first && W.d_vt && W.steps_uploaded == steps) {
+    if (l == vt_first && W.d_vt && W.steps_uploaded == steps && !vt_failed) {
         mark(0);
-        launch_vtail<T>(sd, tr, W.d_vt, d_bar, stream);
+        if (launch_vtail<T>(sd, tr, W.d_vt, d_bar, stream) < 0) {
+            // the cooperative launch was refused (for example not all blocks can be resident in
+            // this context): clear the error and run these levels one launch per phase below
+            cudaGetLastError();
+            vt_failed = true;
+            if (getenv("ST_VERBOSE")) fprintf(stderr, "st: persistent coarse tail refused; one launch per phase\n");
+        }
+    }
+    if (l == vt_first && W.d_vt && W.steps_uploaded == steps && !vt_failed) {
         if (timing) {
             cudaEvent_t e;
             cudaEventCreate(&e);
@@ -850,6 +874,7 @@ st_status Mesh::fgmres(bool tr, const double* rhs, double* x, const st_options& 
     stats->outer_its = 0;
     stats->restarts = 0;
     stats->converged = 0;
+    if (!std::isfinite(nf)) return fail(ST_ERR_NUMERIC, "NaN/Inf in the right-hand side");
     if (!(nf > 0)) {
         CK(cudaMemsetAsync(x, 0, N * sizeof(double), s));
         CK(cudaStreamSynchronize(s));
@@ -1105,6 +1130,8 @@ st_status st_solve_forward(st_mesh* m, const st_source* q, const st_options* o, 
     Mesh* mm = M(m);
     if (!mm->have_design) return fail(ST_ERR_STATE, "st_set_design must precede st_solve_forward");
     if (q->kind != ST_SRC_UNIFORM && q->kind != ST_SRC_SIN_T) return fail(ST_ERR_ARG, "unknown source kind");
+    if (!std::isfinite(q->q0) || !std::isfinite(q->a) || !std::isfinite(q->b) || !std::isfinite(q->f))
+        return fail(ST_ERR_ARG, "source parameters must be finite");
     cudaSetDevice(mm->device);
     st::launch_rhs(mm->sd, mm->lv[0].g, q->kind, q->q0, q->a, q->b, q->f, mm->f, mm->stream);
     st_status r = st::solve(mm, false, o, stats);

@@ -207,6 +207,10 @@ void launch_smooth(int sd, int lvl, const OpL0<T>& o0, const OpLc<T>& oc, bool t
 template <typename T>
 void launch_stencil_scale(const Geom& g, const T* st, const T* dinv, const unsigned char* dir, T* sc,
                           cudaStream_t s);
+// Jacobi diagonal (or its inverse) of a stencil level from the stencil's centre coefficients
+// (k_march.cu); coef is the forward-orientation class stencil set [class][27][P].
+template <typename T>
+void launch_stencil_diag(const Geom& g, const T* coef, const unsigned char* dir, T* d, bool invert, cudaStream_t s);
 // Fused FP32 Arnoldi step j -> j+1 on a stencil level (k_arnoldi.cu).
 void launch_arnoldi(const Geom& g, const float* coef, const unsigned char* dir, const float* dinv,
                     const Ptrs<float>& U, const float* w_in, float* w_out, int j, SmState* st, RedBuf rb,
@@ -252,7 +256,7 @@ template <typename TZ>
 void launch_fg_combine(long long n, double* x, const Ptrs<TZ>& Z, int k, const FgState* fs, cudaStream_t s);
 
 // ---- setup kernels
-void launch_design_cast(const double* in, double* g64, __nv_bfloat16* g16, long long n, cudaStream_t s);
+void launch_design_cast(const double* in, double* g64, __nv_bfloat16* g16, long long n, int* bad, cudaStream_t s);
 void launch_build_from_l0(int sd, const OpL0<double>& f0, const Geom& gc, int kind, int tc, double* elem_c,
                           cudaStream_t s);
 void launch_build_from_lc(int sd, const OpLc<double>& fc, const Geom& gc, int kind, double* elem_c,

@@ -91,6 +91,8 @@ struct Mesh {
     MGWork<double> w64;
 
     int vt_first = -1;             // first level of the persistent coarse tail (-1: none)
+    bool vt_failed = false;        // its cooperative launch was refused: one launch per phase instead
+    unsigned vt_spin_limit = 1u << 24;  // grid-barrier polls before a wait gives up (ST_VTAIL_SPIN_LIMIT)
     long long vt_max_nodes = 0;    // persistent coarse tail off by default (ST_VTAIL_NODES enables it)
     long long ws_version = 0;      // bumped when multigrid buffers move
     unsigned* d_bar = nullptr;

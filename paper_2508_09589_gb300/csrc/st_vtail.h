@@ -34,6 +34,7 @@ struct VTail {
     int* err;                      // set on a barrier timeout
     unsigned long long* trace;     // optional: block 0 records %globaltimer after each barrier
     int trace_cap;
+    unsigned spin_limit;           // polls before a grid-barrier wait gives up (default 2^24)
     OpL0<T> op0;                   // level-0 operator (when first == 0)
     VLevel<T> lv[kMaxLevels];
 };

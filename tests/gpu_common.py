@@ -54,3 +54,25 @@ def parity_rtol(A, s, f) -> float:
     solution's own residual in FP64 arithmetic is about that floor)."""
     floor = np.linalg.norm(abs(A) @ np.abs(s)) * 1.11e-16 / np.linalg.norm(f)
     return max(1e-13, 20.0 * floor)
+
+
+U32 = 2.0 ** -24
+U64 = 2.0 ** -53
+
+
+def rowwise_excess(y, yref, B, x, c, u) -> float:
+    """Largest ratio |y - yref|_i / (c u (B |x|)_i) over the rows: the componentwise rounding
+    bound of an evaluation that sums terms bounded by B |x| (B the element-wise absolute
+    operator or a product of non-negative transfers).  <= 1 means every row is within it."""
+    y = np.asarray(y, dtype=np.float64)
+    yref = np.asarray(yref, dtype=np.float64)
+    allowed = c * u * (B @ np.abs(np.asarray(x, dtype=np.float64))) + 1e-300
+    return float((np.abs(y - yref) / allowed).max())
+
+
+def galerkin_abs(B, Pt, cmask):
+    """Bound matrix of the next coarser level: Pt^T B Pt with the identity on prescribed nodes.
+    The element blocks of the Galerkin operator satisfy |P_E^T (sum_e J_e) P_E| <= P_E^T (sum_e
+    |J_e|) P_E because P >= 0, so this bounds their entry-wise absolute sum."""
+    import scipy.sparse as sp
+    return (Pt.T @ B @ Pt + sp.diags(cmask.astype(np.float64))).tocsr()

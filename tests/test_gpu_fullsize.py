@@ -87,6 +87,11 @@ def test_fullsize_operator_and_source_rows(name):
     gm.apply(0, torch.from_numpy(x32).cuda(), y32, "mixed")
     ref32 = O.apply_rows(om, g32, x32.astype(np.float64), rows)
     assert _rel(y32.cpu().numpy()[rows].astype(np.float64), ref32) < 1e-4
+    # row by row within the componentwise rounding bound c u32 (|J|_elem |x|)_i
+    bnd = O.apply_rows(om, g32, x32.astype(np.float64), rows, absolute=True)
+    c = 80 if om.sd == 2 else 280
+    err = np.abs(y32.cpu().numpy()[rows].astype(np.float64) - ref32)
+    assert (err <= c * 2.0 ** -24 * bnd + 1e-300).all()
     # source vector, assembled on the device at the forward solve
     src = dict(kind=w.source, q0=w.source_q0, a=w.source_a, b=w.source_b, f=w.source_f)
     gm.solve_forward(rtol=1e-2, max_it=3, allow_not_converged=True, **src)

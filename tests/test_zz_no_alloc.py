@@ -3,8 +3,9 @@
 Some callers cannot call cudaMalloc (for example code running inside another framework's
 stream capture or fixed memory pool, or a real-time loop).  For them the library offers
 r = f - J x and ||r||_2 with all scratch in a static device array.  This test calls it
-twice in a row through the C ABI and checks both results against the regular fine-level
-operator entry point (st_op_apply) within the FP64 operator tolerance of the other tests.
+twice in a row through the C ABI and checks both results against the FP64 oracle's assembled
+operator (r = f - A x) and against the regular fine-level operator entry point (st_op_apply),
+within the FP64 operator tolerance of the other tests, for both sink-patch placements.
 This file sorts last so that a run stopping at the first failure has run everything else.
 """
 import ctypes as C
@@ -22,11 +23,12 @@ torch = pytest.importorskip("torch")
 LAYOUT = {"extruded": 0, "spacetime": 1}
 
 
+@pytest.mark.parametrize("bc", ["patch_left", "patch_bottom"])
 @pytest.mark.parametrize("ns,nt,layout", [((40, 24), 20, "spacetime"), ((36, 20), 16, "extruded"),
                                           ((6, 4, 8), 6, "extruded")])
-def test_residual_norm_noalloc_matches_operator_apply(ns, nt, layout):
+def test_residual_norm_noalloc_matches_oracle_and_operator_apply(ns, nt, layout, bc):
     L = ensure_built()
-    om = O.Mesh(ns, nt, mat=O.Material(), bc="patch_left", bc_width=0.3)
+    om = O.Mesh(ns, nt, mat=O.Material(), bc=bc, bc_width=0.3)
     rng = np.random.default_rng(5)
     g = rng.random(om.elem_shape if layout == "spacetime" else tuple(reversed(ns)))
     gm = gpu_mesh(om, coarse_dof_cap=300)
@@ -35,8 +37,11 @@ def test_residual_norm_noalloc_matches_operator_apply(ns, nt, layout):
     f = torch.tensor(rng.standard_normal(om.n_nodes), dtype=torch.float64, device="cuda")
     y = torch.empty_like(x)
     gm.apply(0, x, y, "fp64")
-    r_ref = (f - y).cpu().numpy()
+    r_op = (f - y).cpu().numpy()
+    A = O.assemble(om, g)
+    r_ref = f.cpu().numpy() - A @ x.cpu().numpy()
     n_ref = float(np.linalg.norm(r_ref))
+    assert rel_err(r_op, r_ref) < 1e-12
     gd = torch.tensor(np.ascontiguousarray(g).reshape(-1), dtype=torch.float64, device="cuda")
     for _ in range(2):
         r = torch.full_like(x, float("nan"))
@@ -48,6 +53,7 @@ def test_residual_norm_noalloc_matches_operator_apply(ns, nt, layout):
         assert code == 0, L.st_last_error()
         torch.cuda.synchronize()
         assert rel_err(r.cpu().numpy(), r_ref) < 1e-12
+        assert rel_err(r.cpu().numpy(), r_op) < 1e-12
         assert abs(norm.item() - n_ref) <= 1e-12 * n_ref
 
 
