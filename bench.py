@@ -318,25 +318,35 @@ def serving_bench(args):
     return out
 
 
-def kernel_roofline(N, n_st_elems, apply_ms, apply_n, args):
-    """Dominant kernel: the level-0 smoother operator apply w = A D^-1 u_j (20 launches per
-    V-cycle), its launches timed with CUDA events on the mesh stream inside the timed steps.
-    Algorithmic bytes per launch: on stencil levels (time-constant 2-D designs) u_j read and w
-    written (8 B per node in FP32; the Jacobi scaling is folded into the stencil, whose
-    O(n_x n_y) coefficients stay in L2); on element-block levels u_j and D^-1 read and w
-    written (12 B per node) plus the BF16 density (2 B per space-time element)."""
+def step_bytes_per_node(steps: int, tsz: int) -> float:
+    """Algorithmic bytes per node of one level-0 Arnoldi-step launch on a stencil level, averaged
+    over the steps of a sweep: step 0 reads u_0 and writes w_0; step j >= 1 reads w_{j-1} and
+    u_0 .. u_{j-1} and writes u_j and w_j (4 (j + 3) bytes in FP32).  The stencil, with the Jacobi
+    scaling folded in, is O(n_x n_y) and stays in L2; the re-reads of u_q for the dot products
+    at the node hit L1/L2 (the same block staged them one plane earlier)."""
+    per = [2 * tsz] + [tsz * (j + 3) for j in range(1, steps)]
+    return float(sum(per)) / steps
+
+
+def kernel_roofline(N, n_st_elems, apply_ms, apply_n, args, steps=10):
+    """Dominant kernel, its launches timed with CUDA events on the mesh stream inside the
+    timed steps.  On stencil levels (time-constant 2-D designs) it is the fused Arnoldi step
+    km_sm_step (20 launches per V-cycle at level 0, bytes per step_bytes_per_node); on
+    element-block levels the smoother operator apply k_sm_applyw (u_j and D^-1 read, w written:
+    12 B per node in FP32, plus the BF16 density, 2 B per space-time element)."""
     peak, kind = _peaks()
     tsz = 4 if args.precision == "mixed" else 8
-    if n_st_elems == 0:  # stencil level: u_j in, w out (Jacobi scaling folded into the stencil)
-        byts = 2.0 * tsz * N
-    else:                # element-block level 0: u_j and D^-1 in, w out, plus the density
+    if n_st_elems == 0:
+        byts = step_bytes_per_node(steps, tsz) * N
+    else:
         byts = 3.0 * tsz * N + (2.0 * n_st_elems if args.precision == "mixed" else 8.0 * n_st_elems)
     if apply_n <= 0:
         return {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None, "traffic": None}
     t = apply_ms / 1e3 / apply_n
     ach = byts / t / 1e9
-    name = "km_sm_applyw_sc" if n_st_elems == 0 else "k_sm_applyw"
-    return {"kernel": f"{name} level 0 ({'FP32' if tsz == 4 else 'FP64'} smoother operator apply)",
+    name = "km_sm_step" if n_st_elems == 0 else "k_sm_applyw"
+    what = "fused Arnoldi step: update, stencil apply, dots" if n_st_elems == 0 else "smoother operator apply"
+    return {"kernel": f"{name} level 0 ({'FP32' if tsz == 4 else 'FP64'} {what})",
             "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
             "traffic": TRAFFIC_PER_LAUNCH.get((name, args.workload, args.precision)),
             "peak_source": kind, "algorithmic_bytes_per_launch": byts, "launch_ms": 1e3 * t,
@@ -346,8 +356,6 @@ def kernel_roofline(N, n_st_elems, apply_ms, apply_n, args):
 # DRAM read + write bytes of one launch, from an ncu capture of the current kernel version
 # (profiles/ names the capture); None when no capture of this version exists.
 TRAFFIC_PER_LAUNCH = {
-    # profiles/km_sm_applyw_sc_level0_c1_256x256x256.md: 99.23 MB read + 30.94 MB written
-    ("km_sm_applyw_sc", "c1_256x256x256_grf_extruded", "mixed"): 130173184,
 }
 
 
