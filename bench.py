@@ -202,7 +202,7 @@ def run_native(args):
         opt64 = options(rtol=1e-8, precision="fp64", max_it=400)
         s_mixed = mesh.state("T")
         t64 = []
-        for _ in range(args.fp64_steps):
+        for q in range(args.fp64_steps + 1):  # the first step warms the FP64 arm up (graph captures)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             mesh.set_design(gamma_d, layout)
@@ -210,14 +210,18 @@ def run_native(args):
             phi64, a64 = mesh.solve_adjoint("compliance", opts=opt64)
             mesh.sensitivities(sens_d)
             torch.cuda.synchronize()
-            t64.append(time.perf_counter() - t0)
+            if q > 0:
+                t64.append(time.perf_counter() - t0)
         s64 = mesh.state("T")
         fp64 = {"value": units / statistics.median(t64), "ms_per_step": 1e3 * statistics.median(t64),
+                "steps": len(t64), "warmup": 1, "ms_per_step_samples": [round(1e3 * t, 2) for t in t64],
                 "outer_its_fwd": f64["outer_its"], "outer_its_adj": a64["outer_its"],
                 "rel_res_fwd": f64["rel_res"], "rel_res_adj": a64["rel_res"],
                 "mixed_vs_fp64_rel_T_diff": float(np.abs(s_mixed - s64).max() / np.abs(s64).max())}
 
     roof = kernel_roofline(N, gamma_h.size if layout == "spacetime" else 0, apply_ms, apply_n, args)
+    vc = vcycle_roofline(mesh, args) if (w.extruded and len(w.ns) == 2) else None
+    fp64_apply = fp64_apply_roofline(mesh, L, local) if (w.extruded and len(w.ns) == 2) else None
 
     if rank == 0:
         f, a = stats["fwd"], stats["adj"]
@@ -240,6 +244,8 @@ def run_native(args):
                     "h2d_bytes_per_step": int(gamma_h.nbytes), "d2h_bytes_per_step": int(sens_h.nbytes + 8 * 3)},
             "gpu_launches": int(launches),
             "roofline": roof,
+            "vcycle_roofline": vc,
+            "fp64_apply_roofline": fp64_apply,
             "clocks": clk.summary(),
         }
     mesh.close()
@@ -250,11 +256,20 @@ def run_native(args):
                 line["serving"] = serving_bench(args)
             except Exception as e:  # noqa: BLE001
                 line["serving"] = {"error": f"{type(e).__name__}: {e}"}
+        for name in args.configs:
+            try:
+                line.setdefault("configs", {})[name] = config_leg(name, args)
+            except Exception as e:  # noqa: BLE001
+                line.setdefault("configs", {})[name] = {"error": f"{type(e).__name__}: {e}"}
         if args.cpu_baseline:
             try:
                 line["cpu_baseline"] = cpu_baseline(args.cpu_sample)
             except Exception as e:  # noqa: BLE001
                 line["cpu_baseline"] = {"error": f"{type(e).__name__}: {e}", "kind": "oracle"}
+            try:
+                line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(args.cpu_sample)
+            except Exception as e:  # noqa: BLE001
+                line["cpu_baseline_all_cores"] = {"error": f"{type(e).__name__}: {e}", "kind": "oracle"}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -338,6 +353,8 @@ def kernel_roofline(N, n_st_elems, apply_ms, apply_n, args, steps=10):
     tsz = 4 if args.precision == "mixed" else 8
     if n_st_elems == 0:
         byts = step_bytes_per_node(steps, tsz) * N
+    elif n_st_elems < 0:  # extruded 3-D design: element-block path, the density is O(n_x n_y n_z)
+        byts = 3.0 * tsz * N
     else:
         byts = 3.0 * tsz * N + (2.0 * n_st_elems if args.precision == "mixed" else 8.0 * n_st_elems)
     if apply_n <= 0:
@@ -357,6 +374,136 @@ def kernel_roofline(N, n_st_elems, apply_ms, apply_n, args, steps=10):
 # (profiles/ names the capture); None when no capture of this version exists.
 TRAFFIC_PER_LAUNCH = {
 }
+
+
+def vcycle_bytes(levels, steps: int, tsz: int) -> float:
+    """Algorithmic bytes of one V-cycle on a stencil hierarchy (time-constant 2-D design), each
+    vector element read or written once per kernel:
+    - pre-smoothing from zero: ||b|| (1 vector), the steps (step_bytes_per_node each), the last
+      update (w and the steps basis vectors read, u_steps written), the combination (basis, D^-1
+      read, x written);
+    - residual (b, x read, r written), restriction (r read, coarse b written), prolongation
+      (coarse x read, x read and written);
+    - post-smoothing: the start residual (b, x read, u_0 written), the steps, the last update,
+      the combination (basis, D^-1, x read, x written);
+    - the coarsest level: the dense FP64 inverse (n_c^2 values) and two vectors."""
+    per_step = step_bytes_per_node(steps, tsz) * steps
+    last_update = tsz * (steps + 2)
+    pre = tsz * 1 + per_step + last_update + tsz * (steps + 2)
+    post = tsz * 3 + per_step + last_update + tsz * (steps + 3)
+    total = 0.0
+    for l in range(len(levels) - 1):
+        n, nc = levels[l]["n_nodes"], levels[l + 1]["n_nodes"]
+        total += (pre + post + 3 * tsz + tsz + 2 * tsz) * n + 2 * tsz * nc
+    nc = levels[-1]["n_nodes"]
+    total += 8.0 * nc * nc + 2 * tsz * nc
+    return total
+
+
+def vcycle_roofline(mesh, args, cycles: int = 8):
+    """One V-cycle of the preconditioner (the operation repeated every outer iteration), timed
+    as eager launches through st_vcycle (each call synchronises; the captured graphs of the
+    solve run about 1 % faster), against its algorithmic bytes (vcycle_bytes)."""
+    import torch
+    tsz = 4 if args.precision == "mixed" else 8
+    dt = torch.float32 if tsz == 4 else torch.float64
+    N = mesh.n_nodes
+    g = torch.Generator(device="cuda").manual_seed(7)
+    b = torch.randn(N, dtype=dt, device="cuda", generator=g)
+    x = torch.empty_like(b)
+    mesh.vcycle(b, x, args.precision)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(cycles):
+        mesh.vcycle(b, x, args.precision)
+    torch.cuda.synchronize()
+    t = (time.perf_counter() - t0) / cycles
+    byts = vcycle_bytes(mesh.levels(), 10, tsz)
+    peak, kind = _peaks()
+    return {"ms": 1e3 * t, "algorithmic_bytes": byts, "achieved": byts / t / 1e9, "peak": peak, "unit": "GB/s",
+            "frac": byts / t / 1e9 / peak, "peak_source": kind, "cycles": cycles,
+            "how": "eager V-cycles through st_vcycle, host-timed with a synchronisation per cycle"}
+
+
+def fp64_apply_roofline(mesh, L, device: int, reps: int = 10):
+    """The FP64 fine operator apply (27-point stencil, 27 FP64 FMAs per node: the outer Krylov
+    solver's operator) against the measured FP64 FMA rate of this GPU (st_fp64_fma_rate)."""
+    import ctypes as C
+    import torch
+    N = mesh.n_nodes
+    x = torch.randn(N, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    mesh.apply(0, x, y, "fp64")
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        mesh.apply(0, x, y, "fp64")
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / reps
+    peak = C.c_double()
+    code = L.st_fp64_fma_rate(device, C.byref(peak))
+    tf = 2.0 * 27.0 * N / t / 1e12
+    return {"kernel": "km_apply<double> level 0 (FP64 27-point stencil)", "bound": "fp64-alu", "ms": 1e3 * t,
+            "achieved": tf, "peak": peak.value if code == 0 else None, "unit": "TFLOP/s",
+            "frac": tf / peak.value if code == 0 and peak.value > 0 else None, "flops_per_node": 54,
+            "bytes_per_node": 24, "achieved_gbs": 24.0 * N / t / 1e9,
+            "peak_source": "measured by st_fp64_fma_rate (independent FMA chains on every SM)"}
+
+
+def config_leg(name: str, args, steps: int = 1, warmup: int = 1):
+    """A further workload timed on its own mesh: set_design, forward and adjoint to 1e-8 and the
+    sensitivities, mixed precision (and all-FP64 for one step), with the level-0 smoother
+    kernel's CUDA-event roofline."""
+    import torch
+    from paper_2508_09589_gb300 import Mesh, options, source
+    w = W.WORKLOADS[name]
+    g = W.make_design(w).reshape(-1)
+    layout = "extruded" if w.extruded else "spacetime"
+    mesh = Mesh(w.ns, w.nt, material=w.material, bc=w.bc, bc_width=w.bc_width, tau=w.tau)
+    src = source(w.source, w.source_q0, w.source_a, w.source_b, w.source_f)
+    gd = torch.tensor(g, dtype=torch.float64, device="cuda")
+    sens = torch.empty_like(gd)
+    N = mesh.n_nodes
+    out = {"dofs": N, "mesh": list(w.ns) + [w.nt], "levels": mesh.n_levels}
+    for prec, nstep in (("mixed", steps), ("fp64", 1)):
+        opt = options(rtol=1e-8, precision=prec, max_it=400)
+        if prec == "mixed":
+            mesh.apply_timer(True)
+        ts = []
+        for q in range(warmup + nstep):
+            if prec == "mixed" and q == warmup:
+                mesh.apply_timer(True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            mesh.set_design(gd, layout)
+            f = mesh.solve_forward(src, opt)
+            phi, a = mesh.solve_adjoint("compliance", opts=opt)
+            mesh.sensitivities(sens)
+            torch.cuda.synchronize()
+            if q >= warmup:
+                ts.append(time.perf_counter() - t0)
+        t = statistics.median(ts)
+        leg = {"value": 2.0 * N / t, "unit": "DOF/s", "ms_per_step": 1e3 * t, "steps": len(ts),
+               "forward": {"outer_its": f["outer_its"], "rel_res": f["rel_res"], "seconds": f["seconds"],
+                           "dof_per_s": N / f["seconds"]},
+               "adjoint": {"outer_its": a["outer_its"], "rel_res": a["rel_res"], "seconds": a["seconds"],
+                           "dof_per_s": N / a["seconds"]}}
+        if prec == "mixed":
+            ms, n = mesh.apply_timer_read()
+            mesh.apply_timer(False)
+            args_c = argparse.Namespace(precision="mixed", workload=name)
+            leg["roofline"] = kernel_roofline(N, g.size if layout == "spacetime" else
+                                              (0 if len(w.ns) == 2 else -1), ms, n, args_c)
+            s_mixed = mesh.state("T")
+        else:
+            leg["mixed_vs_fp64_rel_T_diff"] = float(np.abs(s_mixed - mesh.state("T")).max() /
+                                                    np.abs(mesh.state("T")).max())
+        out[prec] = leg
+    out["mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    mesh.close()
+    return out
 
 
 def run_vcycles(args):
@@ -403,6 +550,33 @@ def cpu_baseline(sample: str):
             "seconds": t}
 
 
+def _oracle_sample(n: int) -> float:
+    """Seconds of one oracle sample (used by the all-core baseline's worker processes)."""
+    return cpu_baseline(str(n))["seconds"]
+
+
+def cpu_baseline_all_cores(sample: str):
+    """The same oracle sample run as independent problems on every host core at once (one
+    process per core, spawned, so no state of the GPU process is inherited): total DOFs
+    solved per second of wall time.  SuperLU itself is serial, so this is how the oracle uses
+    a many-core host."""
+    import multiprocessing as mp
+    n = int(sample)
+    cores = os.cpu_count() or 1
+    w = W.scaled(W.C1, (n, n), n)
+    dofs = 2.0 * (n + 1) ** 3
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        secs = pool.map(_oracle_sample, [n] * cores)
+    wall = time.perf_counter() - t0
+    return {"value": cores * dofs / wall, "unit": "DOF/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cores} independent {n}x{n}x{n} problems of the same family ({(n + 1) ** 3} DOFs each), "
+                      f"forward+adjoint direct solve, one process per core",
+            "seconds": wall, "per_problem_seconds_median": statistics.median(secs),
+            "workload": w.name}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -434,7 +608,9 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default=W.C1.name, choices=sorted(W.WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the all-FP64 arm (after one warm-up)")
+    ap.add_argument("--configs", nargs="*", default=["c2_512x512x256_grf_spacetime_sin", "c3_64x64x64x64_grf_extruded_3d"],
+                    help="further workloads timed after the headline one (each on its own mesh)")
     ap.add_argument("--cpu-sample", default="34", help="oracle sample n (n^3 mesh, about 10-15 s of CPU work)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--serve-requests", type=int, default=48, help="serving leg size (0 skips it)")

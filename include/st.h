@@ -279,6 +279,12 @@ st_status st_cancel(st_server* s, uint64_t ticket);
  * replayed CUDA graphs included); a diagnostic for benchmarks. */
 long long st_kernel_launches(void);
 
+/* Diagnostic (no counterpart in the paper): measured FP64 FMA throughput of `device` in
+ * TFLOP/s (2 flops per FMA), from a kernel of independent FMA chains on every SM, best of 5
+ * CUDA-event-timed runs.  It is the denominator of the roofline of the FP64 operator applies
+ * of the outer Krylov solver.  Allocates and frees a small scratch buffer. */
+st_status st_fp64_fma_rate(int device, double* tflops);
+
 /* Device-memory estimate used by admission control for a mesh description. */
 long long st_footprint_bytes(const st_mesh_desc* d, int precision, int restart);
 

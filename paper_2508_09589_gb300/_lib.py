@@ -123,6 +123,7 @@ SIGNATURES = {
     "st_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(Result), C.c_void_p, C.c_size_t, C.POINTER(C.c_int)]),
     "st_footprint_bytes": (C.c_longlong, [C.POINTER(MeshDesc), C.c_int, C.c_int]),
     "st_kernel_launches": (C.c_longlong, []),
+    "st_fp64_fma_rate": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
     "st_residual_norm_noalloc": (C.c_int, [C.POINTER(MeshDesc), C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                                            C.c_void_p, C.c_void_p, C.c_void_p]),
 }
