@@ -279,21 +279,20 @@ def run_native(args):
 def serving_bench(args):
     """Serving stream (the first R requests of the 256-request stream: 2-D + time meshes with
     per-axis element counts log-uniform in 32..512, time 32..256, own seeded designs), each a
-    forward + adjoint solve to 1e-8 with sensitivities.  Per precision: a closed-loop run
-    (all requests submitted at once) gives the saturation throughput; an open-loop run with
-    Poisson arrivals at a fraction of that rate gives the latency distribution."""
+    forward + adjoint solve to 1e-8 with sensitivities.  Per precision: a closed-loop run (all
+    requests submitted at once) gives the saturation throughput; open-loop runs with Poisson
+    arrivals at fractions of that rate give the latency distribution.  The server batches
+    queued small requests into shared graph launches (Server max_batch)."""
     import torch
     from paper_2508_09589_gb300 import Server, options, source
-    reqs = W.serving_requests()[: args.serve_requests]
-    designs = [W.make_design(w).reshape(-1) for w in reqs]
-    dofs = [(w.ns[0] + 1) * (w.ns[1] + 1) * (w.nt + 1) for w in reqs]
+    all_reqs = W.serving_requests()
     free, _ = torch.cuda.mem_get_info()
     budget = int(0.85 * free)
     src = source("uniform", 1.0)
 
-    def run(precision, arrivals):
+    def run(reqs, designs, precision, arrivals, max_batch):
         opt = options(rtol=1e-8, precision=precision, max_it=400)
-        srv = Server(budget, max_inflight=args.serve_slots)
+        srv = Server(budget, max_inflight=args.serve_slots, max_batch=max_batch)
         t0 = time.perf_counter()
         tickets, pending = {}, set()
         k = 0
@@ -314,22 +313,35 @@ def serving_bench(args):
             time.sleep(0.0005)
         span = time.perf_counter() - t0
         srv.close()
+        dofs = [(w.ns[0] + 1) * (w.ns[1] + 1) * (w.nt + 1) for w in reqs]
         lat = np.array([res[q]["latency_s"] for q in range(len(reqs))])
+        bat = np.array([res[q]["batch"] for q in range(len(reqs))])
         bad = sum(1 for q in range(len(reqs)) if res[q]["status"] != 0)
         return {"requests": len(reqs), "seconds": span, "req_per_s": len(reqs) / span,
                 "dof_per_s": 2.0 * sum(dofs) / span,
                 "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-                "max_ms": 1e3 * float(lat.max()), "failed": bad}
+                "max_ms": 1e3 * float(lat.max()), "failed": bad, "mean_batch": float(bat.mean()),
+                "batched_frac": float((bat > 1).mean())}
 
-    out = {"stream": f"first {len(reqs)} of the 256-request stream", "slots": args.serve_slots,
-           "hbm_budget_gb": budget / 1e9, "dofs_total": int(sum(dofs))}
-    for precision in ("mixed", "fp64"):
-        closed = run(precision, np.zeros(len(reqs)))
-        rate = args.serve_load * closed["req_per_s"]
-        arrivals = W.poisson_arrivals(len(reqs), rate)
-        opened = run(precision, arrivals)
-        opened["offered_req_per_s"] = rate
-        out[precision] = {"saturation": closed, f"poisson_{int(100 * args.serve_load)}pct": opened}
+    out = {"stream": "the 256-request stream (first R requests per precision)", "slots": args.serve_slots,
+           "max_batch": args.serve_batch, "hbm_budget_gb": budget / 1e9}
+    for precision, nreq, loads in (("mixed", args.serve_requests, args.serve_loads),
+                                   ("fp64", args.serve_fp64_requests, args.serve_fp64_loads)):
+        if nreq <= 0:
+            continue
+        reqs = all_reqs[:nreq]
+        designs = [W.make_design(w).reshape(-1) for w in reqs]
+        leg = {"requests": nreq, "dofs_total": int(sum((w.ns[0] + 1) * (w.ns[1] + 1) * (w.nt + 1) for w in reqs))}
+        closed = run(reqs, designs, precision, np.zeros(nreq), args.serve_batch)
+        leg["saturation"] = closed
+        if args.serve_batch > 1:
+            leg["saturation_unbatched"] = run(reqs, designs, precision, np.zeros(nreq), 1)
+        for f in loads:
+            rate = f * closed["req_per_s"]
+            r = run(reqs, designs, precision, W.poisson_arrivals(nreq, rate), args.serve_batch)
+            r["offered_req_per_s"] = rate
+            leg[f"poisson_{int(round(100 * f))}pct"] = r
+        out[precision] = leg
     return out
 
 
@@ -613,9 +625,14 @@ def main():
                     help="further workloads timed after the headline one (each on its own mesh)")
     ap.add_argument("--cpu-sample", default="34", help="oracle sample n (n^3 mesh, about 10-15 s of CPU work)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
-    ap.add_argument("--serve-requests", type=int, default=48, help="serving leg size (0 skips it)")
-    ap.add_argument("--serve-slots", type=int, default=4, help="concurrent solves in the server")
-    ap.add_argument("--serve-load", type=float, default=0.7, help="Poisson rate as a fraction of saturation")
+    ap.add_argument("--serve-requests", type=int, default=96, help="mixed-precision serving requests (0 skips)")
+    ap.add_argument("--serve-fp64-requests", type=int, default=48, help="all-FP64 serving requests (0 skips)")
+    ap.add_argument("--serve-slots", type=int, default=4, help="server slots (concurrent batches)")
+    ap.add_argument("--serve-batch", type=int, default=8, help="requests a slot solves together")
+    ap.add_argument("--serve-loads", type=lambda v: [float(x) for x in v.split(",") if x], default=[0.5, 1.0, 1.5],
+                    help="Poisson arrival rates as fractions of saturation (mixed precision)")
+    ap.add_argument("--serve-fp64-loads", type=lambda v: [float(x) for x in v.split(",") if x], default=[0.7],
+                    help="Poisson arrival rates as fractions of saturation (all-FP64)")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--vcycles", type=int, default=0,
                     help="profiling mode: only K mixed V-cycles on the workload, no solve")

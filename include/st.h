@@ -184,6 +184,24 @@ st_status st_solve_forward(st_mesh* m, const st_source* q, const st_options* o, 
 st_status st_solve_adjoint(st_mesh* m, const st_objective* obj, const st_options* o,
                            double* phi_out, st_stats* stats);
 
+/* Batched solves (no counterpart in the paper: concurrent design iterations of the paper's
+ * optimisation loop issue many such solves).  The meshes (all on one device, each at most
+ * once) are solved together: every FGMRES restart cycle of every mesh is captured into ONE CUDA
+ * graph, in which the outer iterations run inside conditional graph nodes (a WHILE node over the
+ * iterations, a SWITCH over the iteration index) and the convergence test and the stop decision
+ * are taken on the device; one graph launch advances all meshes by a whole restart cycle and the
+ * host synchronises once per cycle, not once per iteration.  Results are bit-identical to
+ * st_solve_forward / st_solve_adjoint of each mesh alone.  The graph runs on the first mesh's
+ * stream.  q, obj, phi_out, stats and status are arrays of `count` entries (stats, status and
+ * phi_out may be NULL); status[k] is mesh k's outcome (ST_OK, ST_ERR_NOT_CONVERGED,
+ * ST_ERR_NUMERIC).  Returns ST_OK when every mesh succeeded, else the first failure; argument
+ * and call-order errors (ST_ERR_ARG, ST_ERR_STATE) leave every mesh untouched.
+ * All meshes use the same options o (NULL: defaults). */
+st_status st_solve_forward_batch(st_mesh* const* m, int count, const st_source* q, const st_options* o,
+                                 st_stats* stats, st_status* status);
+st_status st_solve_adjoint_batch(st_mesh* const* m, int count, const st_objective* obj, const st_options* o,
+                                 double* phi_out, st_stats* stats, st_status* status);
+
 /* Sensitivities d phi / d gamma_e = -Lambda_e^T (dJ_e / d gamma_e) s_e (Sec. 3.3.3); for
  * an extruded design summed over time (transpose of the extrusion, Sec. 3.4.1).
  * count must equal the design size. */
@@ -251,12 +269,16 @@ typedef struct {
     double latency_s;        /* submit -> completion */
     double queue_s;          /* submit -> admission */
     long long footprint;     /* admitted device bytes */
+    int batch;               /* requests solved together with this one in shared graph launches
+                                (1: alone) */
 } st_result;
 
 typedef struct {
     long long hbm_budget;    /* device bytes the server may hold for requests */
-    int max_inflight;        /* concurrent requests on the device (slots) */
+    int max_inflight;        /* concurrent slots, each solving one batch at a time */
     int device;
+    int max_batch;           /* requests a slot may solve together in one batch (0: 8; 1: no batching) */
+    long long batch_nodes;   /* only requests of at most this many nodes share a batch (0: 2^21) */
 } st_server_desc;
 
 typedef struct st_server st_server;

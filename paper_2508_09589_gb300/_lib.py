@@ -77,11 +77,13 @@ class Request(C.Structure):
 
 class Result(C.Structure):
     _fields_ = [("status", C.c_int), ("phi", C.c_double), ("forward", Stats), ("adjoint", Stats),
-                ("latency_s", C.c_double), ("queue_s", C.c_double), ("footprint", C.c_longlong)]
+                ("latency_s", C.c_double), ("queue_s", C.c_double), ("footprint", C.c_longlong),
+                ("batch", C.c_int)]
 
 
 class ServerDesc(C.Structure):
-    _fields_ = [("hbm_budget", C.c_longlong), ("max_inflight", C.c_int), ("device", C.c_int)]
+    _fields_ = [("hbm_budget", C.c_longlong), ("max_inflight", C.c_int), ("device", C.c_int),
+                ("max_batch", C.c_int), ("batch_nodes", C.c_longlong)]
 
 
 _lib = None
@@ -103,6 +105,10 @@ SIGNATURES = {
     "st_solve_forward": (C.c_int, [C.c_void_p, C.POINTER(Source), C.POINTER(Options), C.POINTER(Stats)]),
     "st_solve_adjoint": (C.c_int, [C.c_void_p, C.POINTER(Objective), C.POINTER(Options), C.POINTER(C.c_double),
                                    C.POINTER(Stats)]),
+    "st_solve_forward_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(Options), C.c_void_p,
+                                         C.c_void_p]),
+    "st_solve_adjoint_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(Options), C.c_void_p,
+                                         C.c_void_p, C.c_void_p]),
     "st_sensitivities": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int]),
     "st_get_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.c_int]),
     "st_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int]),

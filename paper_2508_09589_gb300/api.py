@@ -284,6 +284,48 @@ class Mesh:
         return ms.value, n.value
 
 
+def _batch_args(meshes):
+    n = len(meshes)
+    arr = (C.c_void_p * n)(*[m._h.value for m in meshes])
+    return n, arr
+
+
+def solve_forward_batch(meshes, src: Optional[L.Source] = None, opts: Optional[L.Options] = None,
+                        allow_not_converged: bool = False, sources=None, **kw):
+    """Forward solves of several meshes together (st_solve_forward_batch): shared graph
+    launches, outer iterations and convergence tests on the device.  Returns per-mesh stats
+    dicts (with "status")."""
+    n, arr = _batch_args(meshes)
+    if sources is None:
+        one = src or source(**{k: v for k, v in kw.items() if k in ("kind", "q0", "a", "b", "f")})
+        sources = [one] * n
+    srcs = (L.Source * n)(*sources)
+    opts = opts or options(**{k: v for k, v in kw.items() if k not in ("kind", "q0", "a", "b", "f")})
+    st = (L.Stats * n)()
+    status = (C.c_int * n)()
+    code = L.lib().st_solve_forward_batch(C.cast(arr, C.c_void_p), n, C.cast(srcs, C.c_void_p), C.byref(opts),
+                                         C.cast(st, C.c_void_p), C.cast(status, C.c_void_p))
+    L.check(code, "st_solve_forward_batch", allow=(-3,) if allow_not_converged else ())
+    return [dict(st[k].as_dict(), status=status[k]) for k in range(n)]
+
+
+def solve_adjoint_batch(meshes, objective: str = "compliance", P: int = 20, opts: Optional[L.Options] = None,
+                        allow_not_converged: bool = False, **kw):
+    """Adjoint solves of several meshes together (st_solve_adjoint_batch).  Returns (phi list,
+    per-mesh stats dicts)."""
+    n, arr = _batch_args(meshes)
+    objs = (L.Objective * n)(*[L.Objective(L.OBJ[objective], int(P))] * n)
+    opts = opts or options(**kw)
+    st = (L.Stats * n)()
+    status = (C.c_int * n)()
+    phi = (C.c_double * n)()
+    code = L.lib().st_solve_adjoint_batch(C.cast(arr, C.c_void_p), n, C.cast(objs, C.c_void_p), C.byref(opts),
+                                         C.cast(phi, C.c_void_p), C.cast(st, C.c_void_p),
+                                         C.cast(status, C.c_void_p))
+    L.check(code, "st_solve_adjoint_batch", allow=(-3,) if allow_not_converged else ())
+    return [phi[k] for k in range(n)], [dict(st[k].as_dict(), status=status[k]) for k in range(n)]
+
+
 def plan_hierarchy(ns, nt, **kw):
     """Algorithm 1 levels for a mesh description (host only, no GPU needed)."""
     d = mesh_desc(ns, nt, **kw)
@@ -303,8 +345,9 @@ def footprint_bytes(ns, nt, precision: str = "mixed", restart: int = 30, **kw) -
 class Server:
     """Continuous-batching request server (st_server_create / st_submit / st_poll)."""
 
-    def __init__(self, hbm_budget: int, max_inflight: int = 4, device: int = 0):
-        d = L.ServerDesc(int(hbm_budget), int(max_inflight), int(device))
+    def __init__(self, hbm_budget: int, max_inflight: int = 4, device: int = 0, max_batch: int = 0,
+                 batch_nodes: int = 0):
+        d = L.ServerDesc(int(hbm_budget), int(max_inflight), int(device), int(max_batch), int(batch_nodes))
         h = C.c_void_p()
         L.check(L.lib().st_server_create(C.byref(d), C.byref(h)), "st_server_create")
         self._h = h
@@ -348,7 +391,7 @@ class Server:
             return False, None, None
         self._keep.pop(ticket, None)
         out = dict(status=res.status, phi=res.phi, forward=res.forward.as_dict(), adjoint=res.adjoint.as_dict(),
-                   latency_s=res.latency_s, queue_s=res.queue_s, footprint=res.footprint)
+                   latency_s=res.latency_s, queue_s=res.queue_s, footprint=res.footprint, batch=res.batch)
         return True, out, grad
 
     def wait(self, ticket: int, timeout: float = 600.0, poll_s: float = 0.001):

@@ -15,6 +15,7 @@ bool g_pdl = [] {
     const char* e = getenv("ST_PDL");
     return !(e && atoi(e) == 0);
 }();
+thread_local bool g_no_pdl = false;
 bool g_smstep = [] {
     const char* e = getenv("ST_SMSTEP");
     return !(e && atoi(e) == 0);
@@ -219,12 +220,60 @@ __global__ void __launch_bounds__(256) k_fg_normalize(Geom g, const double* __re
 __global__ void k_fg_backsolve(FgState* fs, int k) {
     pdl_enter();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (k < 0) k = fs->kdone;  // graph-resident cycle: the iterations it completed
     for (int q = k - 1; q >= 0; --q) {
         double a = fs->g[q];
         for (int l = q + 1; l < k; ++l) a -= fs->H[q * kMaxRestart + l] * fs->h1[l];
         const double d = fs->H[q * kMaxRestart + q];
         fs->h1[q] = d != 0 ? a / d : 0.0;  // y stored in h1
     }
+}
+
+// ---------------------------------------------------------------- graph-resident cycle control
+__global__ void k_fg_begin(FgState* fs, double tol, int max_it, cudaGraphConditionalHandle hw) {
+    pdl_enter();
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double beta = fs->beta;
+    const bool go = beta == beta && !fs->bad && beta > tol && fs->its < max_it;
+    fs->kdone = 0;
+    fs->cont = go ? 1 : 0;
+    cudaGraphSetConditional(hw, go ? 1u : 0u);
+}
+
+__global__ void k_fg_setj(const FgState* fs, cudaGraphConditionalHandle hs) {
+    pdl_enter();
+    if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(hs, (unsigned)fs->kdone);
+}
+
+__global__ void k_fg_check(FgState* fs, int j, double tol, int max_it, int m) {
+    pdl_enter();
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    fs->its += 1;
+    fs->kdone = j + 1;
+    const bool stop = fs->bad || fs->res_est <= tol || fs->breakdown || fs->its >= max_it || j + 1 >= m;
+    fs->cont = stop ? 0 : 1;
+}
+
+__global__ void k_fg_loop(const FgState* fs, cudaGraphConditionalHandle hw) {
+    pdl_enter();
+    if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(hw, fs->cont ? 1u : 0u);
+}
+
+void launch_fg_begin(FgState* fs, double tol, int max_it, cudaGraphConditionalHandle hw, cudaStream_t s) {
+    note_launch(s);
+    launch_pdl(k_fg_begin, 1, 32, 0, s, fs, tol, max_it, hw);
+}
+void launch_fg_setj(const FgState* fs, cudaGraphConditionalHandle hs, cudaStream_t s) {
+    note_launch(s);
+    launch_pdl(k_fg_setj, 1, 32, 0, s, fs, hs);
+}
+void launch_fg_check(FgState* fs, int j, double tol, int max_it, int m, cudaStream_t s) {
+    note_launch(s);
+    launch_pdl(k_fg_check, 1, 32, 0, s, fs, j, tol, max_it, m);
+}
+void launch_fg_loop(const FgState* fs, cudaGraphConditionalHandle hw, cudaStream_t s) {
+    note_launch(s);
+    launch_pdl(k_fg_loop, 1, 32, 0, s, fs, hw);
 }
 
 template <int SD, bool TR>
@@ -676,6 +725,15 @@ void launch_fg_normalize(const Geom& g, const double* w, double* vnext, TZ* bmg,
 }
 
 template <typename TZ>
+void launch_fg_update_x_dev(const Geom& g, double* x, TZ* const* Z, int m, FgState* fs, cudaStream_t s) {
+    note_launch(s);
+    launch_pdl(k_fg_backsolve, 1, 32, 0, s, fs, -1);
+    Ptrs<TZ> P{};
+    for (int q = 0; q < m; ++q) P.p[q] = Z[q];
+    launch_fg_combine<TZ>(g.nnodes, x, P, -m, fs, s);  // -m: up to m vectors, the count read on the device
+}
+
+template <typename TZ>
 void launch_fg_update_x(const Geom& g, double* x, TZ* const* Z, int k, FgState* fs, cudaStream_t s) {
     if (k <= 0) return;
     note_launch(s);
@@ -734,6 +792,7 @@ void launch_mask_copy(int sd, const Geom& g, const double* src, double* dst, cud
                                           int, FgState*, RedBuf, cudaStream_t);                                      \
     template void launch_fg_normalize<T>(const Geom&, const double*, double*, T*, int, FgState*, cudaStream_t);     \
     template void launch_fg_update_x<T>(const Geom&, double*, T* const*, int, FgState*, cudaStream_t);             \
+    template void launch_fg_update_x_dev<T>(const Geom&, double*, T* const*, int, FgState*, cudaStream_t);         \
     template void launch_fg_start<T>(const Geom&, double*, T*, FgState*, cudaStream_t);
 
 ST_INST_T(float)

@@ -207,6 +207,7 @@ template <typename TZ, int NQ>
 __global__ void __launch_bounds__(256) k_fg_combine(long long n, double* __restrict__ x, Ptrs<TZ> Z, int k,
                                                     const FgState* fs) {
     pdl_enter();
+    if (k < 0) k = fs->kdone;  // graph-resident cycle: the count is read on the device (<= -k)
     __shared__ double y[NQ];
     if (threadIdx.x < NQ) y[threadIdx.x] = threadIdx.x < k ? fs->h1[threadIdx.x] : 0.0;
     __syncthreads();
@@ -332,7 +333,7 @@ template <typename TZ>
 void launch_fg_combine(long long n, double* x, const Ptrs<TZ>& Z, int k, const FgState* fs, cudaStream_t s) {
     note_launch(s);
     const int blocks = stream_blocks(n, 2);
-    nq_dispatch(k, [&](auto NQc) {
+    nq_dispatch(k < 0 ? -k : k, [&](auto NQc) {
         constexpr int NQ = decltype(NQc)::value;
         launch_pdl(k_fg_combine<TZ, NQ>, blocks, 256, 0, s, n, x, Z, k, fs);
     });

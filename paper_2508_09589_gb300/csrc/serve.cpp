@@ -9,6 +9,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -71,7 +72,14 @@ struct Job {
     long long footprint = 0;
     double t_submit = 0, t_admit = 0;
     bool done = false;
+    st_mesh* mesh = nullptr;  // an idle mesh of the request's shape taken at admission, if any
+    long long nodes = 0;      // fine-level node count
 };
+
+bool same_options(const st_options& a, const st_options& b) {
+    return a.rtol == b.rtol && a.max_it == b.max_it && a.restart == b.restart && a.precision == b.precision &&
+           a.warm_start == b.warm_start && a.smooth_steps == b.smooth_steps && a.use_graphs == b.use_graphs;
+}
 
 struct Pooled {
     st_mesh* mesh;
@@ -108,42 +116,64 @@ struct st_server {
         }
     }
 
+    int max_batch() const { return desc.max_batch > 0 ? desc.max_batch : 8; }
+    long long batch_nodes() const { return desc.batch_nodes > 0 ? desc.batch_nodes : (1LL << 21); }
+    bool small(const Job& j) const { return j.nodes <= batch_nodes(); }
+
+    // Admission of job j (server lock held): an idle mesh of its shape, else its footprint
+    // within the budget (after taking idle meshes out of the pool when allow_evict).
+    bool admit(Job& j, bool allow_evict, std::vector<st_mesh*>& doomed) {
+        const std::string key = desc_key(j.req.mesh);
+        auto it = idle.find(key);
+        if (it != idle.end()) {  // reuse an idle mesh of this shape
+            j.mesh = it->second.mesh;
+            idle_bytes -= it->second.bytes;
+            in_use += j.footprint;
+            idle.erase(it);
+            for (auto l = idle_lru.begin(); l != idle_lru.end(); ++l)
+                if (*l == key) {
+                    idle_lru.erase(l);
+                    break;
+                }
+            return true;
+        }
+        if (allow_evict) evict_for(j.footprint, doomed);
+        if (in_use + idle_bytes + j.footprint <= desc.hbm_budget) {
+            in_use += j.footprint;
+            return true;
+        }
+        return false;
+    }
+
     void worker(int slot) {
         cudaSetDevice(desc.device);
         cudaStream_t stream = nullptr;
         cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
         (void)slot;
         for (;;) {
-            std::shared_ptr<Job> job;
-            st_mesh* mesh = nullptr;
+            std::vector<std::shared_ptr<Job>> batch;
             std::vector<st_mesh*> doomed;
             {
                 std::unique_lock<std::mutex> lk(mu);
                 for (;;) {
                     if (stopping && queue.empty()) break;
                     if (!queue.empty()) {
-                        auto& head = queue.front();
-                        const std::string key = desc_key(head->req.mesh);
-                        auto it = idle.find(key);
-                        if (it != idle.end()) {  // reuse an idle mesh of this shape
-                            mesh = it->second.mesh;
-                            idle_bytes -= it->second.bytes;
-                            in_use += head->footprint;
-                            idle.erase(it);
-                            for (auto l = idle_lru.begin(); l != idle_lru.end(); ++l)
-                                if (*l == key) {
-                                    idle_lru.erase(l);
-                                    break;
+                        std::shared_ptr<Job> head = queue.front();
+                        if (admit(*head, true, doomed)) {
+                            queue.pop_front();
+                            batch.push_back(head);
+                            // queued small requests with the same options join the head's batch
+                            // as long as they fit without evicting anything
+                            if (small(*head))
+                                for (auto it = queue.begin(); it != queue.end() && (int)batch.size() < max_batch();) {
+                                    if (small(**it) && same_options((*it)->req.options, head->req.options) &&
+                                        admit(**it, false, doomed)) {
+                                        batch.push_back(*it);
+                                        it = queue.erase(it);
+                                    } else {
+                                        ++it;
+                                    }
                                 }
-                            job = head;
-                            queue.pop_front();
-                            break;
-                        }
-                        evict_for(head->footprint, doomed);
-                        if (in_use + idle_bytes + head->footprint <= desc.hbm_budget) {
-                            in_use += head->footprint;
-                            job = head;
-                            queue.pop_front();
                             break;
                         }
                     }
@@ -152,16 +182,17 @@ struct st_server {
                 }
             }
             for (st_mesh* d : doomed) st_destroy_mesh(d);
-            if (!job) {
+            if (batch.empty()) {
                 if (!doomed.empty()) continue;
                 break;
             }
-            job->t_admit = now_s();
-            run(job.get(), mesh, stream);
+            run_batch(batch, stream);
             {
                 std::lock_guard<std::mutex> lk(mu);
-                in_use -= job->footprint;
-                job->done = true;
+                for (auto& j : batch) {
+                    in_use -= j->footprint;
+                    j->done = true;
+                }
             }
             cv_work.notify_all();
             cv_done.notify_all();
@@ -169,32 +200,88 @@ struct st_server {
         if (stream) cudaStreamDestroy(stream);
     }
 
-    void run(Job* job, st_mesh* mesh, cudaStream_t stream) {
-        st_result& r = job->res;
-        memset(&r, 0, sizeof(r));
-        r.footprint = job->footprint;
-        st_status s = ST_OK;
-        if (!mesh) s = st_create_mesh(&job->req.mesh, &mesh);
-        if (s == ST_OK) s = st_set_stream(mesh, stream);
-        if (s == ST_OK) s = st_set_design(mesh, job->gamma.data(), job->req.layout, job->gamma.size(), ST_MEM_HOST);
-        if (s == ST_OK) {
-            s = st_solve_forward(mesh, &job->req.source, &job->req.options, &r.forward);
-            if (s == ST_ERR_NOT_CONVERGED) s = ST_OK;
+    // One batch: set-up of every request's mesh, the forward solves of all of them together
+    // (st_solve_forward_batch: shared graph launches, convergence decided on the device), the
+    // adjoint solves together, then the sensitivities; a request that fails drops out.
+    void run_batch(std::vector<std::shared_ptr<Job>>& batch, cudaStream_t stream) {
+        const int n = (int)batch.size();
+        const double ta = now_s();
+        std::vector<Job*> ok;
+        for (auto& jp : batch) {
+            Job* job = jp.get();
+            job->t_admit = ta;
+            st_result& r = job->res;
+            memset(&r, 0, sizeof(r));
+            r.footprint = job->footprint;
+            r.batch = n;
+            st_status s = ST_OK;
+            if (!job->mesh) s = st_create_mesh(&job->req.mesh, &job->mesh);
+            if (s == ST_OK) s = st_set_stream(job->mesh, stream);
+            if (s == ST_OK)
+                s = st_set_design(job->mesh, job->gamma.data(), job->req.layout, job->gamma.size(), ST_MEM_HOST);
+            r.status = s;
+            if (s == ST_OK) ok.push_back(job);
         }
-        if (s == ST_OK) {
-            s = st_solve_adjoint(mesh, &job->req.objective, &job->req.options, &r.phi, &r.adjoint);
-            if (s == ST_ERR_NOT_CONVERGED) s = ST_OK;
+        auto hard = [](st_status s) { return !(s == ST_OK || s == ST_ERR_NOT_CONVERGED || s == ST_ERR_NUMERIC); };
+        const st_options opt = batch[0]->req.options;
+        // forward
+        std::vector<st_mesh*> ms;
+        std::vector<st_source> src;
+        for (Job* j : ok) {
+            ms.push_back(j->mesh);
+            src.push_back(j->req.source);
         }
-        if (s == ST_OK && job->req.want_gradient) {
-            job->grad.resize(job->gamma.size());
-            s = st_sensitivities(mesh, job->grad.data(), job->grad.size(), ST_MEM_HOST);
+        const int k = (int)ok.size();
+        std::vector<st_stats> fst(k);
+        std::vector<st_status> fs(k, ST_OK);
+        if (k > 0) {
+            const st_status r = st_solve_forward_batch(ms.data(), k, src.data(), &opt, fst.data(), fs.data());
+            if (hard(r)) std::fill(fs.begin(), fs.end(), r);
         }
-        if (s == ST_OK && !(r.forward.converged && r.adjoint.converged)) s = ST_ERR_NOT_CONVERGED;
-        r.status = s;
+        // adjoint, for the requests with a state
+        std::vector<Job*> ok2;
+        std::vector<st_mesh*> ms2;
+        std::vector<st_objective> obj;
+        for (int q = 0; q < k; ++q) {
+            ok[q]->res.forward = fst[q];
+            if (fs[q] == ST_OK || fs[q] == ST_ERR_NOT_CONVERGED) {
+                ok2.push_back(ok[q]);
+                ms2.push_back(ok[q]->mesh);
+                obj.push_back(ok[q]->req.objective);
+            } else {
+                ok[q]->res.status = fs[q];
+            }
+        }
+        const int k2 = (int)ok2.size();
+        std::vector<st_stats> ast(k2);
+        std::vector<st_status> as(k2, ST_OK);
+        std::vector<double> phi(k2, 0.0);
+        if (k2 > 0) {
+            const st_status r =
+                st_solve_adjoint_batch(ms2.data(), k2, obj.data(), &opt, phi.data(), ast.data(), as.data());
+            if (hard(r)) std::fill(as.begin(), as.end(), r);
+        }
+        for (int q = 0; q < k2; ++q) {
+            Job* job = ok2[q];
+            st_result& r = job->res;
+            r.adjoint = ast[q];
+            r.phi = phi[q];
+            st_status s = (as[q] == ST_OK || as[q] == ST_ERR_NOT_CONVERGED) ? ST_OK : as[q];
+            if (s == ST_OK && job->req.want_gradient) {
+                job->grad.resize(job->gamma.size());
+                s = st_sensitivities(job->mesh, job->grad.data(), job->grad.size(), ST_MEM_HOST);
+            }
+            if (s == ST_OK && !(r.forward.converged && r.adjoint.converged)) s = ST_ERR_NOT_CONVERGED;
+            r.status = s;
+        }
         const double t = now_s();
-        r.latency_s = t - job->t_submit;
-        r.queue_s = job->t_admit - job->t_submit;
-        if (mesh) {
+        for (auto& jp : batch) {
+            Job* job = jp.get();
+            job->res.latency_s = t - job->t_submit;
+            job->res.queue_s = job->t_admit - job->t_submit;
+            st_mesh* mesh = job->mesh;
+            job->mesh = nullptr;
+            if (!mesh) continue;
             st_set_stream(mesh, nullptr);
             st_mesh_info info{};
             st_mesh_info_get(mesh, &info);
@@ -305,6 +392,8 @@ st_status st_submit(st_server* s, const st_request* r, uint64_t* ticket) {
     job->gamma.assign(r->gamma, r->gamma + r->count);
     job->req.gamma = nullptr;
     job->footprint = st_footprint_bytes(&r->mesh, r->options.precision, r->options.restart > 0 ? r->options.restart : 30);
+    job->nodes = r->mesh.n_t + 1LL;
+    for (int q = 0; q < (r->mesh.ndim_space == 3 ? 3 : 2); ++q) job->nodes *= r->mesh.n[q] + 1LL;
     if (job->footprint <= 0 || job->footprint > s->desc.hbm_budget) return ST_ERR_BUSY;
     job->t_submit = now_s();
     {

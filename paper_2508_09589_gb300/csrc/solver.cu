@@ -845,13 +845,10 @@ st_status Mesh::vcycle(bool tr, int steps, bool graphs) {
 
 // ---------------------------------------------------------------- FGMRES (FP64, right preconditioned)
 template <typename T>
-st_status Mesh::fgmres(bool tr, const double* rhs, double* x, const st_options& o, st_stats* stats) {
-    const Geom& g = lv[0].g;
-    const int m = o.restart;
-    CKS(ensure_mg<T>(o.smooth_steps));
-    MGWork<T>& W = work<T>();
+st_status Mesh::ensure_krylov(int m, int steps) {
+    CKS(ensure_mg<T>(steps));
     std::vector<T*>& Z = sizeof(T) == 4 ? (std::vector<T*>&)Z32 : (std::vector<T*>&)Z64;
-    const long long N = g.nnodes;
+    const long long N = lv[0].g.nnodes;
     while ((int)V.size() < m + 1) {
         double* p = nullptr;
         CKS(alloc((void**)&p, N * sizeof(double)));
@@ -862,6 +859,17 @@ st_status Mesh::fgmres(bool tr, const double* rhs, double* x, const st_options& 
         CKS(alloc((void**)&p, N * sizeof(T)));
         Z.push_back(p);
     }
+    return ST_OK;
+}
+
+template <typename T>
+st_status Mesh::fgmres(bool tr, const double* rhs, double* x, const st_options& o, st_stats* stats) {
+    const Geom& g = lv[0].g;
+    const int m = o.restart;
+    CKS(ensure_krylov<T>(m, o.smooth_steps));
+    MGWork<T>& W = work<T>();
+    std::vector<T*>& Z = sizeof(T) == 4 ? (std::vector<T*>&)Z32 : (std::vector<T*>&)Z64;
+    const long long N = g.nnodes;
     const OpL0<double> A64 = op0<double>();
     cudaStream_t s = stream;
     // ||f||
@@ -940,6 +948,116 @@ st_status Mesh::fgmres(bool tr, const double* rhs, double* x, const st_options& 
     return result;
 }
 
+// ---------------------------------------------------------------- graph-resident restart cycles
+// Adds a conditional node (WHILE or SWITCH with `size` bodies) at the current end of the
+// capture on stream s and makes it the new end; returns the body graphs.
+static st_status add_conditional(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                                 unsigned size, cudaGraph_t** bodies) {
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, &deps, nullptr, &nd));
+    if (cst != cudaStreamCaptureStatusActive) return fail(ST_ERR_CUDA, "conditional node outside a capture");
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = type;
+    p.conditional.size = size;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, cg, deps, nullptr, nd, &p));
+    CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    *bodies = p.conditional.phGraph_out;
+    return ST_OK;
+}
+
+template <typename T>
+st_status Mesh::capture_cycle(cudaGraph_t G, cudaStream_t* cs, bool tr, const st_options& o, double tol,
+                              const double* rhs, double* x, long long* per_iter, long long* fixed) {
+    const Geom& g = lv[0].g;
+    const int m = o.restart;
+    MGWork<T>& W = work<T>();
+    std::vector<T*>& Z = sizeof(T) == 4 ? (std::vector<T*>&)Z32 : (std::vector<T*>&)Z64;
+    const OpL0<double> A64 = op0<double>();
+    cudaGraphConditionalHandle hw, hs;
+    CK(cudaGraphConditionalHandleCreate(&hw, G, 0, cudaGraphCondAssignDefault));
+    cudaStream_t keep = stream;
+    const bool keep_pdl = g_no_pdl;
+    g_no_pdl = true;
+    // conditional bodies hold kernels, memory copies and conditionals only: no timing events
+    // and no cooperative tail launch inside them
+    const bool keep_at = at_on;
+    const int keep_vt = vt_first;
+    at_on = false;
+    vt_first = -1;
+    st_status r = ST_OK;
+    long long vk = 0;
+    auto body = [&]() -> st_status {
+        CK(cudaStreamBeginCaptureToGraph(cs[0], G, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        capturing = true;
+        launch_fg_residual(sd, A64, tr, rhs, x, V[0], d_fg, rb, cs[0]);
+        launch_fg_begin(d_fg, tol, o.max_it, hw, cs[0]);
+        launch_fg_start<T>(g, V[0], W.b[0], d_fg, cs[0]);
+        cudaGraph_t* wb = nullptr;
+        CKS(add_conditional(cs[0], hw, cudaGraphCondTypeWhile, 1, &wb));
+        // WHILE body: the iteration index for the SWITCH, the V-cycle, the iteration's kernels, loop test
+        CK(cudaGraphConditionalHandleCreate(&hs, wb[0], 0, 0));
+        CK(cudaStreamBeginCaptureToGraph(cs[1], wb[0], nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        launch_fg_setj(d_fg, hs, cs[1]);
+        stream = cs[1];
+        vcycle_rec<T>(0, tr, o.smooth_steps);
+        stream = keep;
+        {
+            size_t nn = 0;
+            cudaGraph_t cg = nullptr;
+            cudaStreamCaptureStatus cst;
+            CK(cudaStreamGetCaptureInfo(cs[1], &cst, nullptr, &cg, nullptr, nullptr, nullptr));
+            CK(cudaGraphGetNodes(cg, nullptr, &nn));
+            vk = (long long)nn;  // the V-cycle's kernels and the index kernel
+        }
+        cudaGraph_t* sb = nullptr;
+        CKS(add_conditional(cs[1], hs, cudaGraphCondTypeSwitch, (unsigned)m, &sb));
+        for (int j = 0; j < m; ++j) {
+            CK(cudaStreamBeginCaptureToGraph(cs[2], sb[j], nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+            launch_fg_apply_dots<T>(sd, A64, tr, W.x[0], Z[j], fg_w, V.data(), j, d_fg, rb, cs[2]);
+            launch_fg_update_dots(g, fg_w, V.data(), j, 0, d_fg, rb, cs[2]);
+            launch_fg_update_dots(g, fg_w, V.data(), j, 1, d_fg, rb, cs[2]);
+            launch_fg_check(d_fg, j, tol, o.max_it, m, cs[2]);
+            if (j + 1 < m) launch_fg_normalize<T>(g, fg_w, V[j + 1], W.b[0], j, d_fg, cs[2]);
+            cudaGraph_t tmp;
+            CK(cudaStreamEndCapture(cs[2], &tmp));
+        }
+        launch_fg_loop(d_fg, hw, cs[1]);
+        cudaGraph_t tmp;
+        CK(cudaStreamEndCapture(cs[1], &tmp));
+        launch_fg_update_x_dev<T>(g, x, Z.data(), m, d_fg, cs[0]);
+        launch_fg_residual(sd, A64, tr, rhs, x, V[0], d_fg, rb, cs[0]);
+        CK(cudaStreamEndCapture(cs[0], &tmp));
+        return ST_OK;
+    };
+    r = body();
+    capturing = false;
+    stream = keep;
+    g_no_pdl = keep_pdl;
+    at_on = keep_at;
+    vt_first = keep_vt;
+    if (r != ST_OK) {
+        // end any capture left open by the failure
+        for (int q = 2; q >= 0; --q) {
+            cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(cs[q], &cst) == cudaSuccess && cst != cudaStreamCaptureStatusNone) {
+                cudaGraph_t tmp = nullptr;
+                cudaStreamEndCapture(cs[q], &tmp);
+            }
+        }
+        cudaGetLastError();
+        return r;
+    }
+    *per_iter = vk + 7;  // V-cycle and index kernel, apply + 3 passes, check, normalize, loop test
+    *fixed = 7;          // residual, begin, start, back substitution, combination, residual
+    return ST_OK;
+}
+
 st_status solve(Mesh* m, bool adjoint, const st_options* op, st_stats* stats) {
     st_options o;
     st_options_default(&o);
@@ -964,6 +1082,139 @@ st_status solve(Mesh* m, bool adjoint, const st_options* op, st_stats* stats) {
     if (tmo) r = fail(ST_ERR_TIMEOUT, "a grid barrier of the coarse V-cycle tail gave up waiting");
     S->seconds = now_s() - t0;
     return r;
+}
+
+st_status solve_batch(Mesh* const* ms, int n, bool adjoint, const st_options* op, st_stats* stats,
+                      st_status* status) {
+    st_options o;
+    st_options_default(&o);
+    if (op) o = *op;
+    if (n < 1 || !ms) return fail(ST_ERR_ARG, "empty batch");
+    if (o.restart < 1 || o.restart > kMaxRestart) return fail(ST_ERR_ARG, "restart must be in [1, 32]");
+    if (o.smooth_steps < 1 || o.smooth_steps > kMaxSmooth) return fail(ST_ERR_ARG, "smooth_steps must be in [1, 16]");
+    if (!(o.rtol > 0) || o.max_it < 1) return fail(ST_ERR_ARG, "rtol and max_it must be positive");
+    if (o.precision != ST_PREC_MIXED && o.precision != ST_PREC_FP64) return fail(ST_ERR_ARG, "unknown precision");
+    for (int k = 0; k < n; ++k) {
+        if (!ms[k]) return fail(ST_ERR_ARG, "null mesh in the batch");
+        if (ms[k]->device != ms[0]->device) return fail(ST_ERR_ARG, "the meshes of a batch must share a device");
+        for (int q = 0; q < k; ++q)
+            if (ms[q] == ms[k]) return fail(ST_ERR_ARG, "a mesh appears twice in the batch");
+    }
+    const bool mixed = o.precision == ST_PREC_MIXED;
+    const double t0 = now_s();
+    cudaSetDevice(ms[0]->device);
+    std::vector<st_stats> S(n);
+    std::vector<st_status> R(n, ST_OK);
+    std::vector<double> nf(n, 0.0), tol(n, 0.0);
+    std::vector<char> active(n, 0);
+    // storage, initial guess, ||f|| (one synchronisation per mesh stream)
+    for (int k = 0; k < n; ++k) {
+        Mesh* m = ms[k];
+        CKS(mixed ? m->ensure_krylov<float>(o.restart, o.smooth_steps) : m->ensure_krylov<double>(o.restart, o.smooth_steps));
+        double* x = adjoint ? m->lam : m->s;
+        const double* rhs = adjoint ? m->adjrhs : m->f;
+        if (!o.warm_start) CK(cudaMemsetAsync(x, 0, m->lv[0].g.nnodes * sizeof(double), m->stream));
+        CK(cudaMemsetAsync(&m->d_fg->its, 0, sizeof(int), m->stream));
+        launch_dot64(m->lv[0].g, rhs, rhs, m->d_scalar, m->rb, m->stream);
+        CK(cudaMemcpyAsync(&nf[k], m->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    }
+    for (int k = 0; k < n; ++k) CK(cudaStreamSynchronize(ms[k]->stream));
+    int n_active = 0;
+    for (int k = 0; k < n; ++k) {
+        nf[k] = sqrt(nf[k]);
+        S[k].norm_f = nf[k];
+        if (!std::isfinite(nf[k])) {
+            R[k] = fail(ST_ERR_NUMERIC, "NaN/Inf in the right-hand side");
+        } else if (!(nf[k] > 0)) {
+            double* x = adjoint ? ms[k]->lam : ms[k]->s;
+            CK(cudaMemsetAsync(x, 0, ms[k]->lv[0].g.nnodes * sizeof(double), ms[k]->stream));
+            CK(cudaStreamSynchronize(ms[k]->stream));
+            S[k].converged = 1;
+        } else {
+            tol[k] = o.rtol * nf[k];
+            active[k] = 1;
+            ++n_active;
+        }
+    }
+    if (n_active > 0) {
+        cudaStream_t bs = ms[0]->stream;
+        cudaStream_t cs[3] = {nullptr, nullptr, nullptr};
+        cudaGraph_t G = nullptr;
+        cudaGraphExec_t X = nullptr;
+        std::vector<long long> per_iter(n, 0), fixed(n, 0);
+        std::vector<int> its_prev(n, 0), cycles(n, 0);
+        st_status r = ST_OK;
+        auto run = [&]() -> st_status {
+            for (int q = 0; q < 3; ++q) CK(cudaStreamCreateWithFlags(&cs[q], cudaStreamNonBlocking));
+            CK(cudaGraphCreate(&G, 0));
+            for (int k = 0; k < n; ++k) {
+                if (!active[k]) continue;
+                Mesh* m = ms[k];
+                double* x = adjoint ? m->lam : m->s;
+                const double* rhs = adjoint ? m->adjrhs : m->f;
+                if (mixed)
+                    CKS(m->capture_cycle<float>(G, cs, adjoint, o, tol[k], rhs, x, &per_iter[k], &fixed[k]));
+                else
+                    CKS(m->capture_cycle<double>(G, cs, adjoint, o, tol[k], rhs, x, &per_iter[k], &fixed[k]));
+            }
+            const cudaError_t e = cudaGraphInstantiate(&X, G, 0);
+            if (e != cudaSuccess) {
+                X = nullptr;
+                return fail(ST_ERR_CUDA, std::string("batch graph instantiation failed: ") + cudaGetErrorString(e));
+            }
+            // one launch advances every unfinished mesh by a restart cycle; finished meshes only
+            // recompute their residual
+            for (int launch = 0; launch <= o.max_it + 1; ++launch) {
+                CK(cudaGraphLaunch(X, bs));
+                for (int k = 0; k < n; ++k)
+                    if (active[k]) CK(cudaMemcpyAsync(ms[k]->h_fg, ms[k]->d_fg, sizeof(FgState), cudaMemcpyDeviceToHost, bs));
+                CK(cudaStreamSynchronize(bs));
+                bool more = false;
+                long long kernels = 0;
+                for (int k = 0; k < n; ++k) {
+                    if (!active[k]) continue;
+                    const FgState* f = ms[k]->h_fg;
+                    kernels += fixed[k] + per_iter[k] * (f->its - its_prev[k]);
+                    if (f->its > its_prev[k]) ++cycles[k];
+                    its_prev[k] = f->its;
+                    const double beta = f->beta;
+                    S[k].outer_its = f->its;
+                    S[k].rel_res = beta / nf[k];
+                    S[k].rel_res_est = f->res_est / nf[k];
+                    if (!(beta == beta) || f->bad) {
+                        R[k] = fail(ST_ERR_NUMERIC, "NaN/Inf in the residual or the Arnoldi process");
+                    } else if (beta <= tol[k]) {
+                        S[k].converged = 1;
+                        R[k] = ST_OK;
+                    } else if (f->its >= o.max_it) {
+                        R[k] = fail(ST_ERR_NOT_CONVERGED, "rtol not reached within max_it outer iterations");
+                    } else {
+                        more = true;
+                    }
+                }
+                note_graph_launch(kernels);
+                if (!more) break;
+            }
+            return ST_OK;
+        };
+        r = run();
+        if (X) cudaGraphExecDestroy(X);
+        if (G) cudaGraphDestroy(G);
+        for (int q = 0; q < 3; ++q)
+            if (cs[q]) cudaStreamDestroy(cs[q]);
+        if (r != ST_OK) return r;
+        for (int k = 0; k < n; ++k) S[k].restarts = cycles[k] > 0 ? cycles[k] - 1 : 0;
+    }
+    const double t = now_s() - t0;
+    st_status worst = ST_OK;
+    for (int k = 0; k < n; ++k) {
+        S[k].seconds = t;
+        if (stats) stats[k] = S[k];
+        if (status) status[k] = R[k];
+        if (R[k] != ST_OK && (worst == ST_OK || worst == ST_ERR_NOT_CONVERGED)) worst = R[k];
+    }
+    if (worst != ST_OK) fail(worst, "a solve of the batch did not succeed (see the per-mesh statuses)");
+    return worst;
 }
 
 }  // namespace st
@@ -1140,10 +1391,8 @@ st_status st_solve_forward(st_mesh* m, const st_source* q, const st_options* o, 
     return r;
 }
 
-st_status st_solve_adjoint(st_mesh* m, const st_objective* obj, const st_options* o, double* phi_out,
-                           st_stats* stats) {
-    if (!m || !obj) return fail(ST_ERR_ARG, "null argument");
-    Mesh* mm = M(m);
+// Objective phi of the stored state and the adjoint right-hand side (d phi / d s)^T.
+static st_status adjoint_rhs(Mesh* mm, const st_objective* obj, double* phi_out) {
     if (!mm->have_state) return fail(ST_ERR_STATE, "st_solve_forward must precede st_solve_adjoint");
     cudaSetDevice(mm->device);
     const st::Geom& g = mm->lv[0].g;
@@ -1162,8 +1411,66 @@ st_status st_solve_adjoint(st_mesh* m, const st_objective* obj, const st_options
     cudaError_t e = cudaStreamSynchronize(mm->stream);
     if (e != cudaSuccess) return fail(ST_ERR_CUDA, cudaGetErrorString(e));
     if (phi_out) *phi_out = phi;
+    return ST_OK;
+}
+
+st_status st_solve_adjoint(st_mesh* m, const st_objective* obj, const st_options* o, double* phi_out,
+                           st_stats* stats) {
+    if (!m || !obj) return fail(ST_ERR_ARG, "null argument");
+    Mesh* mm = M(m);
+    CKS(adjoint_rhs(mm, obj, phi_out));
     st_status r = st::solve(mm, true, o, stats);
     mm->have_adjoint = (r == ST_OK || r == ST_ERR_NOT_CONVERGED);
+    return r;
+}
+
+st_status st_solve_forward_batch(st_mesh* const* m, int count, const st_source* q, const st_options* o,
+                                 st_stats* stats, st_status* status) {
+    if (!m || !q || count < 1) return fail(ST_ERR_ARG, "null argument or empty batch");
+    std::vector<Mesh*> ms(count);
+    for (int k = 0; k < count; ++k) {
+        if (!m[k]) return fail(ST_ERR_ARG, "null mesh in the batch");
+        ms[k] = M(m[k]);
+        if (!ms[k]->have_design) return fail(ST_ERR_STATE, "st_set_design must precede st_solve_forward_batch");
+        if (q[k].kind != ST_SRC_UNIFORM && q[k].kind != ST_SRC_SIN_T) return fail(ST_ERR_ARG, "unknown source kind");
+        if (!std::isfinite(q[k].q0) || !std::isfinite(q[k].a) || !std::isfinite(q[k].b) || !std::isfinite(q[k].f))
+            return fail(ST_ERR_ARG, "source parameters must be finite");
+    }
+    for (int k = 0; k < count; ++k) {
+        cudaSetDevice(ms[k]->device);
+        st::launch_rhs(ms[k]->sd, ms[k]->lv[0].g, q[k].kind, q[k].q0, q[k].a, q[k].b, q[k].f, ms[k]->f,
+                       ms[k]->stream);
+    }
+    std::vector<st_status> st(count, ST_OK);
+    const st_status r = st::solve_batch(ms.data(), count, false, o, stats, st.data());
+    // a failure of the batch itself (argument, CUDA) leaves no state; otherwise per mesh
+    const bool hard = !(r == ST_OK || r == ST_ERR_NOT_CONVERGED || r == ST_ERR_NUMERIC);
+    for (int k = 0; k < count; ++k) {
+        if (hard) st[k] = r;
+        ms[k]->have_state = st[k] == ST_OK || st[k] == ST_ERR_NOT_CONVERGED;
+        ms[k]->have_adjoint = false;
+        if (status) status[k] = st[k];
+    }
+    return r;
+}
+
+st_status st_solve_adjoint_batch(st_mesh* const* m, int count, const st_objective* obj, const st_options* o,
+                                 double* phi_out, st_stats* stats, st_status* status) {
+    if (!m || !obj || count < 1) return fail(ST_ERR_ARG, "null argument or empty batch");
+    std::vector<Mesh*> ms(count);
+    for (int k = 0; k < count; ++k) {
+        if (!m[k]) return fail(ST_ERR_ARG, "null mesh in the batch");
+        ms[k] = M(m[k]);
+        CKS(adjoint_rhs(ms[k], &obj[k], phi_out ? &phi_out[k] : nullptr));
+    }
+    std::vector<st_status> st(count, ST_OK);
+    const st_status r = st::solve_batch(ms.data(), count, true, o, stats, st.data());
+    const bool hard = !(r == ST_OK || r == ST_ERR_NOT_CONVERGED || r == ST_ERR_NUMERIC);
+    for (int k = 0; k < count; ++k) {
+        if (hard) st[k] = r;
+        ms[k]->have_adjoint = st[k] == ST_OK || st[k] == ST_ERR_NOT_CONVERGED;
+        if (status) status[k] = st[k];
+    }
     return r;
 }
 

@@ -30,6 +30,9 @@ __device__ __forceinline__ void pdl_enter() {
 #endif
 
 extern bool g_pdl;  // environment ST_PDL=0 turns the launch attribute off
+// Set by the calling thread while it captures the bodies of conditional graph nodes: launches
+// then carry no programmatic-serialization attribute (plain stream order inside the bodies).
+extern thread_local bool g_no_pdl;
 
 template <typename... KP, typename... A>
 inline void launch_pdl(void (*k)(KP...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A&&... args) {
@@ -42,7 +45,7 @@ inline void launch_pdl(void (*k)(KP...), dim3 grid, dim3 block, size_t smem, cud
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = g_pdl ? 1 : 0;
+    cfg.numAttrs = (g_pdl && !g_no_pdl) ? 1 : 0;
     cudaLaunchKernelEx(&cfg, k, static_cast<A&&>(args)...);
 }
 
@@ -146,6 +149,10 @@ struct FgState {
     double nrm;                    // scratch scalar result
     int breakdown;
     int bad;                       // NaN/Inf seen
+    // graph-resident restart cycles (no host synchronisation per iteration)
+    int its;                       // outer iterations of the solve so far
+    int kdone;                     // iterations completed in the current restart cycle
+    int cont;                      // 1: the cycle takes another iteration
 };
 
 struct RedBuf {
@@ -242,6 +249,18 @@ void launch_fg_normalize(const Geom& g, const double* w, double* vnext, TZ* bmg,
                          cudaStream_t s);
 template <typename TZ>
 void launch_fg_update_x(const Geom& g, double* x, TZ* const* Z, int k, FgState* fs, cudaStream_t s);
+// The same with k read on the device (fs->kdone), for graph-resident restart cycles.
+template <typename TZ>
+void launch_fg_update_x_dev(const Geom& g, double* x, TZ* const* Z, int m, FgState* fs, cudaStream_t s);
+// Graph-resident FGMRES cycle control (conditional graph nodes, Sec. 3.2 outer solve):
+// begin: iterate iff beta > tol, finite, its < max_it (sets the WHILE condition hw, kdone = 0);
+// setj: SWITCH index hs = kdone (the iteration about to run); check (after iteration j's
+// Givens rotation): its += 1, kdone = j + 1, cont = not (NaN, res_est <= tol, breakdown,
+// its >= max_it, j + 1 == m); loop: hw = cont.
+void launch_fg_begin(FgState* fs, double tol, int max_it, cudaGraphConditionalHandle hw, cudaStream_t s);
+void launch_fg_setj(const FgState* fs, cudaGraphConditionalHandle hs, cudaStream_t s);
+void launch_fg_check(FgState* fs, int j, double tol, int max_it, int m, cudaStream_t s);
+void launch_fg_loop(const FgState* fs, cudaGraphConditionalHandle hw, cudaStream_t s);
 void launch_fg_residual(int sd, const OpL0<double>& op, bool tr, const double* f, const double* x,
                         double* r, FgState* fs, RedBuf rb, cudaStream_t s);
 template <typename TZ>

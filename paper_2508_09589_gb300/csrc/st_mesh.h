@@ -155,6 +155,24 @@ struct Mesh {
     st_status vcycle(bool tr, int steps, bool graphs);
     template <typename T>
     st_status fgmres(bool tr, const double* rhs, double* x, const st_options& o, st_stats* stats);
+    // FGMRES storage (V: m + 1 FP64 vectors, Z: m vectors of the preconditioner's precision)
+    template <typename T>
+    st_status ensure_krylov(int m, int steps);
+    // Graph-resident restart cycle: captures into graph G (a branch with no dependencies) the
+    // residual, the cycle start, a WHILE node whose body holds the V-cycle and a SWITCH over the
+    // iteration index with the Arnoldi kernels of each iteration, the solution update and the
+    // final residual.  cs: three capture streams.  *per_iter and *fixed count its kernels.
+    template <typename T>
+    st_status capture_cycle(cudaGraph_t G, cudaStream_t* cs, bool tr, const st_options& o, double tol,
+                            const double* rhs, double* x, long long* per_iter, long long* fixed);
 };
+
+// Forward (adjoint = false) or adjoint solves of several meshes of one device whose right-hand
+// sides are assembled, as graph-resident FGMRES restart cycles: one graph holds every mesh's
+// cycle as an independent branch and one launch advances all of them by a whole restart cycle
+// (iterations, convergence tests and the stop decision on the device); the host synchronises
+// once per cycle.  The graph runs on the first mesh's stream.
+st_status solve_batch(Mesh* const* ms, int n, bool adjoint, const st_options* op, st_stats* stats,
+                      st_status* status);
 
 }  // namespace st

@@ -63,26 +63,67 @@ def _req_set(seed=3):
     return reqs
 
 
-def test_server_results_identical_alone_and_in_mix():
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_server_results_identical_alone_and_in_mix(precision):
+    """Each request alone (one slot, no batching) and in a mix (four slots, batches of up to eight
+    requests solved together in shared graph launches): bit-identical results, and the mix did
+    put several requests into one batch."""
     from paper_2508_09589_gb300 import Server, options
     reqs = _req_set()
     kw = dict(material=mat_dict(MAT))
-    opts = options(rtol=1e-8, precision="mixed")
+    opts = options(rtol=1e-8, precision=precision)
     alone = []
-    srv = Server(hbm_budget=40 << 30, max_inflight=1)
+    srv = Server(hbm_budget=40 << 30, max_inflight=1, max_batch=1)
     for ns, nt, g in reqs:
         t = srv.submit(ns, nt, g, opts=opts, **kw)
         alone.append(srv.wait(t))
     srv.close()
-    srv = Server(hbm_budget=40 << 30, max_inflight=4)
+    srv = Server(hbm_budget=40 << 30, max_inflight=2, max_batch=8)
     tickets = [srv.submit(ns, nt, g, opts=opts, **kw) for ns, nt, g in reqs]
     mixed = [srv.wait(t) for t in tickets]
     srv.close()
     for (ra, ga), (rm, gm_) in zip(alone, mixed):
         assert ra["status"] == 0 and rm["status"] == 0
+        assert ra["batch"] == 1
         assert ra["phi"] == rm["phi"]
         np.testing.assert_array_equal(ga, gm_)
+        assert ra["forward"]["outer_its"] == rm["forward"]["outer_its"]
         assert ra["forward"]["rel_res"] <= 1e-8 and ra["adjoint"]["rel_res"] <= 1e-8
+    assert max(r["batch"] for r, _ in mixed) >= 2
+
+
+def test_batched_solves_match_single_solves_and_the_oracle():
+    """st_solve_forward_batch / st_solve_adjoint_batch over meshes of different sizes, designs
+    and layouts: every state, adjoint and gradient equals the mesh's own st_solve_forward /
+    st_solve_adjoint bit for bit, and the oracle within the parity tolerances."""
+    from paper_2508_09589_gb300 import options, solve_adjoint_batch, solve_forward_batch
+    cases = [((24, 16), 12, False), ((20, 20), 16, True), ((32, 24), 8, False)]
+    rng = np.random.default_rng(41)
+    meshes, designs, oms = [], [], []
+    for ns, nt, st in cases:
+        om = O.Mesh(ns, nt, mat=MAT, bc="patch_left", bc_width=0.3)
+        g = rng.random(om.elem_shape if st else tuple(reversed(ns)))
+        gm = gpu_mesh(om, coarse_dof_cap=200)
+        gm.set_design(g)
+        meshes.append(gm)
+        designs.append(g)
+        oms.append(om)
+    sols = [O.forward(om, g, "uniform", 1.0) for om, g in zip(oms, designs)]
+    rt = max(parity_rtol(sol.A, sol.s, sol.f) for sol in sols)
+    opts = options(rtol=rt, precision="mixed", max_it=400)
+    fst = solve_forward_batch(meshes, opts=opts)
+    phis, ast = solve_adjoint_batch(meshes, opts=opts)
+    out = [(gm.state("T"), gm.state("lambda"), gm.sensitivities()) for gm in meshes]
+    for k, (gm, g, om) in enumerate(zip(meshes, designs, oms)):
+        assert fst[k]["status"] == 0 and fst[k]["converged"] and ast[k]["converged"]
+        st1 = gm.solve_forward(opts=opts)
+        phi1, sa1 = gm.solve_adjoint(opts=opts)
+        assert st1["outer_its"] == fst[k]["outer_its"] and sa1["outer_its"] == ast[k]["outer_its"]
+        assert phi1 == phis[k]
+        np.testing.assert_array_equal(gm.state("T"), out[k][0])
+        np.testing.assert_array_equal(gm.state("lambda"), out[k][1])
+        np.testing.assert_array_equal(gm.sensitivities(), out[k][2])
+        assert rel_err(out[k][0], sols[k].s) < 1e-10
 
 
 def test_server_matches_direct_mesh_solve():
