@@ -4,6 +4,8 @@
 // its adjoint right-hand side (Sec. 3.3.1, 3.3.3) and the sensitivities (Sec. 3.3.3).
 #include <math.h>
 
+#include <mutex>
+
 #include "st_device.cuh"
 
 namespace st {
@@ -210,6 +212,156 @@ __global__ void k_gj_step(const double* __restrict__ src, double* __restrict__ d
     }
 }
 
+// The whole Gauss-Jordan inverse as ONE cooperative kernel: the n pivot steps are separated by
+// a grid barrier instead of a kernel launch each.  Step kp reads the current matrix (src), stages
+// its pivot row in shared memory and writes the next one (dst) with the same expression as
+// k_gj_step, rows spread over the blocks; the block holding element (kp+1, kp+1) publishes the
+// next reciprocal pivot before the barrier.  Every barrier wait is bounded: after `limit` polls
+// the kernel sets *tmo and carries on (every loop and index stays bounded whatever the data).
+__device__ __forceinline__ void gj_grid_barrier(unsigned* ctr, unsigned target, unsigned limit, int* tmo) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(ctr, 1u);
+        unsigned spins = 0;
+        while (*((volatile unsigned*)ctr) < target) {
+            if (++spins > limit) {
+                atomicExch(tmo, 1);
+                break;
+            }
+            __nanosleep(32);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// Blocked form: BB pivots per step.  With K the step's pivot indices and P = S[K,K]^-1,
+// eliminating them one by one is the same as D[K,K] = P, D[K,j] = P S[K,j], D[i,K] = -S[i,K] P
+// and D[i,j] = S[i,j] - S[i,K] P S[K,j] (i, j outside K), so a step needs two grid barriers
+// (after the new pivot rows, after the update) instead of BB launches.  Every block inverts the
+// BB x BB pivot block itself (Gauss-Jordan without pivoting, as the unblocked form); phase 1
+// writes the new pivot rows D[K,:] into dst and PR; phase 2 updates the other rows from PR,
+// staged in shared memory.
+template <int BB>
+__global__ void __launch_bounds__(256) k_gj_block(double* A, double* B, double* PR, int n, int* err, unsigned* bar,
+                                                  int* tmo, unsigned limit) {
+    extern __shared__ double prs[];  // [BB][n] new pivot rows
+    __shared__ double Pm[BB][BB];    // inverse of the pivot block
+    __shared__ double sik[8][BB];    // S[i, K] of up to 8 rows
+    const unsigned nb = gridDim.x;
+    unsigned epoch = 0;
+    double* src = A;
+    double* dst = B;
+    for (int kp = 0; kp < n; kp += BB) {
+        const int bb = min(BB, n - kp);
+        // pivot block inverse: unpivoted Gauss-Jordan on the bb x bb block in shared memory, one
+        // thread per entry (the same expression per entry as the unblocked form)
+        const int tr = threadIdx.x / BB, tc = threadIdx.x % BB;
+        const bool tin = threadIdx.x < BB * BB;
+        if (tin) Pm[tr][tc] = (tr < bb && tc < bb) ? __ldcg(src + (long long)(kp + tr) * n + kp + tc) : 0.0;
+        __syncthreads();
+        for (int k = 0; k < bb; ++k) {
+            double v = 0.0;
+            if (tin && tr < bb && tc < bb) {
+                const double p = Pm[k][k];
+                const bool ok = fabs(p) > 1e-300 && isfinite(p);
+                if (!ok && tr == k && tc == k && blockIdx.x == 0) *err = 1;
+                const double ip = ok ? 1.0 / p : 1.0;
+                if (tr == k && tc == k)
+                    v = ip;
+                else if (tr == k)
+                    v = Pm[k][tc] * ip;
+                else if (tc == k)
+                    v = -Pm[tr][k] * ip;
+                else
+                    v = Pm[tr][tc] - Pm[tr][k] * (Pm[k][tc] * ip);
+            }
+            __syncthreads();
+            if (tin && tr < bb && tc < bb) Pm[tr][tc] = v;
+            __syncthreads();
+        }
+        // phase 1: new pivot rows D[K, j] = P S[K, j] (j outside K), P (j in K), columns over the grid
+        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += nb * blockDim.x) {
+            double sk[BB];
+#pragma unroll
+            for (int l = 0; l < BB; ++l) sk[l] = l < bb ? __ldcg(src + (long long)(kp + l) * n + j) : 0.0;
+            const bool inK = j >= kp && j < kp + bb;
+#pragma unroll
+            for (int k = 0; k < BB; ++k) {
+                if (k >= bb) break;
+                double v;
+                if (inK) {
+                    v = Pm[k][j - kp];
+                } else {
+                    v = 0.0;
+#pragma unroll
+                    for (int l = 0; l < BB; ++l) v += Pm[k][l] * sk[l];
+                }
+                PR[(long long)k * n + j] = v;
+                dst[(long long)(kp + k) * n + j] = v;
+            }
+        }
+        gj_grid_barrier(bar, ++epoch * nb, limit, tmo);
+        // phase 2: the other rows, D[i, j] = S[i, j] - S[i, K] PR[:, j]; D[i, K] = -S[i, K] P
+        for (int q0 = threadIdx.x; q0 < BB * n; q0 += 8 * blockDim.x) {  // 8 loads in flight per thread
+            double t[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int q = q0 + u * blockDim.x;
+                t[u] = q < bb * n ? __ldcg(PR + q) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int q = q0 + u * blockDim.x;
+                if (q < BB * n) prs[q] = t[u];
+            }
+        }
+        __syncthreads();
+        for (int i0 = blockIdx.x; i0 < n; i0 += nb * 8) {
+            // up to 8 rows per pass (i0, i0 + nb, ...): their S[i, K] first
+            if (threadIdx.x < 8 * BB) {
+                const int r = threadIdx.x / BB, l = threadIdx.x % BB, i = i0 + r * nb;
+                sik[r][l] = (i < n && l < bb) ? __ldcg(src + (long long)i * n + kp + l) : 0.0;
+            }
+            __syncthreads();
+            for (int r = 0; r < 8; ++r) {
+                const int i = i0 + r * nb;
+                if (i >= n) break;
+                if (i >= kp && i < kp + bb) continue;  // pivot rows were written in phase 1
+                const long long row = (long long)i * n;
+                double a[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    const int j = threadIdx.x + c * 256;
+                    a[c] = j < n ? __ldcg(src + row + j) : 0.0;
+                }
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    const int j = threadIdx.x + c * 256;
+                    if (j >= n) break;
+                    double v;
+                    if (j >= kp && j < kp + bb) {
+                        v = 0.0;
+#pragma unroll
+                        for (int l = 0; l < BB; ++l) v -= sik[r][l] * Pm[l][j - kp];
+                    } else {
+                        v = a[c];
+#pragma unroll
+                        for (int l = 0; l < BB; ++l) v -= sik[r][l] * prs[l * n + j];
+                    }
+                    dst[row + j] = v;
+                }
+            }
+            __syncthreads();
+        }
+        double* t = src;
+        src = dst;
+        dst = t;
+        gj_grid_barrier(bar, ++epoch * nb, limit, tmo);
+    }
+}
+
 // ---------------------------------------------------------------- source (Sec. 3.1.2)
 // f_i = int N_i Q: spatially uniform Q, so the spatial integral of each adjacent element is
 // its volume / 2^SD; the time integral of N_i q(t) over each adjacent slab uses 2-point
@@ -404,9 +556,44 @@ void launch_dense_assemble(int sd, int lvl, const OpL0<double>& o0, const OpLc<d
     }
 }
 
-void launch_gauss_jordan(double* A, double* B, double* pinv, int n, int* err, cudaStream_t s) {
-    note_launch(s, n + 1);
+void launch_gauss_jordan(double* A, double* B, double* pinv, double* PR, int n, int* err, unsigned* bar, int* tmo,
+                         cudaStream_t s) {
     const long long nn = (long long)n * n;
+    // one cooperative launch of the blocked form: a co-resident grid of up to 2 blocks per SM
+    if (n <= 4096 && PR) {
+        static std::once_flag once;
+        // 8 pivots per step (4 when the staged pivot rows, bw n doubles, would not fit in 200 KB);
+        // 16 measured no faster on the 1377-node coarsest level of the 256^2 x 256 mesh
+        static int per8 = 0, per4 = 0, sms = 0;
+        std::call_once(once, [] {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaFuncSetAttribute(k_gj_block<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * 3200 * 8);
+            cudaFuncSetAttribute(k_gj_block<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 4096 * 8);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per8, k_gj_block<8>, 256, 8 * 3200 * 8);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per4, k_gj_block<4>, 256, 4 * 4096 * 8);
+        });
+        const int bw = n <= 3200 ? 8 : 4;
+        const int per = bw == 8 ? per8 : per4;
+        int nb = sms * (per < 2 ? per : 2);
+        const size_t smem = (size_t)bw * n * sizeof(double);
+        if (nb >= 1) {
+            cudaMemsetAsync(bar, 0, sizeof(unsigned), s);
+            unsigned limit = 1u << 24;  // polls per barrier (about a second) before giving up
+            void* args[] = {(void*)&A, (void*)&B, (void*)&PR, (void*)&n, (void*)&err, (void*)&bar, (void*)&tmo,
+                            (void*)&limit};
+            const void* k = bw == 8 ? (const void*)k_gj_block<8> : (const void*)k_gj_block<4>;
+            if (cudaLaunchCooperativeKernel(k, dim3(nb), dim3(256), args, smem, s) == cudaSuccess) {
+                note_launch(s);
+                const int steps = (n + bw - 1) / bw;
+                if (steps & 1) cudaMemcpyAsync(A, B, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s);
+                return;
+            }
+            cudaGetLastError();  // refused (e.g. not co-resident): one launch per pivot below
+        }
+    }
+    note_launch(s, n + 1);
     const int blocks = (int)((nn + 255) / 256);
     double* src = A;
     double* dst = B;

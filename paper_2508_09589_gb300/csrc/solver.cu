@@ -432,6 +432,7 @@ st_status create_mesh(const st_mesh_desc* d, Mesh** out) {
         A((void**)&m->Ainv, nc * nc * sizeof(double));
         A((void**)&m->Awork, nc * nc * sizeof(double));
         A((void**)&m->pinv, (nc + 1) * sizeof(double));
+        A((void**)&m->gjpr, 8 * (size_t)nc * sizeof(double));
     }
     if (st == ST_OK && cudaMallocHost((void**)&m->h_fg, sizeof(FgState)) != cudaSuccess) {
         cudaGetLastError();
@@ -542,19 +543,27 @@ st_status set_design(Mesh* m, const double* gamma, int layout, size_t count, int
     }
     // coarsest operator, dense, and its inverse (the iterative coarsest solve needs only its
     // Jacobi diagonal, built with the multigrid workspace)
-    int herr = 0;
+    int herr = 0, htmo = 0;
     if (!m->coarse_iter) {
         const int nc = (int)m->lv[L - 1].g.nnodes;
         launch_dense_assemble(m->sd, L - 1, m->op0<double>(), m->opc<double>(L - 1), m->Ainv, s);
         CK(cudaMemsetAsync(m->d_err, 0, sizeof(int), s));
-        launch_gauss_jordan(m->Ainv, m->Awork, m->pinv, nc, m->d_err, s);
+        CK(cudaMemsetAsync(m->d_err + 3, 0, sizeof(int), s));
+        launch_gauss_jordan(m->Ainv, m->Awork, m->pinv, m->gjpr, nc, m->d_err, m->d_bar, m->d_err + 3, s);
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(&herr, m->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&htmo, m->d_err + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
     }
     int gbad = 0;
     CK(cudaMemcpyAsync(&gbad, m->d_err + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     m->design_version++;
+    if (htmo) {
+        m->have_design = false;
+        m->have_state = false;
+        m->have_adjoint = false;
+        return fail(ST_ERR_TIMEOUT, "a grid barrier of the coarsest-level inverse gave up waiting");
+    }
     if (gbad || herr) {
         // the operators now hold a rejected design: no solve until a valid one is set
         m->have_design = false;

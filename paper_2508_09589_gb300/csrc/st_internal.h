@@ -300,7 +300,12 @@ template <typename TI, typename TO>
 void launch_convert(const TI* in, TO* out, long long n, cudaStream_t s);
 void launch_dense_assemble(int sd, int lvl, const OpL0<double>& o0, const OpLc<double>& oc, double* A,
                            cudaStream_t s);
-void launch_gauss_jordan(double* A, double* B, double* pinv, int n, int* err, cudaStream_t s);  // result in A
+// Gauss-Jordan inverse of the dense n x n matrix A (result in A, B scratch); *err = 1 on a zero
+// pivot.  One cooperative kernel eliminating 8 (or 4) pivots per step with two bounded grid
+// barriers per step (PR: 8 n doubles of scratch, bar: barrier counter, *tmo = 1 if a barrier wait gave
+// up), else one launch per pivot.
+void launch_gauss_jordan(double* A, double* B, double* pinv, double* PR, int n, int* err, unsigned* bar, int* tmo,
+                         cudaStream_t s);
 void launch_rhs(int sd, const Geom& g, int kind, double q0, double a, double b, double f, double* out,
                 cudaStream_t s);
 void launch_pnorm(int sd, const Geom& g, const double* s, int P, double* rhs, double* phi, RedBuf rb,

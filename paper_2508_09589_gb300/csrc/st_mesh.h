@@ -74,6 +74,7 @@ struct Mesh {
     void coarse_gmres(bool tr);
     double* Ainv = nullptr;
     double* Awork = nullptr;
+    double* gjpr = nullptr;        // scratch of the blocked inverse (8 rows of the coarsest size)
     double* pinv = nullptr;
     int* d_err = nullptr;
 
