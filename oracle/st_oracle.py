@@ -731,3 +731,103 @@ def apply_rows(m: Mesh, gamma: np.ndarray, x: np.ndarray, rows: np.ndarray,
                     acc += (C * Jc[a, b] + k * Jk[a, b]) * x[q]
         out[r] = acc
     return out
+
+
+# ----------------------------------------------------------------------------
+# PDE filter and Heaviside projection (Sec. 3.3.2).
+# The filter solves  -div(D grad psi) + psi = gamma  over the space-time domain, D = diag(
+# r_x^2/12 per spatial axis, r_t^2/12 in time), natural boundary conditions on every face.
+# Reading: it is discretised with the same trilinear space-time elements as the state: nodal
+# psi, (M_f + K_f) psi = T gamma with T_ie = int_e N_i (the element's volume / n_v), and the
+# filtered element value is the mean of the element's nodal values, gamma~ = E psi.  An extruded
+# (time-constant) design gives a time-constant psi, equal to the spatial filter of one slab.
+# ----------------------------------------------------------------------------
+def filter_element_matrix(h: Sequence[float], dt: float, r_x: float, r_t: float, ngauss: int = 3) -> np.ndarray:
+    """int N_a N_b + sum_d D_dd dN_a/dxi_d dN_b/dxi_d on one h x ... x dt brick (Gauss quadrature)."""
+    sd = len(h)
+    nv = 2 ** (sd + 1)
+    gp, gw = gauss_1d(ngauss)
+    sizes = list(h) + [dt]
+    D = [r_x ** 2 / 12.0] * sd + [r_t ** 2 / 12.0]
+    Ke = np.zeros((nv, nv))
+    for q in itertools.product(range(ngauss), repeat=sd + 1):
+        wq = np.prod([gw[qi] * sizes[d] for d, qi in enumerate(q)])
+        N = np.ones(nv)
+        dN = np.ones((sd + 1, nv))
+        for a in range(nv):
+            for d in range(sd + 1):
+                bit = (a >> d) & 1
+                phi, dphi = _basis_1d(gp[q[d]])
+                N[a] *= phi[bit]
+                for dd in range(sd + 1):
+                    dN[dd, a] *= (dphi[bit] / sizes[d]) if dd == d else phi[bit]
+        Ke += wq * np.outer(N, N)
+        for d in range(sd + 1):
+            Ke += wq * D[d] * np.outer(dN[d], dN[d])
+    return Ke
+
+
+def filter_operator(m: Mesh, r_x: float, r_t: float) -> sp.csr_matrix:
+    """Assembled filter matrix M_f + K_f on the nodes of m (no prescribed nodes)."""
+    Ke = filter_element_matrix(m.h, m.dt, r_x, r_t)
+    conn = element_connectivity(m)
+    nv = m.nv
+    rows = np.repeat(conn, nv, axis=1).reshape(-1)
+    cols = np.tile(conn, (1, nv)).reshape(-1)
+    vals = np.broadcast_to(Ke, (m.n_elem, nv, nv)).reshape(-1)
+    return sp.csr_matrix((vals, (rows, cols)), shape=(m.n_nodes, m.n_nodes))
+
+
+def element_to_node(m: Mesh) -> sp.csr_matrix:
+    """T (nodes x elements): T_ie = int_e N_i = v_e / n_v for the nodes i of element e."""
+    conn = element_connectivity(m)
+    ve = float(np.prod(m.h)) * m.dt
+    rows = conn.reshape(-1)
+    cols = np.repeat(np.arange(m.n_elem), m.nv)
+    return sp.csr_matrix((np.full(rows.size, ve / m.nv), (rows, cols)), shape=(m.n_nodes, m.n_elem))
+
+
+def node_to_element(m: Mesh) -> sp.csr_matrix:
+    """E (elements x nodes): the mean of the element's n_v nodal values."""
+    conn = element_connectivity(m)
+    rows = np.repeat(np.arange(m.n_elem), m.nv)
+    return sp.csr_matrix((np.full(rows.size, 1.0 / m.nv), (rows, conn.reshape(-1))), shape=(m.n_elem, m.n_nodes))
+
+
+def _filter_mesh(m: Mesh, gamma: np.ndarray) -> Tuple[Mesh, bool]:
+    extruded = np.asarray(gamma).size == int(np.prod(m.ns))
+    return (with_size(m, m.ns, 1) if extruded else m), extruded
+
+
+def pde_filter(m: Mesh, gamma: np.ndarray, r_x: float, r_t: float) -> np.ndarray:
+    """gamma~ = E (M_f + K_f)^-1 T gamma (direct sparse solve), same layout as gamma."""
+    fm, extruded = _filter_mesh(m, gamma)
+    g = np.asarray(gamma, dtype=np.float64).reshape(-1)
+    A = filter_operator(fm, r_x, r_t)
+    psi = solve_direct(A, element_to_node(fm) @ g)
+    return (node_to_element(fm) @ psi).reshape(np.asarray(gamma).shape)
+
+
+def heaviside(x: np.ndarray, beta: float = 32.0, eta: float = 0.5) -> np.ndarray:
+    """Projection of Sec. 3.3.2: (tanh(beta eta) + tanh(beta (x - eta))) / (tanh(beta eta) + tanh(beta (1 - eta)))."""
+    den = np.tanh(beta * eta) + np.tanh(beta * (1.0 - eta))
+    return (np.tanh(beta * eta) + np.tanh(beta * (np.asarray(x) - eta))) / den
+
+
+def heaviside_derivative(x: np.ndarray, beta: float = 32.0, eta: float = 0.5) -> np.ndarray:
+    """d heaviside / dx = beta (1 - tanh^2(beta (x - eta))) / (tanh(beta eta) + tanh(beta (1 - eta)))."""
+    den = np.tanh(beta * eta) + np.tanh(beta * (1.0 - eta))
+    return beta * (1.0 - np.tanh(beta * (np.asarray(x) - eta)) ** 2) / den
+
+
+def design_chain(m: Mesh, gamma: np.ndarray, r_x: float, r_t: float, beta: float = 32.0, eta: float = 0.5):
+    """Physical design gamma_bar = H(F gamma) and gamma~ = F gamma."""
+    gt = pde_filter(m, gamma, r_x, r_t)
+    return heaviside(gt, beta, eta), gt
+
+
+def chain_rule(m: Mesh, dphi_dphys: np.ndarray, gamma_tilde: np.ndarray, r_x: float, r_t: float,
+               beta: float = 32.0, eta: float = 0.5) -> np.ndarray:
+    """d phi / d gamma = F^T (H'(gamma~) * d phi / d gamma_bar).  F = E A^-1 T with T = v_e E^T and
+    A symmetric, so F^T = F: the sensitivities pass through the same filter (Sec. 3.3.2)."""
+    return pde_filter(m, heaviside_derivative(gamma_tilde, beta, eta) * dphi_dphys, r_x, r_t)

@@ -6,6 +6,7 @@ products, brute-force integration of global hat functions, exact discrete
 solutions, conservation, convergence orders, the hierarchies printed in the
 paper, finite differences and complex-step derivatives.
 """
+import itertools
 import math
 import os
 
@@ -708,3 +709,120 @@ def test_abs_operator_bounds_the_operator_and_is_exact_on_one_element():
     y = np.where(dm, x.astype(np.float32), y).astype(np.float64)
     err = np.abs(y - A @ x)
     assert np.all(err <= 16 * 2.0 ** -24 * (B @ np.abs(x)) + 1e-30)
+
+
+# ---------------------------------------------------------------- PDE filter and projection (Sec. 3.3.2)
+def _cosine_mode(m, k):
+    """Nodal field prod_d cos(k_d pi i_d / n_d) in node order (t, [z,] y, x); k = (kx, ky, [kz,] kt)."""
+    axes_n = [m.nt] + list(reversed(m.ns))
+    axes_k = [k[-1]] + list(reversed(k[:-1]))
+    grids = [np.cos(kk * np.pi * np.arange(n + 1) / n) for kk, n in zip(axes_k, axes_n)]
+    out = grids[0]
+    for gg in grids[1:]:
+        out = np.multiply.outer(out, gg)
+    return out.reshape(-1)
+
+
+def _boundary_weights(m):
+    axes_n = [m.nt] + list(reversed(m.ns))
+    ws = []
+    for n in axes_n:
+        w = np.ones(n + 1); w[0] = w[-1] = 0.5
+        ws.append(w)
+    out = ws[0]
+    for w in ws[1:]:
+        out = np.multiply.outer(out, w)
+    return out.reshape(-1)
+
+
+@pytest.mark.parametrize("ns,nt", [((5, 4), 6), ((3, 4, 2), 3)])
+def test_filter_operator_acts_on_cosine_modes_by_its_closed_form(ns, nt):
+    """On a regular Q1 mesh with natural boundary conditions, sampled cosines are eigenvectors of the
+    1-D mass and stiffness matrices up to halved boundary rows: M v = mu (w v), K v = kappa (w v) with
+    mu = h (4 + 2 cos theta) / 6, kappa = (2 - 2 cos theta) / h, theta = k pi / n.  So the filter matrix
+    acts on prod_d cos(k_d pi x_d / L_d) by
+    sigma = prod mu + (r_x^2/12) sum_spatial kappa_a prod_{d != a} mu_d + (r_t^2/12) kappa_t prod_{d != t} mu_d."""
+    ext = tuple(0.6 + 0.2 * d for d in range(len(ns)))
+    m = O.Mesh(ns, nt, ext=ext, tau=0.9, bc="none")
+    r_x, r_t = 0.31, 0.23
+    A = O.filter_operator(m, r_x, r_t)
+    w = _boundary_weights(m)
+    sizes = list(m.h) + [m.dt]
+    counts = list(ns) + [nt]
+    for k in itertools.product(*[range(0, c + 1, max(1, c // 2)) for c in counts]):
+        mu = [hh * (4 + 2 * np.cos(kk * np.pi / c)) / 6 for hh, kk, c in zip(sizes, k, counts)]
+        ka = [(2 - 2 * np.cos(kk * np.pi / c)) / hh for hh, kk, c in zip(sizes, k, counts)]
+        sd = len(ns)
+        sigma = np.prod(mu)
+        for a in range(sd + 1):
+            coef = (r_x if a < sd else r_t) ** 2 / 12.0
+            sigma += coef * ka[a] * np.prod([mu[d] for d in range(sd + 1) if d != a])
+        psi = _cosine_mode(m, k)
+        np.testing.assert_allclose(A @ psi, sigma * w * psi, rtol=0, atol=1e-13 * np.abs(sigma))
+
+
+def test_filter_preserves_constants_and_volume_and_is_symmetric():
+    m = O.Mesh((6, 5), 4, ext=(1.0, 0.8), tau=1.2, bc="none")
+    rng = np.random.default_rng(31)
+    g = rng.random(m.elem_shape)
+    r_x, r_t = 2.4 * m.h[0], 2.4 * m.dt
+    np.testing.assert_allclose(O.pde_filter(m, np.ones(m.elem_shape), r_x, r_t), 1.0, rtol=1e-13)
+    gt = O.pde_filter(m, g, r_x, r_t)
+    np.testing.assert_allclose(gt.sum(), g.sum(), rtol=1e-13)  # equal element volumes
+    assert np.abs(gt - g).max() > 1e-3 and gt.min() >= 0 and gt.max() <= 1
+    a, b = rng.standard_normal(m.elem_shape), rng.standard_normal(m.elem_shape)
+    np.testing.assert_allclose(np.sum(a * O.pde_filter(m, b, r_x, r_t)), np.sum(b * O.pde_filter(m, a, r_x, r_t)),
+                               rtol=1e-12)
+
+
+def test_filter_of_an_extruded_design_is_time_constant():
+    """A time-constant design filtered on the full space-time mesh gives the same value on every slab,
+    equal to the one-slab (spatial) filter used for extruded designs."""
+    m = O.Mesh((5, 4), 6, bc="none")
+    g2 = np.random.default_rng(32).random((4, 5))
+    r_x, r_t = 0.5, 0.4
+    full = O.pde_filter(m, np.broadcast_to(g2[None], m.elem_shape).copy(), r_x, r_t)
+    one = O.pde_filter(m, g2, r_x, r_t)
+    for n in range(m.nt):
+        np.testing.assert_allclose(full[n], one, rtol=1e-12)
+
+
+def test_heaviside_projection_values_and_derivative():
+    x = np.linspace(0.0, 1.0, 21)
+    for beta, eta in ((32.0, 0.5), (8.0, 0.3)):
+        H = O.heaviside(x, beta, eta)
+        np.testing.assert_allclose(H[[0, -1]], [0.0, 1.0], atol=1e-15)
+        assert np.all(np.diff(H) > 0)
+        h = 1e-6
+        fd = (O.heaviside(x + h, beta, eta) - O.heaviside(x - h, beta, eta)) / (2 * h)
+        np.testing.assert_allclose(O.heaviside_derivative(x, beta, eta), fd, rtol=1e-6, atol=1e-9)
+    np.testing.assert_allclose(O.heaviside(np.array([0.5]), 32.0, 0.5), [0.5], atol=1e-15)
+
+
+@pytest.mark.parametrize("spacetime", [False, True])
+def test_filtered_projected_compliance_gradient_matches_central_differences(spacetime):
+    """phi(gamma) = compliance of the design H(F gamma): the chain rule F (H' * dphi/dgamma_bar) with
+    the adjoint sensitivities equals central differences of the whole chain."""
+    m = O.Mesh((4, 4), 4, mat=O.Material(), bc="patch_left", bc_width=0.5)
+    rng = np.random.default_rng(33)
+    g = 0.3 + 0.4 * rng.random(m.elem_shape if spacetime else (4, 4))
+    r_x, r_t, beta, eta = 0.5, 0.5, 8.0, 0.5
+
+    def phi(gam):
+        gb, _ = O.design_chain(m, gam, r_x, r_t, beta, eta)
+        sol = O.forward(m, gb, "uniform", 1.0)
+        return O.compliance(sol.f, sol.s), sol, gb
+
+    p0, sol, gb = phi(g)
+    _, gt = O.design_chain(m, g, r_x, r_t, beta, eta)
+    lam = O.adjoint(sol.A, sol.f, O.dirichlet_mask(m), sol.lu)
+    dphys = O.sensitivities(m, gb, sol.s, lam, extruded=not spacetime)
+    grad = O.chain_rule(m, dphys, gt, r_x, r_t, beta, eta)
+    h = 1e-6
+    for flat in rng.choice(g.size, 5, replace=False):
+        idx = np.unravel_index(flat, g.shape)
+        gp, gm_ = g.copy(), g.copy()
+        gp[idx] += h
+        gm_[idx] -= h
+        fd = (phi(gp)[0] - phi(gm_)[0]) / (2 * h)
+        np.testing.assert_allclose(grad[idx], fd, rtol=2e-6, atol=1e-10 * abs(p0))
