@@ -184,6 +184,26 @@ st_status st_solve_forward(st_mesh* m, const st_source* q, const st_options* o, 
 st_status st_solve_adjoint(st_mesh* m, const st_objective* obj, const st_options* o,
                            double* phi_out, st_stats* stats);
 
+/* PDE filter of an element field (Sec. 3.3.2): solves -div(D grad psi) + psi = gamma over the
+ * space-time domain, D = diag(r_x^2/12 per spatial axis, r_t^2/12 in time), natural boundary
+ * conditions, with the mesh's trilinear space-time elements ((M + K) psi = T gamma, T_ie =
+ * v_e / n_v) by Jacobi-preconditioned conjugate gradients to ||r|| <= rtol ||T gamma||, and
+ * returns the element means of psi.  in/out: element fields of `count` values (spatial elements
+ * for a time-constant field, solved on one slab, or all space-time elements), host or device
+ * per mem.  r_x, r_t <= 0 take the paper's minimum 2.4 h_min and 2.4 dt.  The filtered field
+ * of a field equal to 1 is 1 and the element sum is preserved.  The filter is symmetric, so the
+ * chain rule of the sensitivities is the same call: d phi / d gamma = filter(H'(gamma~) *
+ * d phi / d gamma_bar).  *iterations (may be NULL) receives the CG iterations.
+ * ST_ERR_NOT_CONVERGED: max_it reached (out holds the last iterate's means); ST_ERR_NUMERIC:
+ * a NaN or infinite input.  Uses scratch memory held by the mesh (allocated at the first call). */
+st_status st_filter(st_mesh* m, const double* in, double* out, size_t count, int mem, double r_x, double r_t,
+                    double rtol, int max_it, int* iterations);
+/* Heaviside projection of Sec. 3.3.2, element by element on the mesh's device:
+ * out = (tanh(beta eta) + tanh(beta (in - eta))) / (tanh(beta eta) + tanh(beta (1 - eta))) and its
+ * derivative dout (either may be NULL).  Paper values: eta = 0.5, beta = 32. */
+st_status st_heaviside(st_mesh* m, const double* in, double* out, double* dout, size_t count, int mem, double beta,
+                       double eta);
+
 /* Batched solves (no counterpart in the paper: concurrent design iterations of the paper's
  * optimisation loop issue many such solves).  The meshes (all on one device, each at most
  * once) are solved together: every FGMRES restart cycle of every mesh is captured into ONE CUDA

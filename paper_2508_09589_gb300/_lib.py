@@ -105,6 +105,10 @@ SIGNATURES = {
     "st_solve_forward": (C.c_int, [C.c_void_p, C.POINTER(Source), C.POINTER(Options), C.POINTER(Stats)]),
     "st_solve_adjoint": (C.c_int, [C.c_void_p, C.POINTER(Objective), C.POINTER(Options), C.POINTER(C.c_double),
                                    C.POINTER(Stats)]),
+    "st_filter": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_int, C.c_double, C.c_double,
+                            C.c_double, C.c_int, C.POINTER(C.c_int)]),
+    "st_heaviside": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_int, C.c_double,
+                               C.c_double]),
     "st_solve_forward_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(Options), C.c_void_p,
                                          C.c_void_p]),
     "st_solve_adjoint_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(Options), C.c_void_p,

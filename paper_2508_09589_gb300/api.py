@@ -272,6 +272,36 @@ class Mesh:
         L.check(L.lib().st_coarse_inverse(self._h, C.c_void_p(out.ctypes.data), out.size), "st_coarse_inverse")
         return out.reshape(n, n)
 
+    # -- design filter and projection (Sec. 3.3.2)
+    def filter(self, gamma, r_x: float = 0.0, r_t: float = 0.0, rtol: float = 1e-12, max_it: int = 2000, out=None):
+        """PDE-filtered element field (st_filter); numpy in -> numpy out, CUDA tensor in -> tensor out.
+        Returns (field, CG iterations)."""
+        its = C.c_int()
+        if _is_torch(gamma):
+            import torch
+            out = out if out is not None else torch.empty_like(gamma)
+            _sync_torch(gamma)
+            L.check(L.lib().st_filter(self._h, C.c_void_p(gamma.data_ptr()), C.c_void_p(out.data_ptr()), gamma.numel(),
+                                      L.MEM_DEVICE, float(r_x), float(r_t), float(rtol), int(max_it), C.byref(its)),
+                    "st_filter")
+            return out, its.value
+        arr = np.ascontiguousarray(np.asarray(gamma, dtype=np.float64))
+        res = np.empty_like(arr)
+        L.check(L.lib().st_filter(self._h, C.c_void_p(arr.ctypes.data), C.c_void_p(res.ctypes.data), arr.size,
+                                  L.MEM_HOST, float(r_x), float(r_t), float(rtol), int(max_it), C.byref(its)),
+                "st_filter")
+        return res, its.value
+
+    def heaviside(self, x, beta: float = 32.0, eta: float = 0.5):
+        """(H(x), H'(x)) of the projection (st_heaviside), host arrays."""
+        arr = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+        h = np.empty_like(arr)
+        dh = np.empty_like(arr)
+        L.check(L.lib().st_heaviside(self._h, C.c_void_p(arr.ctypes.data), C.c_void_p(h.ctypes.data),
+                                     C.c_void_p(dh.ctypes.data), arr.size, L.MEM_HOST, float(beta), float(eta)),
+                "st_heaviside")
+        return h, dh
+
     def apply_timer(self, enable: bool = True):
         """Start (reset) or stop CUDA-event timing of the level-0 smoother operator apply."""
         L.check(L.lib().st_apply_timer(self._h, int(bool(enable))), "st_apply_timer")

@@ -43,3 +43,33 @@ class SpaceTimeObjective(torch.autograd.Function):
 def objective(gamma: torch.Tensor, mesh: Mesh, src=None, opts=None, kind: str = "compliance", P: int = 20):
     """phi(gamma) with d phi / d gamma available through autograd."""
     return SpaceTimeObjective.apply(gamma, mesh, src or source(), opts or options(), kind, P)
+
+
+class FilterProject(torch.autograd.Function):
+    """Physical design gamma_bar = H(F gamma) of Sec. 3.3.2 (PDE filter st_filter, Heaviside
+    projection st_heaviside); the backward pass is F (H'(gamma~) * grad), the same filter
+    (it is symmetric)."""
+
+    @staticmethod
+    def forward(ctx, gamma: torch.Tensor, mesh: Mesh, r_x: float, r_t: float, beta: float, eta: float,
+                rtol: float = 1e-12):
+        g = gamma.detach().to(dtype=torch.float64).cpu().contiguous().numpy()
+        gt, _ = mesh.filter(g, r_x, r_t, rtol)
+        gb, dh = mesh.heaviside(gt, beta, eta)
+        ctx.mesh, ctx.dh, ctx.args = mesh, dh, (r_x, r_t, rtol)
+        ctx.device, ctx.dtype, ctx.shape = gamma.device, gamma.dtype, gamma.shape
+        return torch.from_numpy(gb).to(device=gamma.device, dtype=gamma.dtype)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        r_x, r_t, rtol = ctx.args
+        gin = grad_out.detach().to(torch.float64).cpu().numpy() * ctx.dh
+        g, _ = ctx.mesh.filter(gin, r_x, r_t, rtol)
+        return (torch.from_numpy(g).reshape(ctx.shape).to(device=ctx.device, dtype=ctx.dtype),
+                None, None, None, None, None, None)
+
+
+def filter_project(gamma: torch.Tensor, mesh: Mesh, r_x: float = 0.0, r_t: float = 0.0, beta: float = 32.0,
+                   eta: float = 0.5):
+    """gamma_bar = H(F gamma), differentiable (filter radii <= 0: the paper's 2.4 h and 2.4 dt)."""
+    return FilterProject.apply(gamma, mesh, r_x, r_t, beta, eta)

@@ -1226,6 +1226,143 @@ st_status solve_batch(Mesh* const* ms, int n, bool adjoint, const st_options* op
     return worst;
 }
 
+// ---------------------------------------------------------------- PDE filter (Sec. 3.3.2)
+// Coefficient table of the filter matrix: for each node class (lower boundary, interior, upper
+// boundary along each axis; axes ordered t, [z,] y, x with x fastest) the coefficients of its
+// 3^(SD+1) neighbours, products of the 1-D mass (h/6 [1 4 1], boundary diagonal h/3) and
+// stiffness (1/h [-1 2 -1], boundary diagonal 1/h) entries of each axis.
+static void filter_table(int sd, const double* h, double dt, double rx, double rt, std::vector<double>& tab) {
+    const int na = sd + 1;  // axes: 0 = x ... sd-1 spatial, sd = t
+    int no = 1;
+    for (int a = 0; a < na; ++a) no *= 3;
+    tab.assign((size_t)no * no, 0.0);
+    auto m1 = [](int c, int o, double hh) {
+        if (o == 0) return c == 1 ? 2.0 * hh / 3.0 : hh / 3.0;
+        if (o < 0) return c == 0 ? 0.0 : hh / 6.0;
+        return c == 2 ? 0.0 : hh / 6.0;
+    };
+    auto k1 = [](int c, int o, double hh) {
+        if (o == 0) return c == 1 ? 2.0 / hh : 1.0 / hh;
+        if (o < 0) return c == 0 ? 0.0 : -1.0 / hh;
+        return c == 2 ? 0.0 : -1.0 / hh;
+    };
+    const double Dx = rx * rx / 12.0, Dt = rt * rt / 12.0;
+    for (int cls = 0; cls < no; ++cls)
+        for (int o = 0; o < no; ++o) {
+            int c[4], off[4];
+            double sz[4];
+            int cc = cls, oo = o;
+            for (int a = 0; a < na; ++a) {  // x first (fastest) ... t last
+                c[a] = cc % 3;
+                off[a] = oo % 3 - 1;
+                cc /= 3;
+                oo /= 3;
+                sz[a] = a < sd ? h[a] : dt;
+            }
+            double mass = 1.0;
+            for (int a = 0; a < na; ++a) mass *= m1(c[a], off[a], sz[a]);
+            double v = mass;
+            for (int a = 0; a < na; ++a) {
+                double t = (a < sd ? Dx : Dt) * k1(c[a], off[a], sz[a]);
+                for (int b = 0; b < na; ++b)
+                    if (b != a) t *= m1(c[b], off[b], sz[b]);
+                v += t;
+            }
+            tab[(size_t)cls * no + o] = v;
+        }
+}
+
+st_status filter(Mesh* m, const double* in, double* out, size_t count, int mem, double rx, double rt, double rtol,
+                 int max_it, int* iters) {
+    if (!in || !out) return fail(ST_ERR_ARG, "null argument");
+    const Geom& g0 = m->lv[0].g;
+    const bool extruded = (long long)count == g0.sp_elems;
+    if (!extruded && (long long)count != g0.sp_elems * g0.net)
+        return fail(ST_ERR_ARG, "count must be the number of spatial or space-time elements");
+    if (!(rtol > 0) || max_it < 1) return fail(ST_ERR_ARG, "rtol and max_it must be positive");
+    Geom fg = g0;
+    if (extruded) {  // a time-constant field: one slab (its filtered field is time-constant)
+        fg.net = 1;
+        fg.nt1 = 2;
+        fg.dt = m->desc.tau;
+        fg.nnodes = 2 * fg.plane;
+    }
+    double hmin = fg.h[0];
+    for (int d = 1; d < m->sd; ++d) hmin = std::min(hmin, fg.h[d]);
+    if (!(rx > 0)) rx = 2.4 * hmin;
+    if (!(rt > 0)) rt = 2.4 * g0.dt;
+    const long long N = fg.nnodes;
+    const int no = m->sd == 2 ? 27 : 81;
+    const long long need = 7 * N + 2 * (long long)count + (long long)no * no + 8;
+    cudaSetDevice(m->device);
+    if (m->fbuf_len < need) {
+        m->release(m->fbuf);
+        m->fbuf = nullptr;
+        m->fbuf_len = 0;
+        CKS(m->alloc((void**)&m->fbuf, need * sizeof(double)));
+        m->fbuf_len = need;
+    }
+    double *b = m->fbuf, *x = b + N, *r = x + N, *z = r + N, *p = z + N, *q = p + N, *dinv = q + N;
+    double* ein = dinv + N;
+    double* eout = ein + count;
+    double* tab = eout + count;
+    double* sc = tab + (long long)no * no;
+    std::vector<double> htab;
+    filter_table(m->sd, fg.h, fg.dt, rx, rt, htab);
+    cudaStream_t s = m->stream;
+    CK(cudaMemcpyAsync(tab, htab.data(), htab.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ein, in, count * sizeof(double),
+                       mem == ST_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    double ve = fg.dt;
+    for (int d = 0; d < m->sd; ++d) ve *= fg.h[d];
+    launch_filter_rhs(m->sd, fg, ein, ve / (double)(1 << (m->sd + 1)), b, s);
+    launch_filter_apply(m->sd, fg, tab, nullptr, nullptr, dinv, s);
+    CK(cudaMemsetAsync(x, 0, N * sizeof(double), s));
+    CK(cudaMemcpyAsync(r, b, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(p, 0, N * sizeof(double), s));
+    launch_cg_zp(N, 0.0, dinv, r, z, p, s);  // z = D^-1 r, p = z
+    double hs[2];
+    launch_dot64(fg, r, z, sc, m->rb, s);
+    launch_dot64(fg, b, b, sc + 1, m->rb, s);
+    CK(cudaMemcpyAsync(hs, sc, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double rz = hs[0];
+    const double bn = sqrt(hs[1]);
+    if (!std::isfinite(bn)) return fail(ST_ERR_NUMERIC, "NaN/Inf in the field to filter");
+    int it = 0;
+    bool conv = !(bn > 0);
+    while (!conv && it < max_it) {
+        launch_filter_apply(m->sd, fg, tab, p, q, nullptr, s);
+        launch_dot64(fg, p, q, sc, m->rb, s);
+        CK(cudaMemcpyAsync(hs, sc, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (!(hs[0] > 0) || !std::isfinite(hs[0])) return fail(ST_ERR_NUMERIC, "filter CG breakdown (p^T A p <= 0)");
+        const double alpha = rz / hs[0];
+        launch_cg_xr(N, alpha, p, q, x, r, s);
+        launch_cg_zp(N, 0.0, dinv, r, z, z, s);  // z = D^-1 r
+        launch_dot64(fg, r, r, sc, m->rb, s);
+        launch_dot64(fg, r, z, sc + 1, m->rb, s);
+        CK(cudaMemcpyAsync(hs, sc, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        ++it;
+        if (!std::isfinite(hs[0])) return fail(ST_ERR_NUMERIC, "NaN/Inf in the filter solve");
+        if (sqrt(hs[0]) <= rtol * bn) {
+            conv = true;
+            break;
+        }
+        const double beta = hs[1] / rz;
+        rz = hs[1];
+        launch_cg_p(N, beta, z, p, s);
+    }
+    launch_filter_mean(m->sd, fg, x, eout, s);
+    CK(cudaMemcpyAsync(out, eout, count * sizeof(double),
+                       mem == ST_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (iters) *iters = it;
+    if (!conv) return fail(ST_ERR_NOT_CONVERGED, "filter CG did not reach rtol within max_it iterations");
+    return ST_OK;
+}
+
 }  // namespace st
 
 // ================================================================= C ABI
@@ -1431,6 +1568,40 @@ st_status st_solve_adjoint(st_mesh* m, const st_objective* obj, const st_options
     st_status r = st::solve(mm, true, o, stats);
     mm->have_adjoint = (r == ST_OK || r == ST_ERR_NOT_CONVERGED);
     return r;
+}
+
+st_status st_filter(st_mesh* m, const double* in, double* out, size_t count, int mem, double r_x, double r_t,
+                    double rtol, int max_it, int* iterations) {
+    if (!m) return fail(ST_ERR_ARG, "null mesh");
+    return st::filter(M(m), in, out, count, mem, r_x, r_t, rtol, max_it, iterations);
+}
+
+st_status st_heaviside(st_mesh* m, const double* in, double* out, double* dout, size_t count, int mem, double beta,
+                       double eta) {
+    if (!m || !in || (!out && !dout)) return fail(ST_ERR_ARG, "null argument");
+    if (!(beta > 0) || !(eta > 0 && eta < 1)) return fail(ST_ERR_ARG, "beta > 0 and 0 < eta < 1 required");
+    Mesh* mm = M(m);
+    cudaSetDevice(mm->device);
+    cudaStream_t s = mm->stream;
+    const double* din = in;
+    double *o1 = out, *o2 = dout;
+    double* tmp = nullptr;
+    if (mem == ST_MEM_HOST) {
+        CKS(mm->alloc((void**)&tmp, 3 * count * sizeof(double)));
+        CK(cudaMemcpyAsync(tmp, in, count * sizeof(double), cudaMemcpyHostToDevice, s));
+        din = tmp;
+        o1 = out ? tmp + count : nullptr;
+        o2 = dout ? tmp + 2 * count : nullptr;
+    }
+    st::launch_heaviside((long long)count, din, o1, o2, beta, eta, s);
+    if (mem == ST_MEM_HOST) {
+        if (out) CK(cudaMemcpyAsync(out, o1, count * sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (dout) CK(cudaMemcpyAsync(dout, o2, count * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (tmp) mm->release(tmp);
+    if (e != cudaSuccess) return fail(ST_ERR_CUDA, cudaGetErrorString(e));
+    return ST_OK;
 }
 
 st_status st_solve_forward_batch(st_mesh* const* m, int count, const st_source* q, const st_options* o,

@@ -316,6 +316,21 @@ void launch_sens(int sd, const OpL0<double>& op, const double* s, const double* 
 void launch_stencil_build(int lvl, const OpL0<double>& o0, const OpLc<double>& oc, double* st64, float* st32,
                           unsigned char* dir, cudaStream_t s);
 
+// ---- PDE filter and projection (k_filter.cu, Sec. 3.3.2)
+// y = (M_f + K_f) x with the class table tab (3^(SD+1) classes x 3^(SD+1) offsets), or dinv = the
+// inverse diagonal when dinv is given; rhs: (T gamma) = scale * sum of the adjacent elements'
+// values; mean: element means of a nodal field; CG vector updates (z and p of cg_zp may be the
+// same vector); projection H and H'.
+void launch_filter_apply(int sd, const Geom& g, const double* tab, const double* x, double* y, double* dinv,
+                         cudaStream_t s);
+void launch_filter_rhs(int sd, const Geom& g, const double* gam, double scale, double* out, cudaStream_t s);
+void launch_filter_mean(int sd, const Geom& g, const double* psi, double* out, cudaStream_t s);
+void launch_cg_xr(long long n, double a, const double* p, const double* q, double* x, double* r, cudaStream_t s);
+void launch_cg_zp(long long n, double b, const double* dinv, const double* r, double* z, double* p, cudaStream_t s);
+void launch_cg_p(long long n, double b, const double* z, double* p, cudaStream_t s);
+void launch_heaviside(long long n, const double* in, double* out, double* dout, double beta, double eta,
+                      cudaStream_t s);
+
 // element storage sizes
 inline int nsp(int sd) { return 1 << sd; }
 inline int nsym(int sd) { return nsp(sd) * (nsp(sd) + 1) / 2; }

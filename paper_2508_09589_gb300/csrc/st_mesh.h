@@ -128,6 +128,11 @@ struct Mesh {
     long long at_launches = 0;
     void timer_collect();
 
+    // PDE filter scratch: 7 nodal vectors (rhs, x, r, z, p, q, D^-1), 2 element fields, the
+    // class table and 4 scalars
+    double* fbuf = nullptr;
+    long long fbuf_len = 0;
+
     std::vector<void*> allocs;
     std::vector<size_t> alloc_sizes;
     long long bytes_held = 0;
@@ -175,5 +180,10 @@ struct Mesh {
 // once per cycle.  The graph runs on the first mesh's stream.
 st_status solve_batch(Mesh* const* ms, int n, bool adjoint, const st_options* op, st_stats* stats,
                       st_status* status);
+
+// PDE filter of an element field (Sec. 3.3.2) on the mesh's geometry (one slab for an extruded
+// field), by Jacobi-preconditioned CG; *iters receives the iterations.
+st_status filter(Mesh* m, const double* in, double* out, size_t count, int mem, double rx, double rt, double rtol,
+                 int max_it, int* iters);
 
 }  // namespace st
