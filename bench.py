@@ -256,6 +256,11 @@ def run_native(args):
                 line["serving"] = serving_bench(args)
             except Exception as e:  # noqa: BLE001
                 line["serving"] = {"error": f"{type(e).__name__}: {e}"}
+        if args.ablation:
+            try:
+                line["coarsening_ablation"] = coarsening_ablation(args)
+            except Exception as e:  # noqa: BLE001
+                line["coarsening_ablation"] = {"error": f"{type(e).__name__}: {e}"}
         for name in args.configs:
             try:
                 line.setdefault("configs", {})[name] = config_leg(name, args)
@@ -518,6 +523,38 @@ def config_leg(name: str, args, steps: int = 1, warmup: int = 1):
     return out
 
 
+def coarsening_ablation(args):
+    """Semi- against full space-time coarsening on the headline workload (the ablation of Sec.
+    5.1.2): the same mixed-precision forward + adjoint solve to 1e-8, with every level halving
+    space and time together; outer iterations, levels and time of one step after one warm-up."""
+    import torch
+    from paper_2508_09589_gb300 import Mesh, options, source
+    w = W.WORKLOADS[args.workload]
+    g = torch.tensor(W.make_design(w).reshape(-1), dtype=torch.float64, device="cuda")
+    layout = "extruded" if w.extruded else "spacetime"
+    src = source(w.source, w.source_q0, w.source_a, w.source_b, w.source_f)
+    opt = options(rtol=1e-8, precision="mixed", max_it=600)
+    out = {}
+    for mode in ("semi", "full"):
+        mesh = Mesh(w.ns, w.nt, material=w.material, bc=w.bc, bc_width=w.bc_width, tau=w.tau, coarsening=mode)
+        ts = []
+        for q in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            mesh.set_design(g, layout)
+            f = mesh.solve_forward(src, opt, allow_not_converged=True)
+            _, a = mesh.solve_adjoint("compliance", opts=opt, allow_not_converged=True)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        lev = mesh.levels()
+        out[mode] = {"levels": len(lev), "coarsest": list(lev[-1]["ns"]) + [lev[-1]["nt"]],
+                     "outer_its_fwd": f["outer_its"], "outer_its_adj": a["outer_its"],
+                     "converged": bool(f["converged"] and a["converged"]),
+                     "ms_per_step": 1e3 * ts[-1], "ms_per_outer_it_fwd": 1e3 * f["seconds"] / max(1, f["outer_its"])}
+        mesh.close()
+    return out
+
+
 def run_vcycles(args):
     """Kernel-profiling mode: design set-up and K mixed-precision V-cycles on the workload
     (no Krylov solve, so only the multigrid storage is resident: a few GB at 256^2 x 256)."""
@@ -625,6 +662,8 @@ def main():
                     help="further workloads timed after the headline one (each on its own mesh)")
     ap.add_argument("--cpu-sample", default="34", help="oracle sample n (n^3 mesh, about 10-15 s of CPU work)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-ablation", dest="ablation", action="store_false",
+                    help="skip the semi- against full-coarsening comparison")
     ap.add_argument("--serve-requests", type=int, default=96, help="mixed-precision serving requests (0 skips)")
     ap.add_argument("--serve-fp64-requests", type=int, default=48, help="all-FP64 serving requests (0 skips)")
     ap.add_argument("--serve-slots", type=int, default=4, help="server slots (concurrent batches)")

@@ -526,3 +526,36 @@ def test_few_time_planes_smoother_and_solve(nt):
         st = gm.solve_forward(rtol=parity_rtol(sol.A, sol.s, sol.f), precision=precision, max_it=400)
         assert st["converged"]
         assert rel_err(gm.state("T"), sol.s) < 1e-10
+
+
+@pytest.mark.parametrize("i", [0, 1, 3])
+def test_full_coarsening_hierarchy_and_solves(i):
+    """Full space-time coarsening (both directions halved on every level, the ablation of Sec.
+    5.1.2): the hierarchy, every level's Galerkin operator and transfers, and the forward and
+    adjoint solves match the oracle in FP64 and mixed precision."""
+    om, g = _case(i)
+    gm = gpu_mesh(om, coarse_dof_cap=300, coarsening="full")
+    gm.set_design(g)
+    olev = O.hierarchy(om, coarse_cap=300, mode="full")
+    assert [(tuple(L.ns), L.nt, L.to_next) for L in olev] == [(L["ns"], L["nt"], L["to_next"]) for L in gm.levels()]
+    mg = O.build_mg(om, g, olev)
+    rng = np.random.default_rng(5)
+    for l in range(len(mg)):
+        N = mg[l].A.shape[0]
+        x = rng.standard_normal(N)
+        y = torch.empty(N, dtype=torch.float64, device="cuda")
+        gm.apply(l, _dev(x), y, "fp64")
+        assert rel_err(y.cpu().numpy(), mg[l].A @ x) < 1e-12, l
+        if l + 1 < len(mg):
+            Pt = mg[l].Pt
+            rc = torch.empty(Pt.shape[1], dtype=torch.float64, device="cuda")
+            gm.restrict(l, _dev(x), rc, "fp64")
+            assert rel_err(rc.cpu().numpy(), Pt.T @ x) < 1e-14
+    sol = O.forward(om, g, "uniform", 1.0)
+    lam = O.adjoint(sol.A, sol.f, O.dirichlet_mask(om), sol.lu)
+    for precision in ("fp64", "mixed"):
+        st = gm.solve_forward(rtol=parity_rtol(sol.A, sol.s, sol.f), precision=precision, max_it=600)
+        assert st["converged"]
+        assert rel_err(gm.state("T"), sol.s) < (1e-10 if precision == "fp64" else 1e-6)
+        gm.solve_adjoint("compliance", rtol=parity_rtol(sol.A.T, lam, sol.f), precision=precision, max_it=600)
+        assert rel_err(gm.state("lambda"), lam) < (1e-10 if precision == "fp64" else 1e-6)

@@ -98,3 +98,16 @@ def test_create_mesh_without_gpu_fails_cleanly(L):
     with pytest.raises(STError) as e:
         Mesh((8, 8), 8)
     assert e.value.code == -6
+
+
+@pytest.mark.parametrize("ns,nt,cap", [((32, 32), 32, 300), ((64, 48), 16, 500), ((16, 16, 16), 16, 300)])
+def test_full_coarsening_planner_matches_oracle(L, ns, nt, cap):
+    """Full space-time coarsening (the ablation of Sec. 5.1.2): every level halves space and time
+    together while both can be halved, as the oracle's hierarchy in mode 'full'."""
+    from paper_2508_09589_gb300 import plan_hierarchy
+    om = O.Mesh(ns, nt, mat=O.Material(C_ins=1.0, C_con=1.0, k_ins=1e-3, k_con=1.0, p_c=1, p_k=3))
+    ref = O.hierarchy(om, coarse_cap=cap, mode="full")
+    got = plan_hierarchy(ns, nt, material=dict(C_ins=1.0, C_con=1.0, k_ins=1e-3, k_con=1.0, p_c=1, p_k=3),
+                         coarse_dof_cap=cap, coarsening="full")
+    assert [(tuple(L_.ns), L_.nt, L_.to_next) for L_ in ref] == [(g["ns"], g["nt"], g["to_next"]) for g in got]
+    assert all(g["to_next"] in ("full", "") for g in got)
