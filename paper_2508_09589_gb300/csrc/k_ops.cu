@@ -20,6 +20,10 @@ bool g_smstep = [] {
     const char* e = getenv("ST_SMSTEP");
     return !(e && atoi(e) == 0);
 }();
+bool g_l0st = [] {
+    const char* e = getenv("ST_L0ST");
+    return !(e && atoi(e) == 0);
+}();
 
 void note_launch(cudaStream_t s, long long n) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -496,6 +500,16 @@ void launch_apply_l0(int sd, const OpL0<T>& op, bool tr, const T* x, T* y, cudaS
         launch_pdl(km_apply<T>, grid, block, 0, s, op.g, op.st_coef[tr ? 1 : 0], op.st_dir, mg.chunk, x, y);
         return;
     }
+    if constexpr (std::is_same<T, float>::value) {
+        const void* vecs[2] = {x, y};
+        if (l0_march_usable(sd, op, vecs, 2)) {
+            if (sd == 2)
+                launch_l0st(3, tr, op, x, nullptr, nullptr, y, 0, 0, nullptr, RedBuf{}, s);
+            else
+                launch_l0x3(3, tr, op, x, nullptr, nullptr, y, 0, 0, nullptr, RedBuf{}, s);
+            return;
+        }
+    }
     const LaunchCfg c = node_cfg(op.g);
     const OpLc<T> oc = dummy_lc<T>(op.g);
     ST_SD_DISPATCH(sd, if (tr) launch_pdl(k_apply<SD, T, 0, true>, c.grid, c.block, 0, s, op, oc, x, y);
@@ -552,6 +566,16 @@ void launch_residual(int sd, int lvl, const OpL0<T>& o0, const OpLc<T>& oc, bool
             return;
         }
     }
+    if constexpr (std::is_same<T, float>::value) {
+        const void* vecs[3] = {b, x, r};
+        if (lvl == 0 && l0_march_usable(sd, o0, vecs, 3)) {
+            if (sd == 2)
+                launch_l0st(1, tr, o0, x, nullptr, b, r, 0, 0, nullptr, RedBuf{}, s);
+            else
+                launch_l0x3(1, tr, o0, x, nullptr, b, r, 0, 0, nullptr, RedBuf{}, s);
+            return;
+        }
+    }
     const LaunchCfg c = node_cfg(lvl == 0 ? o0.g : oc.g);
     if (lvl == 0) {
         ST_SD_DISPATCH(sd, if (tr) launch_pdl(k_residual<SD, T, 0, true>, c.grid, c.block, 0, s, o0, oc, b, x, r);
@@ -584,6 +608,30 @@ static void record_timing_event(cudaEvent_t e, cudaStream_t s) {
     if (cudaEventRecordWithFlags(e, s, flags) != cudaSuccess) cudaGetLastError();
 }
 
+// The level-0 space-time kernels (k_l0st.cu) where the instantiation can use them (FP32,
+// 2-D, level 0) and on is set; false when the caller must launch the node-parallel kernel.
+template <int SD, typename T, int LV>
+static bool launch_l0st_if(bool on, int mode, bool tr, const OpL0<T>& o0, const T* u, const T* dinv, const T* b,
+                           T* out, int j, int steps, SmState* st, RedBuf rb, cudaStream_t s) {
+    if constexpr (LV == 0 && std::is_same<T, float>::value) {
+        if (on) {
+            if constexpr (SD == 2)
+                launch_l0st(mode, tr, o0, u, dinv, b, out, j, steps, st, rb, s);
+            else
+                launch_l0x3(mode, tr, o0, u, dinv, b, out, j, steps, st, rb, s);
+            return true;
+        }
+    }
+    return false;
+}
+
+// Whether the level-0 marching kernels of k_l0st.cu (space-time 2-D designs) or k_l0x3.cu
+// (extruded 3-D designs) take these vectors.
+static bool l0_march_usable(int sd, const OpL0<float>& op, const void* const* vecs, int nvec) {
+    if (!g_l0st) return false;
+    return sd == 2 ? l0st_usable(op, vecs, nvec) : l0x3_usable(op, vecs, nvec);
+}
+
 template <int SD, typename T, int LV, bool TR>
 static void smooth_impl(const OpL0<T>& o0, const OpLc<T>& oc, const T* b, T* x, const T* dinv, Basis<T> U, T* w,
                         T* w2, int steps, bool zero_init, SmState* st, RedBuf rb, cudaStream_t s,
@@ -599,6 +647,14 @@ static void smooth_impl(const OpL0<T>& o0, const OpLc<T>& oc, const T* b, T* x, 
     if (zero_init) U.u[0] = const_cast<T*>(b);
     Ptrs<T> P{};
     for (int q = 0; q <= steps; ++q) P.p[q] = U.u[q];
+    // level 0 of a space-time 2-D or an extruded 3-D design in FP32: the time-marching kernels
+    // of k_l0st.cu and k_l0x3.cu
+    bool l0st = false;
+    if constexpr (LV == 0 && std::is_same<T, float>::value) {
+        const void* vecs[4 + kMaxSmooth + 1] = {b, x, dinv, w};
+        for (int q = 0; q <= steps; ++q) vecs[4 + q] = U.u[q];
+        l0st = !march && l0_march_usable(SD, o0, vecs, 4 + steps + 1);
+    }
     // The fused Arnoldi step (one pass per step, halo recomputed) only pays on tiny, latency
     // bound levels; on large levels the split apply / dots / update kernels stream faster.
     constexpr long long kFusedMaxNodes = 15000;
@@ -610,7 +666,7 @@ static void smooth_impl(const OpL0<T>& o0, const OpLc<T>& oc, const T* b, T* x, 
         note_launch(s);
         if (march)
             launch_pdl(km_sm_start<T>, mgrid, mblock, 0, s, g, coef, dir, mg.chunk, b, x, U.u[0], steps, st, rb);
-        else
+        else if (!launch_l0st_if<SD, T, LV>(l0st, 2, TR, o0, x, nullptr, b, U.u[0], 0, steps, st, rb, s))
             launch_pdl(k_sm_start<SD, T, LV, TR, false>, c.grid, c.block, 0, s, o0, oc, b, x, U.u[0], steps, st, rb);
     }
     if (fused) {
@@ -633,7 +689,7 @@ static void smooth_impl(const OpL0<T>& o0, const OpLc<T>& oc, const T* b, T* x, 
             return;
         }
     }
-    if (march && sc && w2 != nullptr && g_smstep && sm_step_aligned<T>(P, steps, w, w2, N)) {
+    if (march && sc && w2 != nullptr && g_smstep && sm_step_aligned<T>(P, steps, w, w2, N, g.plane)) {
         // one kernel per Arnoldi step (update of step j - 1, apply and dots of step j), w_j
         // alternating between w and w2; then the last update (norm of u_steps and the back
         // substitution) and the combination
@@ -660,7 +716,7 @@ static void smooth_impl(const OpL0<T>& o0, const OpLc<T>& oc, const T* b, T* x, 
                        dinv, U.u[j], w, j, st);
         else if (march)
             launch_pdl(km_sm_applyw<T>, mgrid, mblock, 0, s, g, coef, dir, mg.chunk, dinv, U.u[j], w, j, st);
-        else
+        else if (!launch_l0st_if<SD, T, LV>(l0st, 0, TR, o0, U.u[j], dinv, nullptr, w, j, steps, st, rb, s))
             launch_pdl(k_sm_applyw<SD, T, LV, TR>, c.grid, c.block, 0, s, o0, oc, dinv, U.u[j], w, j, st);
         if (ev) record_timing_event(ev[2 * j + 1], s);
         launch_dots<T>(N, w, P, j + 1, j, 0, st, rb, s);

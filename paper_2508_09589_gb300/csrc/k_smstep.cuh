@@ -4,25 +4,51 @@
 //   u_j = s_{j-1} w_{j-1} - sum_{q<j} H[q][j-1] s_q u_q        (basis update of step j - 1)
 //   w_j = A D^-1 u_j                                          (27-point stencil)
 //   (w_j, u_q) for q <= j and ||u_j||^2                      (one deterministic reduction)
-// A block owns a 32 x 8 tile of spatial nodes and a chunk of time planes.  For each plane,
-// the tile with its one-node halo (34 x 10 cells) of w_{j-1} and u_0 .. u_{j-1} is staged in
-// shared memory by cp.async in 16-byte chunks: each halo row is copied as the aligned
-// 16-byte chunks that cover it (10 per row in FP32), so a row sits at a per-row offset s
-// (the row start's position inside its first chunk).  Threads form u_j two elements at a
-// time into a staging buffer, writing the tile-interior values to global memory once and
-// adding their squares; the stencil reads u_j from that buffer, and the dots read u_q at the
-// row's node from the staged ring.  Against separate apply, dot and update passes this reads
-// the basis once instead of twice and w once instead of twice per step.  Step 0 applies the
-// stencil to u_0 and takes (w_0, u_0).  The last block closes Hessenberg column j - 1 (norm,
-// Givens rotation, breakdown test) and opens column j.  All vectors must start on 16-byte
-// boundaries (the launcher checks).
+// A block owns a 32 x 8 tile of spatial nodes and a chunk of time planes, and takes two planes
+// per iteration and per barrier, so that the 27 time-constant stencil coefficients held in
+// registers serve both.  For each plane, the tile with its one-node halo (34 x 10 cells) of
+// w_{j-1} and u_0 .. u_{j-1} is staged in a shared-memory ring by cp.async in 16-byte chunks:
+// each halo row is copied as the aligned 16-byte chunks that cover it (10 per row in FP32), so
+// a row sits at a per-row offset s (the row start's position inside its first chunk).  Lanes
+// form u_j two elements at a time and write it over w_{j-1} in the ring slot, storing the
+// tile-interior values to global memory once and adding their squares; the stencil reads u_j
+// there two planes later, and the dots read u_q at the row's node from the same slot.  Against
+// separate apply, dot and update passes this reads the basis once instead of twice and w once
+// instead of twice per step.  Step 0 applies the stencil to the staged u_0.  The last block
+// closes Hessenberg column j - 1 (norm, Givens rotation, breakdown test) and opens column j.
+// All vectors must start on 16-byte boundaries (the launcher checks).
 #include <stdint.h>
 
 #include <mutex>
 
-#include "st_device.cuh"
+#include "k_ring.cuh"
 
 namespace st {
+
+// Dynamic shared memory of one block when two blocks share an SM (228 KB per SM, 1 KB reserved
+// per block, about 1.5 KB of static shared memory for the reduction), and the opt-in maximum.
+constexpr long long kStepTwoBlocks = 114176;
+constexpr long long kStepMaxSmem = 232448;
+
+// Ring slots of the step kernel for NQ source vectors of es-byte elements: the five planes in
+// use by one iteration (the row m - 1 whose dots are due, the two planes whose stencils are
+// applied, the two planes being combined) plus D pairs of planes in flight: about 16 FP32 or 8
+// FP64 vector-planes, fewer where the ring would not leave room for two blocks per SM, at
+// least one pair.
+constexpr int step_ring_slots(int nq, int es) {
+    const int vw = 16 / es;
+    const long long plane = 10LL * ((vw - 1 + 34 + vw - 1) / vw) * vw;
+    const long long slot = (long long)nq * plane * es;
+    int d = (64 / es + 2 * nq - 1) / (2 * nq);
+    if (d > 6) d = 6;
+    const int fit = ((int)(kStepTwoBlocks / slot) - 5) / 2;
+    if (d > fit) d = fit < 1 ? 1 : fit;
+    return 5 + 2 * d;
+}
+constexpr long long step_smem_bytes(int nq, int es) {
+    const int vw = 16 / es;
+    return (long long)step_ring_slots(nq, es) * nq * 10LL * ((vw - 1 + 34 + vw - 1) / vw) * vw * es;
+}
 
 template <typename T, int NQ>
 struct StepRing {
@@ -32,62 +58,15 @@ struct StepRing {
     static constexpr int PLANE = 10 * ROW;                  // one vector-plane of the tile
     static constexpr int NCH = 10 * ROWC;                   // 16-byte chunk positions per vector-plane
     static constexpr int NPAIR = PLANE / 2;                 // element pairs per plane (combine units)
-    static constexpr int NPAR = 2 * NCH <= 256 ? 2 : 1;     // threads sharing one chunk position's copies
-    // ring of RING plane slots: PF = RING - 2 planes issued ahead (PF - 1 in flight while a
-    // plane is consumed: about 16 FP32 or 8 FP64 vector-planes per block, within 110 KB so that
-    // two blocks share an SM), plus the plane being combined and the one whose dots are due
-    static constexpr int K = 64 / (int)sizeof(T);
-    static constexpr int want = 3 + (K + NQ - 1) / NQ;
-    static constexpr size_t slot_bytes = (size_t)NQ * PLANE * sizeof(T);
-    static constexpr int fit = (int)((110u * 1024u - 2 * PLANE * sizeof(T)) / slot_bytes);  // 2 blocks per SM
-    static constexpr int RING0 = want > 16 ? 16 : want;
-    static constexpr int RING1 = RING0 > fit ? fit : RING0;
-    static constexpr int RING = RING1 < 4 ? 4 : RING1;  // at least 2 planes in flight
-    static constexpr int PF = RING - 2;
-    static_assert(PF >= 2, "the pipeline waits for the plane after the current one");
-    static constexpr size_t smem = sizeof(T) * ((size_t)RING * NQ * PLANE + 2 * PLANE);
+    static constexpr int PW = (NPAIR + 7) / 8;              // combine pairs per warp, the same on both planes
+    static constexpr bool CP1 = 2 * NCH <= 256;             // one (chunk position, plane) per copying lane
+    static constexpr int CW = CP1 ? (2 * NCH + 7) / 8 : (NCH + 7) / 8;  // copy units per warp
+    static_assert(PW <= 32 && CW <= 32, "one unit per lane");
+    static constexpr int RING = step_ring_slots(NQ, (int)sizeof(T));
+    static constexpr int D = (RING - 5) / 2;  // pairs of planes in flight
+    static_assert(D >= 1, "the pipeline keeps at least one pair of planes in flight");
+    static constexpr size_t smem = (size_t)step_smem_bytes(NQ, (int)sizeof(T));
 };
-
-template <typename T>
-struct Pair;
-template <>
-struct Pair<float> {
-    using V = float2;
-};
-template <>
-struct Pair<double> {
-    using V = double2;
-};
-
-__device__ __forceinline__ void cp_async16(unsigned smem_dst, const void* gsrc, int src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_dst), "l"(gsrc), "r"(src_bytes)
-                 : "memory");
-}
-
-// Shared-memory accesses by 32-bit shared-window address (ld/st.shared), one or two elements.
-template <typename T>
-__device__ __forceinline__ T lds1(unsigned a) {
-    T v;
-    if constexpr (sizeof(T) == 4)
-        asm volatile("ld.shared.f32 %0, [%1];\n" : "=f"(v) : "r"(a) : "memory");
-    else
-        asm volatile("ld.shared.f64 %0, [%1];\n" : "=d"(v) : "r"(a) : "memory");
-    return v;
-}
-template <typename T>
-__device__ __forceinline__ void lds2(unsigned a, T& x, T& y) {
-    if constexpr (sizeof(T) == 4)
-        asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];\n" : "=f"(x), "=f"(y) : "r"(a) : "memory");
-    else
-        asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];\n" : "=d"(x), "=d"(y) : "r"(a) : "memory");
-}
-template <typename T>
-__device__ __forceinline__ void sts2(unsigned a, T x, T y) {
-    if constexpr (sizeof(T) == 4)
-        asm volatile("st.shared.v2.f32 [%0], {%1, %2};\n" ::"r"(a), "f"(x), "f"(y) : "memory");
-    else
-        asm volatile("st.shared.v2.f64 [%0], {%1, %2};\n" ::"r"(a), "d"(x), "d"(y) : "memory");
-}
 
 // a0 * x - sum_q b_q y_q on a pair (packed two-lane FMAs in FP32)
 template <typename T>
@@ -161,19 +140,20 @@ __global__ void __launch_bounds__(256, 2) km_sm_step(Geom g, const T* __restrict
     pdl_enter();
     using R = StepRing<T, NQ>;
     constexpr bool FIRST = NQ == 1;  // step 0: the stencil of u_0 itself
-    constexpr int VW = R::VW, ROW = R::ROW, PLANE = R::PLANE, ROWC = R::ROWC, PF = R::PF, RING = R::RING;
+    constexpr int VW = R::VW, ROW = R::ROW, PLANE = R::PLANE, ROWC = R::ROWC, D = R::D, RING = R::RING;
     constexpr int M = VW - 1;  // element offset within a chunk
     constexpr unsigned ES = sizeof(T);
     constexpr unsigned SLOTB = NQ * PLANE * ES, PLANEB = PLANE * ES, ROWB = ROW * ES;
     SmStateT<T>* st = smt<T>(st_);
     if (st->stop || (FIRST ? 0 : j - 1) >= st->kdim) return;
-    extern __shared__ __align__(16) unsigned char smem_bytes[];
-    // [RING][NQ][10][ROW] staged source planes, then [2][10][ROW] u_j of the current and next plane
-    const unsigned raw_s = (unsigned)__cvta_generic_to_shared(smem_bytes);
-    const unsigned stg_s = raw_s + RING * SLOTB;
+    // [RING][NQ][10][ROW] staged source planes; vector 0 of a slot (w_{j-1}) is overwritten by
+    // u_j once the plane is combined, and the stencil reads it there.  Loads and stores take
+    // byte offsets (raw_s = 0); cp.async takes shared-window addresses (cwin + offset).
+    constexpr unsigned raw_s = 0;
+    const unsigned cwin = (unsigned)__cvta_generic_to_shared(g_step_smem);
 
     // node indices fit in 32 bits (the launcher checks)
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // blockDim = (32, 8): lane tx of warp ty
     const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 8;
     const int i = i0 + tx, jj = j0 + ty;
     const int nt = g.net, nx1 = g.nx1, ny1 = g.ny1;
@@ -185,7 +165,6 @@ __global__ void __launch_bounds__(256, 2) km_sm_step(Geom g, const T* __restrict
     const int N = (int)g.nnodes;
     const bool in = i < nx1 && jj < ny1;
     const int p = in ? jj * nx1 + i : 0;
-    const int pstep = P & M;  // row offsets advance by P mod VW per plane
 
     // update coefficients (column j - 1)
     T cf[NQ > 1 ? NQ - 1 : 1];
@@ -197,25 +176,28 @@ __global__ void __launch_bounds__(256, 2) km_sm_step(Geom g, const T* __restrict
     }
     T* __restrict__ uj = U.p[FIRST ? 0 : j];
 
-    // copy role: chunk position cpos of halo row ccy (threads < NPAR * NCH), every NPAR-th vector
-    const bool cthr = tid < R::NPAR * R::NCH;
-    const int cpar = cthr ? tid / R::NCH : 0;
-    const int cpos = cthr ? tid - cpar * R::NCH : 0;
+    // copy role, CW lanes of every warp: one chunk position of one plane of a pair (or of both
+    // planes where the positions outnumber the lanes), every source vector
+    const int cu = ty * R::CW + tx;
+    const bool cthr = tx < R::CW && cu < (R::CP1 ? 2 * R::NCH : R::NCH);
+    const int chalf = (R::CP1 && cthr) ? cu / R::NCH : 0;
+    const int cpos = cthr ? cu - chalf * R::NCH : 0;
     const int ccy = cpos / ROWC, cch = cpos - (cpos / ROWC) * ROWC;
     const int cgy = j0 - 1 + ccy;
     const bool crow = cthr && cgy >= 0 && cgy < ny1;
     const int cbytes = crow ? 16 : 0;        // on planes 1 .. n_t - 1 every chunk lies inside the vector
     const int crowE = cgy * nx1 + (i0 - 1);  // element of cell x = i0 - 1 on plane 0 (may be < 0)
-    const unsigned cdst = raw_s + ES * (unsigned)(ccy * ROW + cch * VW);
-    // combine role: element pair at ue of halo row uy (threads < NPAIR)
-    const bool uthr = tid < R::NPAIR;
-    const int uy = uthr ? tid / (ROW / 2) : 0;
-    const int ue = uthr ? 2 * (tid - uy * (ROW / 2)) : 0;
+    const unsigned cdst = cwin + ES * (unsigned)(ccy * ROW + cch * VW);
+    // combine role, PW lanes of every warp: the element pair at ue of halo row uy, on each
+    // plane the block combines
+    const int upi = ty * R::PW + tx;
+    const bool uthr = !FIRST && tx < R::PW && upi < R::NPAIR;
+    const int uy = uthr ? upi / (ROW / 2) : 0;
+    const int ue = uthr ? 2 * (upi - uy * (ROW / 2)) : 0;
     const int ugy = j0 - 1 + uy;
     const bool urow_own = uthr && uy >= 1 && uy <= 8 && ugy < ny1;
     const int urowE = ugy * nx1 + (i0 - 1);
     const unsigned usrc = raw_s + ES * (unsigned)(uy * ROW + ue);
-    const unsigned udst = stg_s + ES * (unsigned)(uy * ROW + ue);
     const int uroff = urowE & M;
     // for each row offset s: which of the pair's two cells lie in the tile interior (2 bits)
     unsigned uown = 0;
@@ -230,7 +212,7 @@ __global__ void __launch_bounds__(256, 2) km_sm_step(Geom g, const T* __restrict
     int roff[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) roff[d] = ((j0 - 1 + ty + d) * nx1 + (i0 - 1)) & M;
-    const unsigned gbase = stg_s + ES * (unsigned)(ty * ROW + tx);         // row ty, cell tx
+    const unsigned gbase = raw_s + ES * (unsigned)(ty * ROW + tx);            // row ty, cell tx
     const unsigned ebase = raw_s + ES * (unsigned)((ty + 1) * ROW + tx + 1);  // the node's cell
 
     Sten<T> S;
@@ -251,75 +233,73 @@ __global__ void __launch_bounds__(256, 2) km_sm_step(Geom g, const T* __restrict
     const bool dirp = in ? (dir[p] != 0) : true;
 
     auto wrap = [](int k) { return k >= RING ? k - RING : k; };
-    // plane m (first element qm = m P) of the source vectors into ring slot k; one commit
+    // planes m0 and m0 + 1 of the source vectors into ring slots k0 and k0 + 1; one commit
     // group per call
-    auto issue = [&](int m, int qm, int k) {
-        if (m <= me && cthr) {
-            const int E = qm + crowE;
-            const int A = (E & ~M) + cch * VW;  // chunk start (element)
-            int bytes = cbytes;
-            if (m == 0 || m == nt) {  // the chunk may begin before the vector or run past its end
-                bytes = 0;
-                if (crow && A >= 0 && A < N) bytes = A <= N - VW ? 16 : (N - A) * (int)ES;
-            }
-            const int Ac = bytes ? A : 0;  // a valid address when nothing is read
-            const unsigned d = cdst + (unsigned)k * SLOTB;
-            auto copy = [&](auto first) {
-                constexpr int v0 = decltype(first)::value;
+    auto issue = [&](int m0, int k0) {
+        if (cthr) {
 #pragma unroll
-                for (int v = v0; v < NQ; v += R::NPAR) {
-                    const T* src = v == 0 ? (FIRST ? U.p[0] : wprev) : U.p[v - 1];
-                    cp_async16(d + (unsigned)v * PLANEB, src + Ac, bytes);
+            for (int h = 0; h < (R::CP1 ? 1 : 2); ++h) {
+                const int hh = R::CP1 ? chalf : h;
+                const int mm = m0 + hh;
+                if (mm <= me) {
+                    const int E = mm * P + crowE;
+                    const int A = (E & ~M) + cch * VW;  // chunk start (element)
+                    int bytes = cbytes;
+                    if (mm == 0 || mm == nt) {  // the chunk may begin before the vector or run past its end
+                        bytes = 0;
+                        if (crow && A >= 0 && A < N) bytes = A <= N - VW ? 16 : (N - A) * (int)ES;
+                    }
+                    const int Ac = bytes ? A : 0;  // a valid address when nothing is read
+                    const unsigned d = cdst + (unsigned)(hh ? wrap(k0 + 1) : k0) * SLOTB;
+#pragma unroll
+                    for (int v = 0; v < NQ; ++v) {
+                        const T* src = v == 0 ? (FIRST ? U.p[0] : wprev) : U.p[v - 1];
+                        cp_async16(d + (unsigned)v * PLANEB, src + Ac, bytes);
+                    }
                 }
-            };
-            if (R::NPAR == 1 || cpar == 0)
-                copy(std::integral_constant<int, 0>{});
-            else
-                copy(std::integral_constant<int, 1>{});
+            }
         }
         cp_async_commit();
     };
     T nrm = T(0);
-    // u_j of plane m (first element qm, offset mp) from slot k into stg buffer b at this
-    // thread's pair; own: the plane is in this block's range (the pair's tile-interior cells
-    // are then written to global memory)
-    auto combine = [&](int qm, int mp, int k, int b, bool own) {
+    // u_j of plane mm (ring slot k) at this lane's pair, written over w_{j-1} in the slot; own:
+    // the plane is in this block's range (the pair's tile-interior cells then go to global
+    // memory and into ||u_j||^2)
+    auto combine = [&](int mm, int k, bool own) {
         if (!uthr) return;
         const unsigned sl = usrc + (unsigned)k * SLOTB;
         T x0, x1;
         lds2<T>(sl, x0, x1);
-        if constexpr (!FIRST) {
-            pair_scale(x0, x1, a);
+        pair_scale(x0, x1, a);
 #pragma unroll
-            for (int q = 0; q < NQ - 1; ++q) {
-                T y0, y1;
-                lds2<T>(sl + (unsigned)(1 + q) * PLANEB, y0, y1);
-                pair_fms(x0, x1, cf[q], y0, y1);
-            }
-            if (own && urow_own) {
-                const int s = (mp + uroff) & M;
-                const unsigned o = (uown >> (2 * s)) & 3u;
-                const bool o0 = o & 1u, o1 = o & 2u;
-                T* dst = uj + (qm + urowE - s + ue);  // the pair's first element
-                if (o == 3u) {
-                    if constexpr (sizeof(T) == 4)
-                        *reinterpret_cast<float2*>(dst) = make_float2(x0, x1);
-                    else
-                        *reinterpret_cast<double2*>(dst) = make_double2(x0, x1);
-                    nrm += x0 * x0 + x1 * x1;
-                } else {
-                    if (o0) {
-                        dst[0] = x0;
-                        nrm += x0 * x0;
-                    }
-                    if (o1) {
-                        dst[1] = x1;
-                        nrm += x1 * x1;
-                    }
+        for (int q = 0; q < NQ - 1; ++q) {
+            T y0, y1;
+            lds2<T>(sl + (unsigned)(1 + q) * PLANEB, y0, y1);
+            pair_fms(x0, x1, cf[q], y0, y1);
+        }
+        if (own && urow_own) {
+            const int qm = mm * P;
+            const int s = (qm + uroff) & M;
+            const unsigned o = (uown >> (2 * s)) & 3u;
+            T* dst = uj + (qm + urowE - s + ue);  // the pair's first element
+            if (o == 3u) {
+                if constexpr (sizeof(T) == 4)
+                    *reinterpret_cast<float2*>(dst) = make_float2(x0, x1);
+                else
+                    *reinterpret_cast<double2*>(dst) = make_double2(x0, x1);
+                nrm += x0 * x0 + x1 * x1;
+            } else {
+                if (o & 1u) {
+                    dst[0] = x0;
+                    nrm += x0 * x0;
+                }
+                if (o & 2u) {
+                    dst[1] = x1;
+                    nrm += x1 * x1;
                 }
             }
         }
-        sts2<T>(udst + (unsigned)b * PLANEB, x0, x1);
+        sts2<T>(sl, x0, x1);
     };
     T acc[NQ];
 #pragma unroll
@@ -335,107 +315,118 @@ __global__ void __launch_bounds__(256, 2) km_sm_step(Geom g, const T* __restrict
         }
         acc[NQ - 1] += wv * uc;
     };
-    // the 3 x 3 neighbourhood of the node on the staged u_j of a plane (buffer b, offset mp)
-    auto gather = [&](int b, int mp) {
-        const unsigned base = gbase + (unsigned)b * PLANEB;
+    // the 3 x 3 neighbourhood of the node on the u_j of a plane (slot k, offset mp)
+    auto gather = [&](int k, int mp) {
+        const unsigned base = gbase + (unsigned)k * SLOTB;
         S.gather(base + ES * (unsigned)((mp + roff[0]) & M), base + ROWB + ES * (unsigned)((mp + roff[1]) & M),
                  base + 2 * ROWB + ES * (unsigned)((mp + roff[2]) & M));
     };
-
-    // running plane state: m, its first element qm = m P, offset mp = qm mod VW, ring slot km
-    int m = ms, km = 0, qm = ms * P;
-    int mp = qm & M;
-    {
-        int q = qm, mm = ms;
-#pragma unroll
-        for (int d = 0; d < PF; ++d) {
-            issue(mm, q, d);
-            ++mm;
-            q += P;
-        }
-    }
-    cp_async_wait<PF - 1>();
-    __syncthreads();
-    combine(qm, mp, 0, ms & 1, ms >= n0 && ms < n1);
-    // lean planes: rows m - 1, m, m + 1 interior, row m - 1 in range, plane m + 1 staged and in
-    // this block's range, no last-row emission: no tests beyond the thread's own
-    const int ml = max(n0 + 1, 3), mh = min(min(me - 1, nt - 2), n1 - 2);
-    T A = 0, B = 0, Cc = 0, E0 = 0, E1 = 0, E2 = 0;
-    int mp_prev = (mp - pstep) & M;  // offset of plane m - 1
-    // plane m: wait for plane m + 1, refill, stage u_j of plane m + 1, stencil plane m, emit
-    auto step = [&](T& a_prev, T& a_cur, T& a_next, T& c_prev, T& c_cur) {
-        cp_async_wait<PF - 2>();
-        __syncthreads();
-        const int k1 = wrap(km + 1), kp = wrap(km + RING - 1);
-        const int mp1 = (mp + pstep) & M;
-        issue(m + PF, qm + PF * P, wrap(km + PF));
-        if (m >= ml && m <= mh) {
-            combine(qm + P, mp1, k1, (m + 1) & 1, true);
-            gather(m & 1, mp);
-            c_cur = S.centre();
+    // plane gp (slot kg; slot kq holds plane gp - 1) near a boundary of the block's range or of
+    // the time axis: its three row parts, the emission of row gp - 1 and, on the last plane, of
+    // row n_t, with every test of the general case
+    auto plane_general = [&](int gp, int kg, int kq, T& a_prev, T& a_cur, T& a_next, T c_prev, T& c_cur) {
+        const int qg = gp * P;
+        const int mpg = qg & M;
+        gather(kg, mpg);
+        c_cur = S.centre();
+        if (gp >= 3 && gp + 2 <= nt) {  // rows gp - 1, gp, gp + 1 interior: scaled interior stencil
             a_next = S.part(0);
             a_cur += S.part(1);
             a_prev += S.part(2);
-            if (in) emit(qm - P + p, a_prev, c_prev, kp, (mp_prev + roff[1]) & M);
         } else {
-            if (m + 1 <= me) combine(qm + P, mp1, k1, (m + 1) & 1, m + 1 >= n0 && m + 1 < n1);
-            gather(m & 1, mp);
-            c_cur = S.centre();
-            if (m >= 3 && m + 2 <= nt) {  // rows m - 1, m, m + 1 interior: scaled interior stencil
-                a_next = S.part(0);
-                a_cur += S.part(1);
-                a_prev += S.part(2);
-            } else {
-                T v[9];
-                const T* dm = dinv + qm;
+            T v[9];
+            const T* dm = dinv + qg;
 #pragma unroll
-                for (int dj = 0; dj < 3; ++dj)
+            for (int dj = 0; dj < 3; ++dj)
 #pragma unroll
-                    for (int di = 0; di < 3; ++di) {
-                        const int ii = i + di - 1, jn = jj + dj - 1;
-                        const bool ok = in && ii >= 0 && ii < nx1 && jn >= 0 && jn < ny1;
-                        v[dj * 3 + di] = ok ? S.vk(dj * 3 + di) * dm[jn * nx1 + ii] : T(0);
-                    }
-#pragma unroll
-                for (int part = 0; part < 3; ++part) {
-                    const int r = m + 1 - part;
-                    T sum = 0;
-                    if (r >= 1 && r <= nt) {
-                        const int cl = (r == 1) ? (nt == 1 ? 3 : 0) : (r == nt ? 2 : 1);
-                        const T* cc = coef + (long long)(cl * 27 + part * 9) * P + p;
-#pragma unroll
-                        for (int k = 0; k < 9; ++k) sum += cc[(long long)k * P] * v[k];
-                    }
-                    if (part == 0)
-                        a_next = sum;
-                    else if (part == 1)
-                        a_cur += sum;
-                    else
-                        a_prev += sum;
+                for (int di = 0; di < 3; ++di) {
+                    const int ii = i + di - 1, jn = jj + dj - 1;
+                    const bool ok = in && ii >= 0 && ii < nx1 && jn >= 0 && jn < ny1;
+                    v[dj * 3 + di] = ok ? S.vk(dj * 3 + di) * dm[jn * nx1 + ii] : T(0);
                 }
-            }
-            if (in && m - 1 >= n0 && m - 1 < n1) {
-                const int qn = qm - P + p;
-                emit(qn, (m - 1 == 0 || dirp) ? c_prev * dinv[qn] : a_prev, c_prev, kp, (mp_prev + roff[1]) & M);
-            }
-            if (in && m == nt && nt >= n0 && nt < n1) {
-                const int qn = qm + p;
-                emit(qn, dirp ? c_cur * dinv[qn] : a_cur, c_cur, km, (mp + roff[1]) & M);
+#pragma unroll
+            for (int part = 0; part < 3; ++part) {
+                const int r = gp + 1 - part;
+                T sum = 0;
+                if (r >= 1 && r <= nt) {
+                    const int cl = (r == 1) ? (nt == 1 ? 3 : 0) : (r == nt ? 2 : 1);
+                    const T* cc = coef + (long long)(cl * 27 + part * 9) * P + p;
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) sum += cc[(long long)k * P] * v[k];
+                }
+                if (part == 0)
+                    a_next = sum;
+                else if (part == 1)
+                    a_cur += sum;
+                else
+                    a_prev += sum;
             }
         }
-        // advance to plane m + 1
-        ++m;
-        qm += P;
-        km = k1;
-        mp_prev = mp;
-        mp = mp1;
+        if (in && gp - 1 >= n0 && gp - 1 < n1) {
+            const int qn = qg - P + p;
+            emit(qn, (gp - 1 == 0 || dirp) ? c_prev * dinv[qn] : a_prev, c_prev, kq, (((qg - P) & M) + roff[1]) & M);
+        }
+        if (in && gp == nt && nt >= n0 && nt < n1) {
+            const int qn = qg + p;
+            emit(qn, dirp ? c_cur * dinv[qn] : a_cur, c_cur, kg, (mpg + roff[1]) & M);
+        }
     };
+
+    // prologue: planes ms .. ms + 2 D + 1 in D + 1 groups, the first pair combined
+#pragma unroll
+    for (int d = 0; d <= D; ++d) issue(ms + 2 * d, 2 * d);
+    cp_async_wait<D>();
+    __syncthreads();
+    if constexpr (!FIRST) {
+        combine(ms, 0, ms >= n0 && ms < n1);
+        if (ms + 1 <= me) combine(ms + 1, 1, ms + 1 >= n0 && ms + 1 < n1);
+    }
+    // two planes m, m + 1 per iteration (one barrier): apply the stencil on planes m and m + 1,
+    // emit rows m - 1 and m, combine planes m + 2 and m + 3.  Carried: aL (row m - 1, lower
+    // and own parts), aM (row m, lower part), cL (u_j of row m - 1 at the node).  Lean
+    // iterations: rows m - 1 .. m + 2 interior, rows m - 1 and m in range, planes m + 2 and
+    // m + 3 staged and in range, no last-row emission: no tests beyond the thread's own.
+    const int ml = max(n0 + 1, 3), mh = min(n1 - 1, nt) - 3;
+    T aL = T(0), aM = T(0), cL = T(0);
+    int m = ms, km = 0;  // km: ring slot of plane m
     while (m <= me) {
-        step(A, B, Cc, E0, E1);
-        if (m > me) break;
-        step(B, Cc, A, E1, E2);
-        if (m > me) break;
-        step(Cc, A, B, E2, E0);
+        cp_async_wait<D - 1>();  // this thread's copies of planes m + 2, m + 3 have landed
+        __syncthreads();
+        const int k1 = wrap(km + 1), k2 = wrap(km + 2), k3 = wrap(km + 3), kp = wrap(km + RING - 1);
+        issue(m + 2 + 2 * D, wrap(km + 2 + 2 * D));  // into the slots of planes m - 3, m - 2
+        T aN = T(0), aN2 = T(0), cM = T(0), cN = T(0);
+        if (m >= ml && m <= mh) {
+            const int qm = m * P;
+            const int mp = qm & M, mp1 = (qm + P) & M, mpp = (qm - P) & M;
+            gather(km, mp);
+            cM = S.centre();
+            aN = S.part(0);
+            aM += S.part(1);
+            aL += S.part(2);
+            if (in) emit(qm - P + p, aL, cL, kp, (mpp + roff[1]) & M);
+            gather(k1, mp1);
+            cN = S.centre();
+            aN2 = S.part(0);
+            aN += S.part(1);
+            aM += S.part(2);
+            if (in) emit(qm + p, aM, cM, km, (mp + roff[1]) & M);
+            if constexpr (!FIRST) {  // after the loads of this iteration's other slots
+                combine(m + 2, k2, true);
+                combine(m + 3, k3, true);
+            }
+        } else {
+            plane_general(m, km, kp, aL, aM, aN, cL, cM);
+            if (m + 1 <= me) plane_general(m + 1, k1, km, aM, aN, aN2, cM, cN);
+            if constexpr (!FIRST) {
+                if (m + 2 <= me) combine(m + 2, k2, m + 2 >= n0 && m + 2 < n1);
+                if (m + 3 <= me) combine(m + 3, k3, m + 3 >= n0 && m + 3 < n1);
+            }
+        }
+        aL = aN;
+        aM = aN2;
+        cL = cN;
+        m += 2;
+        km = k2;
     }
     cp_async_wait<0>();
 
@@ -447,7 +438,7 @@ __global__ void __launch_bounds__(256, 2) km_sm_step(Geom g, const T* __restrict
     if constexpr (!FIRST) red[NQ] = nrm;
     __shared__ double out[NR];
     if (reduce_publish_t<T, NR>(red, NR, rb, out)) {
-        if (tid == 0) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
             if constexpr (FIRST) {
                 sm_apply_finish<T>(st_, out, 0);
             } else {
@@ -474,11 +465,15 @@ static void launch_sm_step_nq(const Geom& g, const T* sc, const T* coef, const u
 }
 
 // The vectors the step kernel stages or stores with 16-byte copies must start on 16-byte
-// boundaries and the level must have fewer than 2^31 nodes; the caller uses the separate
-// kernels otherwise.
+// boundaries, the level must have fewer than 2^31 nodes and at least 64 per plane, and the ring
+// of every step must fit in one block's shared memory; the caller uses the separate kernels
+// otherwise.
 template <typename T>
-bool sm_step_aligned(const Ptrs<T>& U, int steps, const T* w, const T* w2, long long nnodes) {
+bool sm_step_aligned(const Ptrs<T>& U, int steps, const T* w, const T* w2, long long nnodes, long long plane) {
     if (nnodes > (1LL << 31) - 64) return false;  // the kernel indexes nodes in 32 bits
+    if (plane < 64) return false;  // the chunks of a plane's last halo row end inside the next plane
+    for (int nq = 1; nq <= steps; ++nq)
+        if (step_smem_bytes(nq, (int)sizeof(T)) > kStepMaxSmem) return false;  // ring beyond one block's limit
     auto ok = [](const void* q) { return ((uintptr_t)q & 15u) == 0; };
     if (!ok(w) || !ok(w2)) return false;
     for (int q = 0; q <= steps; ++q)

@@ -4,5 +4,5 @@
 namespace st {
 template void launch_sm_step<double>(const Geom&, const double*, const double*, const unsigned char*, const double*,
                                    const Ptrs<double>&, const double*, double*, int, int, SmState*, RedBuf, cudaStream_t);
-template bool sm_step_aligned<double>(const Ptrs<double>&, int, const double*, const double*, long long);
+template bool sm_step_aligned<double>(const Ptrs<double>&, int, const double*, const double*, long long, long long);
 }  // namespace st

@@ -227,8 +227,22 @@ void launch_sm_step(const Geom& g, const T* sc, const T* coef, const unsigned ch
                     cudaStream_t s);
 // Whether the basis vectors and w buffers start on 16-byte boundaries (the step kernel needs it).
 template <typename T>
-bool sm_step_aligned(const Ptrs<T>& U, int steps, const T* w, const T* w2, long long nnodes);
+bool sm_step_aligned(const Ptrs<T>& U, int steps, const T* w, const T* w2, long long nnodes, long long plane);
 extern bool g_smstep;  // environment ST_SMSTEP=0: separate apply, dot and update kernels instead
+extern bool g_l0st;   // environment ST_L0ST=0: level-0 space-time rows by the node-parallel kernels instead
+// Level-0 rows of a space-time 2-D design in FP32 as time-marching kernels (k_l0st.cu): mode 0
+// w = A D^-1 u (smoother apply), 1 r = b - A x, 2 u_0 = b - A x with ||u_0||^2 (smoother
+// start), 3 y = A x.  Usable when the design is per space-time element, the level has fewer than 2^31
+// nodes and elements and at least 64 nodes per plane, and every vector (null entries skipped)
+// starts on a 16-byte boundary.
+bool l0st_usable(const OpL0<float>& op, const void* const* vecs, int nvec);
+void launch_l0st(int mode, bool tr, const OpL0<float>& op, const float* u, const float* dinv, const float* b,
+                 float* out, int j, int steps, SmState* st, RedBuf rb, cudaStream_t s);
+// The same rows for extruded 3-D designs (k_l0x3.cu), usable for those designs with at least 64
+// nodes per plane, fewer than 2^31 nodes and 16-byte aligned vectors.
+bool l0x3_usable(const OpL0<float>& op, const void* const* vecs, int nvec);
+void launch_l0x3(int mode, bool tr, const OpL0<float>& op, const float* u, const float* dinv, const float* b,
+                 float* out, int j, int steps, SmState* st, RedBuf rb, cudaStream_t s);
 // Fused FP32 Arnoldi step j -> j+1 on a stencil level (k_arnoldi.cu).
 void launch_arnoldi(const Geom& g, const float* coef, const unsigned char* dir, const float* dinv,
                     const Ptrs<float>& U, const float* w_in, float* w_out, int j, SmState* st, RedBuf rb,
