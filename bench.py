@@ -363,14 +363,15 @@ def step_bytes_per_node(steps: int, tsz: int) -> float:
 def kernel_roofline(N, n_st_elems, apply_ms, apply_n, args, steps=10):
     """Dominant kernel, its launches timed with CUDA events on the mesh stream inside the
     timed steps.  On stencil levels (time-constant 2-D designs) it is the fused Arnoldi step
-    km_sm_step (20 launches per V-cycle at level 0, bytes per step_bytes_per_node); on
-    element-block levels the smoother operator apply k_sm_applyw (u_j and D^-1 read, w written:
-    12 B per node in FP32, plus the BF16 density, 2 B per space-time element)."""
+    km_sm_step (20 launches per V-cycle at level 0, bytes per step_bytes_per_node); on the
+    finest level of space-time 2-D designs the marching element apply km_l0st and of extruded
+    3-D designs km_l0x3 (w = A D^-1 u: u_j and D^-1 read, w written, 12 B per node in FP32;
+    km_l0st also reads the BF16 density, 2 B per space-time element)."""
     peak, kind = _peaks()
     tsz = 4 if args.precision == "mixed" else 8
     if n_st_elems == 0:
         byts = step_bytes_per_node(steps, tsz) * N
-    elif n_st_elems < 0:  # extruded 3-D design: element-block path, the density is O(n_x n_y n_z)
+    elif n_st_elems < 0:  # extruded 3-D design: the density is O(n_x n_y n_z)
         byts = 3.0 * tsz * N
     else:
         byts = 3.0 * tsz * N + (2.0 * n_st_elems if args.precision == "mixed" else 8.0 * n_st_elems)
@@ -378,8 +379,11 @@ def kernel_roofline(N, n_st_elems, apply_ms, apply_n, args, steps=10):
         return {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None, "traffic": None}
     t = apply_ms / 1e3 / apply_n
     ach = byts / t / 1e9
-    name = "km_sm_step" if n_st_elems == 0 else "k_sm_applyw"
-    what = "fused Arnoldi step: update, stencil apply, dots" if n_st_elems == 0 else "smoother operator apply"
+    if n_st_elems == 0:
+        name, what = "km_sm_step", "fused Arnoldi step: update, stencil apply, dots"
+    else:
+        name = "km_l0st" if n_st_elems > 0 else "km_l0x3"
+        what = "marching smoother operator apply"
     return {"kernel": f"{name} level 0 ({'FP32' if tsz == 4 else 'FP64'} {what})",
             "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
             "traffic": TRAFFIC_PER_LAUNCH.get((name, args.workload, args.precision)),

@@ -524,6 +524,13 @@ void launch_apply_lc(int sd, const OpLc<T>& op, bool tr, const T* x, T* y, cudaS
         launch_pdl(km_apply<T>, grid, block, 0, s, op.g, op.st_coef[tr ? 1 : 0], op.st_dir, mg.chunk, x, y);
         return;
     }
+    if constexpr (std::is_same<T, float>::value) {
+        const void* vecs[2] = {x, y};
+        if (sd == 3 && g_l0st && lcx3_usable(op, vecs, 2)) {
+            launch_lcx3(3, tr, op, x, nullptr, nullptr, y, 0, 0, nullptr, RedBuf{}, s);
+            return;
+        }
+    }
     const LaunchCfg c = node_cfg(op.g);
     const OpL0<T> o0 = dummy_l0<T>(op.g);
     ST_SD_DISPATCH(sd, if (tr) launch_pdl(k_apply<SD, T, 1, true>, c.grid, c.block, 0, s, o0, op, x, y);
@@ -575,6 +582,10 @@ void launch_residual(int sd, int lvl, const OpL0<T>& o0, const OpLc<T>& oc, bool
                 launch_l0x3(1, tr, o0, x, nullptr, b, r, 0, 0, nullptr, RedBuf{}, s);
             return;
         }
+        if (lvl > 0 && sd == 3 && g_l0st && lcx3_usable(oc, vecs, 3)) {
+            launch_lcx3(1, tr, oc, x, nullptr, b, r, 0, 0, nullptr, RedBuf{}, s);
+            return;
+        }
     }
     const LaunchCfg c = node_cfg(lvl == 0 ? o0.g : oc.g);
     if (lvl == 0) {
@@ -611,14 +622,17 @@ static void record_timing_event(cudaEvent_t e, cudaStream_t s) {
 // The level-0 space-time kernels (k_l0st.cu) where the instantiation can use them (FP32,
 // 2-D, level 0) and on is set; false when the caller must launch the node-parallel kernel.
 template <int SD, typename T, int LV>
-static bool launch_l0st_if(bool on, int mode, bool tr, const OpL0<T>& o0, const T* u, const T* dinv, const T* b,
-                           T* out, int j, int steps, SmState* st, RedBuf rb, cudaStream_t s) {
-    if constexpr (LV == 0 && std::is_same<T, float>::value) {
+static bool launch_l0st_if(bool on, int mode, bool tr, const OpL0<T>& o0, const OpLc<T>& oc, const T* u,
+                           const T* dinv, const T* b, T* out, int j, int steps, SmState* st, RedBuf rb,
+                           cudaStream_t s) {
+    if constexpr (std::is_same<T, float>::value) {
         if (on) {
-            if constexpr (SD == 2)
+            if constexpr (LV == 0 && SD == 2)
                 launch_l0st(mode, tr, o0, u, dinv, b, out, j, steps, st, rb, s);
-            else
+            else if constexpr (LV == 0)
                 launch_l0x3(mode, tr, o0, u, dinv, b, out, j, steps, st, rb, s);
+            else
+                launch_lcx3(mode, tr, oc, u, dinv, b, out, j, steps, st, rb, s);
             return true;
         }
     }
@@ -647,13 +661,16 @@ static void smooth_impl(const OpL0<T>& o0, const OpLc<T>& oc, const T* b, T* x, 
     if (zero_init) U.u[0] = const_cast<T*>(b);
     Ptrs<T> P{};
     for (int q = 0; q <= steps; ++q) P.p[q] = U.u[q];
-    // level 0 of a space-time 2-D or an extruded 3-D design in FP32: the time-marching kernels
-    // of k_l0st.cu and k_l0x3.cu
+    // FP32 levels of a space-time 2-D design (level 0) or an extruded 3-D design (every level
+    // with extracted stencils): the time-marching kernels of k_l0st.cu and k_l0x3.cu
     bool l0st = false;
-    if constexpr (LV == 0 && std::is_same<T, float>::value) {
+    if constexpr (std::is_same<T, float>::value) {
         const void* vecs[4 + kMaxSmooth + 1] = {b, x, dinv, w};
         for (int q = 0; q <= steps; ++q) vecs[4 + q] = U.u[q];
-        l0st = !march && l0_march_usable(SD, o0, vecs, 4 + steps + 1);
+        if constexpr (LV == 0)
+            l0st = !march && l0_march_usable(SD, o0, vecs, 4 + steps + 1);
+        else
+            l0st = SD == 3 && g_l0st && lcx3_usable(oc, vecs, 4 + steps + 1);
     }
     // The fused Arnoldi step (one pass per step, halo recomputed) only pays on tiny, latency
     // bound levels; on large levels the split apply / dots / update kernels stream faster.
@@ -666,7 +683,7 @@ static void smooth_impl(const OpL0<T>& o0, const OpLc<T>& oc, const T* b, T* x, 
         note_launch(s);
         if (march)
             launch_pdl(km_sm_start<T>, mgrid, mblock, 0, s, g, coef, dir, mg.chunk, b, x, U.u[0], steps, st, rb);
-        else if (!launch_l0st_if<SD, T, LV>(l0st, 2, TR, o0, x, nullptr, b, U.u[0], 0, steps, st, rb, s))
+        else if (!launch_l0st_if<SD, T, LV>(l0st, 2, TR, o0, oc, x, nullptr, b, U.u[0], 0, steps, st, rb, s))
             launch_pdl(k_sm_start<SD, T, LV, TR, false>, c.grid, c.block, 0, s, o0, oc, b, x, U.u[0], steps, st, rb);
     }
     if (fused) {
@@ -716,7 +733,7 @@ static void smooth_impl(const OpL0<T>& o0, const OpLc<T>& oc, const T* b, T* x, 
                        dinv, U.u[j], w, j, st);
         else if (march)
             launch_pdl(km_sm_applyw<T>, mgrid, mblock, 0, s, g, coef, dir, mg.chunk, dinv, U.u[j], w, j, st);
-        else if (!launch_l0st_if<SD, T, LV>(l0st, 0, TR, o0, U.u[j], dinv, nullptr, w, j, steps, st, rb, s))
+        else if (!launch_l0st_if<SD, T, LV>(l0st, 0, TR, o0, oc, U.u[j], dinv, nullptr, w, j, steps, st, rb, s))
             launch_pdl(k_sm_applyw<SD, T, LV, TR>, c.grid, c.block, 0, s, o0, oc, dinv, U.u[j], w, j, st);
         if (ev) record_timing_event(ev[2 * j + 1], s);
         launch_dots<T>(N, w, P, j + 1, j, 0, st, rb, s);

@@ -298,6 +298,10 @@ OpLc<float> Mesh::opc<float>(int l) const {
         o.st_coef[1] = lv[l].st32 + 4LL * 27 * lv[l].g.plane;
         o.st_dir = lv[l].sdir;
     }
+    if (l > 0 && lv[l].x3st) {
+        o.x3st = lv[l].x3st;
+        for (int q = 0; q < 8; ++q) o.x3tw[q] = lv[l].x3tw[q];
+    }
     return o;
 }
 
@@ -468,6 +472,8 @@ st_status Mesh::ensure_level_storage() {
         release(lv[l].st64);
         release(lv[l].st32);
         release(lv[l].sdir);
+        release(lv[l].x3st);
+        lv[l].x3st = nullptr;
         lv[l].e64 = nullptr;
         lv[l].e32 = nullptr;
         lv[l].st64 = nullptr;
@@ -488,9 +494,41 @@ st_status Mesh::ensure_level_storage() {
             CKS(alloc((void**)&lv[l].sdir, P));
         }
     }
+    if (tc && sd == 3) {
+        for (size_t l = 1; l < lv.size(); ++l)
+            if (lv[l].g.net >= 2) CKS(alloc((void**)&lv[l].x3st, 54LL * lv[l].g.plane * sizeof(float)));
+    }
     storage_tc = tc;
     ws_version++;
     return ST_OK;
+}
+
+// 2 x 2 time element matrices of level l ([a_t][b_t], row-major): level 0's upwind
+// D_t = [[0, 0], [-1, 1]] and M_t = dt/6 [[2, 1], [1, 2]], then, for every coarsening that halves
+// time, the Galerkin product over the two fine slabs of a coarse slab with the nested linear
+// interpolation (fine nodes: c0, (c0 + c1) / 2, c1).
+static void level_time_mats(const Mesh* m, int l, double Dt[4], double Mt[4]) {
+    const double dt = m->lv[0].g.dt;
+    double D[4] = {0.0, 0.0, -1.0, 1.0}, Mm[4] = {dt / 3.0, dt / 6.0, dt / 6.0, dt / 3.0};
+    auto coarsen = [](double* T) {
+        const double P1[2][2] = {{1.0, 0.0}, {0.5, 0.5}}, P2[2][2] = {{0.5, 0.5}, {0.0, 1.0}};
+        double C[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b)
+                for (int i = 0; i < 2; ++i)
+                    for (int j = 0; j < 2; ++j)
+                        C[a * 2 + b] += P1[i][a] * T[i * 2 + j] * P1[j][b] + P2[i][a] * T[i * 2 + j] * P2[j][b];
+        for (int q = 0; q < 4; ++q) T[q] = C[q];
+    };
+    for (int q = 0; q < l; ++q)
+        if (m->lv[q].to_next == 1 || m->lv[q].to_next == 2) {
+            coarsen(D);
+            coarsen(Mm);
+        }
+    for (int q = 0; q < 4; ++q) {
+        Dt[q] = D[q];
+        Mt[q] = Mm[q];
+    }
 }
 
 st_status set_design(Mesh* m, const double* gamma, int layout, size_t count, int mem) {
@@ -533,6 +571,17 @@ st_status set_design(Mesh* m, const double* gamma, int layout, size_t count, int
         else
             launch_build_from_lc(m->sd, m->opc<double>(l - 1), m->lv[l].g, kind, m->lv[l].e64, s);
         launch_to_float(m->lv[l].e64, m->lv[l].e32, m->lv[l].nstore * nvals(m->sd), s);
+    }
+    // the two stencils of every coarse level of extruded 3-D designs (FP32 marching kernels)
+    for (int l = 1; l < L; ++l) {
+        if (!m->lv[l].x3st) continue;
+        double Dt[4], Mt[4];
+        level_time_mats(m, l, Dt, Mt);
+        launch_x3_stencil(m->opc<double>(l), Dt, Mt, m->lv[l].x3st, s);
+        for (int q = 0; q < 4; ++q) {
+            m->lv[l].x3tw[q] = (float)Dt[q];
+            m->lv[l].x3tw[4 + q] = (float)Mt[q];
+        }
     }
     // 27-point stencils of every level (extruded designs, 2 spatial dimensions)
     if (m->lv[0].sdir) {

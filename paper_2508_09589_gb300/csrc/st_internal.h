@@ -104,6 +104,8 @@ struct OpLc {
     int tc;
     const T* st_coef[2];           // as in OpL0
     const unsigned char* st_dir;
+    const float* x3st;             // extruded 3-D designs, FP32 path: stencils MC, KD [54][P], or null
+    float x3tw[8];                 // the level's time matrices D_t, M_t ([a_t][b_t]) for x3st
 };
 
 // Per-call smoother state (device), in the arithmetic type T of its multigrid (float for
@@ -243,6 +245,13 @@ void launch_l0st(int mode, bool tr, const OpL0<float>& op, const float* u, const
 bool l0x3_usable(const OpL0<float>& op, const void* const* vecs, int nvec);
 void launch_l0x3(int mode, bool tr, const OpL0<float>& op, const float* u, const float* dinv, const float* b,
                  float* out, int j, int steps, SmState* st, RedBuf rb, cudaStream_t s);
+// Coarse levels of extruded 3-D designs (k_l0x3.cu): the same marching rows from each node's
+// two extracted stencils (op.x3st) and the level's time matrices; k_x3_stencil extracts them
+// from the FP64 element blocks once per design.
+bool lcx3_usable(const OpLc<float>& op, const void* const* vecs, int nvec);
+void launch_lcx3(int mode, bool tr, const OpLc<float>& op, const float* u, const float* dinv, const float* b,
+                 float* out, int j, int steps, SmState* st, RedBuf rb, cudaStream_t s);
+void launch_x3_stencil(const OpLc<double>& op, const double Dt[4], const double Mt[4], float* out, cudaStream_t s);
 // Fused FP32 Arnoldi step j -> j+1 on a stencil level (k_arnoldi.cu).
 void launch_arnoldi(const Geom& g, const float* coef, const unsigned char* dir, const float* dinv,
                     const Ptrs<float>& U, const float* w_in, float* w_out, int j, SmState* st, RedBuf rb,

@@ -22,6 +22,8 @@ struct LevelH {
     double* st64 = nullptr;    // 27-point stencils [orientation][class][27][P] (extruded, 2-D)
     float* st32 = nullptr;
     unsigned char* sdir = nullptr;
+    float* x3st = nullptr;     // extruded 3-D designs, levels >= 1 with n_t >= 2: stencils MC, KD [54][P]
+    float x3tw[8] = {};        // and the level's time matrices D_t, M_t ([a_t][b_t])
 };
 
 template <typename T>

@@ -1,13 +1,14 @@
-"""The level-0 time-marching kernels of extruded 3-D designs in FP32 (k_l0x3.cu): operator
-apply, smoother apply and start, residual inside the mixed V-cycle, and mixed solves, against
-the oracle.  Cases: ragged 16 x 4 x 4 tiles on every axis, every boundary kind, few time
+"""The time-marching kernels of extruded 3-D designs in FP32 (k_l0x3.cu), on level 0 and on the
+coarse levels (stencils extracted from the Galerkin blocks): operator apply, smoother apply and
+start, residual inside the mixed V-cycle, and mixed solves, against the oracle.  Cases: ragged 16 x 4 x 4 tiles on every axis, every boundary kind, few time
 slabs, and thread-block budgets that cut the time axis into short chunks with a ragged last
 chunk."""
 import numpy as np
 import pytest
 
 from oracle import st_oracle as O
-from tests.gpu_common import U32, bf16_round, ensure_built, gpu_mesh, parity_rtol, rel_err, rowwise_excess
+from tests.gpu_common import (U32, bf16_round, ensure_built, galerkin_abs, gpu_mesh, parity_rtol, rel_err,
+                               rowwise_excess)
 
 pytestmark = pytest.mark.gpu
 
@@ -119,3 +120,35 @@ def test_mixed_vcycle_and_solves(i):
     assert rel_err(gm.state("lambda"), lam) < 1e-6
     st64 = gm.solve_forward(rtol=parity_rtol(sol.A, sol.s, sol.f), precision="fp64", max_it=400)
     assert st64["converged"] and rel_err(gm.state("T"), sol.s) < 1e-10
+
+
+@pytest.mark.parametrize("i", [1, 2, 3])
+def test_fp32_coarse_apply_rowwise(i):
+    """Every coarse level with at least two time slabs (space-, time- and mixed coarsening):
+    y = A_l x and A_l^T x in FP32, from the two stencils extracted from the FP64 Galerkin blocks,
+    within 280 u32 (B_l |x|)_i of the oracle's P^T A P row by row (B_l the Galerkin products of
+    |J|_elem), prescribed rows exact."""
+    om, g, gm = _case(i)
+    olev = O.hierarchy(om, coarse_cap=300)
+    assert [(tuple(L.ns), L.nt, L.to_next) for L in olev] == [(L["ns"], L["nt"], L["to_next"])
+                                                             for L in gm.levels()]
+    mg = O.build_mg(om, g, olev)
+    B = O.abs_operator(om, g)
+    rng = np.random.default_rng(21 + i)
+    checked = 0
+    for l in range(1, len(mg)):
+        B = galerkin_abs(B, mg[l - 1].Pt, mg[l].mask)
+        if olev[l].nt < 2:
+            continue
+        N = mg[l].A.shape[0]
+        x = rng.standard_normal(N)
+        x32 = x.astype(np.float32).astype(np.float64)
+        for tr in (False, True):
+            A = mg[l].A.T.tocsr() if tr else mg[l].A
+            y = torch.empty(N, dtype=torch.float32, device="cuda")
+            gm.apply(l, _dev(x, torch.float32), y, "mixed", tr)
+            yv = y.cpu().numpy().astype(np.float64)
+            assert rowwise_excess(yv, A @ x32, B.T.tocsr() if tr else B, x32, 280, U32) <= 1.0, (l, tr)
+            assert np.array_equal(yv[mg[l].mask], x32[mg[l].mask])
+        checked += 1
+    assert checked >= 1
