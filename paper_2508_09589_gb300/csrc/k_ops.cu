@@ -530,6 +530,10 @@ void launch_apply_lc(int sd, const OpLc<T>& op, bool tr, const T* x, T* y, cudaS
             launch_lcx3(3, tr, op, x, nullptr, nullptr, y, 0, 0, nullptr, RedBuf{}, s);
             return;
         }
+        if (sd == 2 && g_l0st && lcst_usable(op, vecs, 2)) {
+            launch_lcst(3, tr, op, x, nullptr, nullptr, y, 0, 0, nullptr, RedBuf{}, s);
+            return;
+        }
     }
     const LaunchCfg c = node_cfg(op.g);
     const OpL0<T> o0 = dummy_l0<T>(op.g);
@@ -586,6 +590,10 @@ void launch_residual(int sd, int lvl, const OpL0<T>& o0, const OpLc<T>& oc, bool
             launch_lcx3(1, tr, oc, x, nullptr, b, r, 0, 0, nullptr, RedBuf{}, s);
             return;
         }
+        if (lvl > 0 && sd == 2 && !oc.st_dir && g_l0st && lcst_usable(oc, vecs, 3)) {
+            launch_lcst(1, tr, oc, x, nullptr, b, r, 0, 0, nullptr, RedBuf{}, s);
+            return;
+        }
     }
     const LaunchCfg c = node_cfg(lvl == 0 ? o0.g : oc.g);
     if (lvl == 0) {
@@ -631,8 +639,10 @@ static bool launch_l0st_if(bool on, int mode, bool tr, const OpL0<T>& o0, const 
                 launch_l0st(mode, tr, o0, u, dinv, b, out, j, steps, st, rb, s);
             else if constexpr (LV == 0)
                 launch_l0x3(mode, tr, o0, u, dinv, b, out, j, steps, st, rb, s);
-            else
+            else if constexpr (SD == 3)
                 launch_lcx3(mode, tr, oc, u, dinv, b, out, j, steps, st, rb, s);
+            else
+                launch_lcst(mode, tr, oc, u, dinv, b, out, j, steps, st, rb, s);
             return true;
         }
     }
@@ -670,7 +680,8 @@ static void smooth_impl(const OpL0<T>& o0, const OpLc<T>& oc, const T* b, T* x, 
         if constexpr (LV == 0)
             l0st = !march && l0_march_usable(SD, o0, vecs, 4 + steps + 1);
         else
-            l0st = SD == 3 && g_l0st && lcx3_usable(oc, vecs, 4 + steps + 1);
+            l0st = g_l0st && !march &&
+                   (SD == 3 ? lcx3_usable(oc, vecs, 4 + steps + 1) : lcst_usable(oc, vecs, 4 + steps + 1));
     }
     // The fused Arnoldi step (one pass per step, halo recomputed) only pays on tiny, latency
     // bound levels; on large levels the split apply / dots / update kernels stream faster.

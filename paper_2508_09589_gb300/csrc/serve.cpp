@@ -316,6 +316,7 @@ long long st_footprint_bytes(const st_mesh_desc* d, int precision, int restart) 
     double dt = d->tau / d->n_t;
     const int tsz = precision == ST_PREC_FP64 ? 8 : 4;
     long long bytes = 0, N0 = 0, ne0 = 0, nc = 0;
+    bool space_only = true;  // every coarsening so far halved space only
     for (int l = 0; l < 40; ++l) {
         long long N = nt + 1, ne = nt;
         for (int q = 0; q < sd; ++q) {
@@ -327,6 +328,7 @@ long long st_footprint_bytes(const st_mesh_desc* d, int precision, int restart) 
             ne0 = ne;
         } else {
             bytes += ne * NV * 12;  // FP64 + FP32 element blocks
+            if (sd == 2 && space_only) bytes += ne * 128;  // M, K rows of the marching kernels
         }
         bytes += N * (long long)tsz * 16;  // b, x, r, dinv, w and 11 basis vectors
         nc = N;
@@ -345,6 +347,7 @@ long long st_footprint_bytes(const st_mesh_desc* d, int precision, int restart) 
             else if (kind == 0 && !can_s) kind = can_t ? 1 : -1;
         }
         if (kind < 0) break;
+        space_only = space_only && kind == 0;
         if (kind != 1)
             for (int q = 0; q < sd; ++q) {
                 n[q] /= 2;

@@ -302,6 +302,7 @@ OpLc<float> Mesh::opc<float>(int l) const {
         o.x3st = lv[l].x3st;
         for (int q = 0; q < 8; ++q) o.x3tw[q] = lv[l].x3tw[q];
     }
+    if (l > 0) o.x2blk = lv[l].x2blk;
     return o;
 }
 
@@ -474,6 +475,8 @@ st_status Mesh::ensure_level_storage() {
         release(lv[l].sdir);
         release(lv[l].x3st);
         lv[l].x3st = nullptr;
+        release(lv[l].x2blk);
+        lv[l].x2blk = nullptr;
         lv[l].e64 = nullptr;
         lv[l].e32 = nullptr;
         lv[l].st64 = nullptr;
@@ -497,6 +500,10 @@ st_status Mesh::ensure_level_storage() {
     if (tc && sd == 3) {
         for (size_t l = 1; l < lv.size(); ++l)
             if (lv[l].g.net >= 2) CKS(alloc((void**)&lv[l].x3st, 54LL * lv[l].g.plane * sizeof(float)));
+    }
+    if (!tc && sd == 2) {  // levels reached from level 0 by coarsening space only
+        for (size_t l = 1; l < lv.size() && lv[l - 1].to_next == 0; ++l)
+            CKS(alloc((void**)&lv[l].x2blk, 32LL * lv[l].g.net * lv[l].g.sp_elems * sizeof(float)));
     }
     storage_tc = tc;
     ws_version++;
@@ -583,6 +590,9 @@ st_status set_design(Mesh* m, const double* gamma, int layout, size_t count, int
             m->lv[l].x3tw[4 + q] = (float)Mt[q];
         }
     }
+    // M and K rows of the space-coarsened levels of space-time 2-D designs
+    for (int l = 1; l < L; ++l)
+        if (m->lv[l].x2blk) launch_x2_blocks(m->opc<double>(l), m->lv[l].x2blk, s);
     // 27-point stencils of every level (extruded designs, 2 spatial dimensions)
     if (m->lv[0].sdir) {
         for (int l = 0; l < L; ++l) {

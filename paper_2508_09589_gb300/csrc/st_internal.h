@@ -106,6 +106,7 @@ struct OpLc {
     const unsigned char* st_dir;
     const float* x3st;             // extruded 3-D designs, FP32 path: stencils MC, KD [54][P], or null
     float x3tw[8];                 // the level's time matrices D_t, M_t ([a_t][b_t]) for x3st
+    const float* x2blk;            // space-time 2-D designs, space-coarsened levels: M, K rows [slab][elem][32]
 };
 
 // Per-call smoother state (device), in the arithmetic type T of its multigrid (float for
@@ -252,6 +253,12 @@ bool lcx3_usable(const OpLc<float>& op, const void* const* vecs, int nvec);
 void launch_lcx3(int mode, bool tr, const OpLc<float>& op, const float* u, const float* dinv, const float* b,
                  float* out, int j, int steps, SmState* st, RedBuf rb, cudaStream_t s);
 void launch_x3_stencil(const OpLc<double>& op, const double Dt[4], const double Mt[4], float* out, cudaStream_t s);
+// Space-coarsened levels of space-time 2-D designs (k_lcst.cu): marching rows from each
+// (slab, element)'s M and K rows (op.x2blk), extracted once per design by k_x2_blocks.
+bool lcst_usable(const OpLc<float>& op, const void* const* vecs, int nvec);
+void launch_lcst(int mode, bool tr, const OpLc<float>& op, const float* u, const float* dinv, const float* b,
+                 float* out, int j, int steps, SmState* st, RedBuf rb, cudaStream_t s);
+void launch_x2_blocks(const OpLc<double>& op, float* out, cudaStream_t s);
 // Fused FP32 Arnoldi step j -> j+1 on a stencil level (k_arnoldi.cu).
 void launch_arnoldi(const Geom& g, const float* coef, const unsigned char* dir, const float* dinv,
                     const Ptrs<float>& U, const float* w_in, float* w_out, int j, SmState* st, RedBuf rb,

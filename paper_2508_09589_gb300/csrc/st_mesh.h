@@ -24,6 +24,7 @@ struct LevelH {
     unsigned char* sdir = nullptr;
     float* x3st = nullptr;     // extruded 3-D designs, levels >= 1 with n_t >= 2: stencils MC, KD [54][P]
     float x3tw[8] = {};        // and the level's time matrices D_t, M_t ([a_t][b_t])
+    float* x2blk = nullptr;    // space-time 2-D designs, levels reached by space coarsening only: M, K rows
 };
 
 template <typename T>

@@ -1,13 +1,14 @@
-"""The level-0 time-marching element kernels of space-time 2-D designs in FP32 (k_l0st.cu):
-operator apply, smoother apply and start, residual inside the mixed V-cycle, and mixed solves,
-against the oracle.  Cases: ragged 32 x 8 tiles in both axes, every boundary kind, one to few
+"""The time-marching element kernels of space-time 2-D designs in FP32: level 0 (k_l0st.cu) and
+the levels reached by coarsening space only (k_lcst.cu): operator apply, smoother apply and
+start, residual inside the mixed V-cycle, and mixed solves, against the oracle.  Cases: ragged 32 x 8 tiles in both axes, every boundary kind, one to few
 time slabs, and thread-block budgets that give each block the whole time axis or short time
 chunks with a ragged last chunk."""
 import numpy as np
 import pytest
 
 from oracle import st_oracle as O
-from tests.gpu_common import U32, bf16_round, ensure_built, gpu_mesh, parity_rtol, rel_err, rowwise_excess
+from tests.gpu_common import (U32, bf16_round, ensure_built, galerkin_abs, gpu_mesh, parity_rtol, rel_err,
+                               rowwise_excess)
 
 pytestmark = pytest.mark.gpu
 
@@ -120,3 +121,35 @@ def test_mixed_vcycle_and_solves(i):
     assert rel_err(gm.state("lambda"), lam) < 1e-6
     st64 = gm.solve_forward(rtol=parity_rtol(sol.A, sol.s, sol.f), precision="fp64", max_it=400)
     assert st64["converged"] and rel_err(gm.state("T"), sol.s) < 1e-10
+
+
+@pytest.mark.parametrize("i", [0, 1, 6])
+def test_fp32_coarse_apply_rowwise(i):
+    """Every level reached from level 0 by coarsening space only: y = A_l x and A_l^T x in FP32
+    from the (slab, element) M and K rows extracted from the FP64 Galerkin blocks, within
+    80 u32 (B_l |x|)_i of the oracle's P^T A P row by row (B_l the Galerkin products of
+    |J|_elem), prescribed rows exact."""
+    om, g, gm = _case(i)
+    olev = O.hierarchy(om, coarse_cap=300)
+    assert [(tuple(L.ns), L.nt, L.to_next) for L in olev] == [(L["ns"], L["nt"], L["to_next"])
+                                                             for L in gm.levels()]
+    mg = O.build_mg(om, g, olev)
+    B = O.abs_operator(om, g)
+    rng = np.random.default_rng(31 + i)
+    checked = 0
+    for l in range(1, len(mg)):
+        if olev[l - 1].to_next != "space":
+            break
+        B = galerkin_abs(B, mg[l - 1].Pt, mg[l].mask)
+        N = mg[l].A.shape[0]
+        x = rng.standard_normal(N)
+        x32 = x.astype(np.float32).astype(np.float64)
+        for tr in (False, True):
+            A = mg[l].A.T.tocsr() if tr else mg[l].A
+            y = torch.empty(N, dtype=torch.float32, device="cuda")
+            gm.apply(l, _dev(x, torch.float32), y, "mixed", tr)
+            yv = y.cpu().numpy().astype(np.float64)
+            assert rowwise_excess(yv, A @ x32, B.T.tocsr() if tr else B, x32, 80, U32) <= 1.0, (l, tr)
+            assert np.array_equal(yv[mg[l].mask], x32[mg[l].mask])
+        checked += 1
+    assert checked >= 1
