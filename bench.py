@@ -392,8 +392,11 @@ def kernel_roofline(N, n_st_elems, apply_ms, apply_n, args, steps=10):
 
 
 # DRAM read + write bytes of one launch, from an ncu capture of the current kernel version
-# (profiles/ names the capture); None when no capture of this version exists.
+# (profiles/ names the capture); None when no capture of this version exists.  km_sm_step on
+# c1: the mean over the ten level-0 launches j = 0..9 of one sweep (421.1 MB read + 105.4 MB
+# written), the same average over j as the achieved bandwidth.
 TRAFFIC_PER_LAUNCH = {
+    ("km_sm_step", "c1_256x256x256_grf_extruded", "mixed"): 526.5e6,
 }
 
 

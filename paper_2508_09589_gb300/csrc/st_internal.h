@@ -223,12 +223,14 @@ template <typename T>
 void launch_stencil_diag(const Geom& g, const T* coef, const unsigned char* dir, T* d, bool invert, cudaStream_t s);
 // One Arnoldi step j of the smoother on a stencil level as one kernel (k_smstep.cuh): the
 // update u_j = s_{j-1} w_{j-1} - sum H[q][j-1] s_q u_q (j >= 1), w_j = A D^-1 u_j with the
-// scaled interior stencil sc, and the dots (w_j, u_q), q <= j, with ||u_j||^2.
+// scaled interior stencil sc, and the dots (w_j, u_q), q <= j, with ||u_j||^2.  Instantiated for
+// float (the mixed V-cycle); the FP64 V-cycle uses the separate kernels.
 template <typename T>
 void launch_sm_step(const Geom& g, const T* sc, const T* coef, const unsigned char* dir, const T* dinv,
                     const Ptrs<T>& U, const T* wprev, T* wout, int j, int steps, SmState* st, RedBuf rb,
                     cudaStream_t s);
-// Whether the basis vectors and w buffers start on 16-byte boundaries (the step kernel needs it).
+// Whether the step kernel can run the sweep: 16-byte aligned vectors, fewer than 2^31 nodes, at
+// least 64 per plane, and every step's ring within one block's shared memory.
 template <typename T>
 bool sm_step_aligned(const Ptrs<T>& U, int steps, const T* w, const T* w2, long long nnodes, long long plane);
 extern bool g_smstep;  // environment ST_SMSTEP=0: separate apply, dot and update kernels instead
