@@ -500,6 +500,13 @@ void launch_apply_l0(int sd, const OpL0<T>& op, bool tr, const T* x, T* y, cudaS
         launch_pdl(km_apply<T>, grid, block, 0, s, op.g, op.st_coef[tr ? 1 : 0], op.st_dir, mg.chunk, x, y);
         return;
     }
+    if constexpr (std::is_same<T, double>::value) {
+        const void* vecs[2] = {x, y};
+        if (fg_march_usable(sd, op, vecs, 2)) {
+            launch_fg_march<double>(sd, 0, tr, op, x, nullptr, nullptr, y, nullptr, RedBuf{}, s);
+            return;
+        }
+    }
     if constexpr (std::is_same<T, float>::value) {
         const void* vecs[2] = {x, y};
         if (l0_march_usable(sd, op, vecs, 2)) {
@@ -788,9 +795,14 @@ void launch_fg_apply_dots(int sd, const OpL0<double>& op, bool tr, const TZ* z, 
         const MarchGrid mg = march_grid(op.g, grid, block);
         launch_pdl(km_fg_apply<TZ>, grid, block, 0, s, op.g, op.st_coef[tr ? 1 : 0], op.st_dir, mg.chunk, z, zstore, w);
     } else {
-        const LaunchCfg c = node_cfg(op.g);
-        ST_SD_DISPATCH(sd, if (tr) launch_pdl(k_fg_apply<SD, TZ, true>, c.grid, c.block, 0, s, op, z, zstore, w);
-                       else launch_pdl(k_fg_apply<SD, TZ, false>, c.grid, c.block, 0, s, op, z, zstore, w));
+        const void* vecs[3] = {z, zstore, w};
+        if (fg_march_usable(sd, op, vecs, 3)) {
+            launch_fg_march<TZ>(sd, 0, tr, op, z, zstore, nullptr, w, nullptr, RedBuf{}, s);
+        } else {
+            const LaunchCfg c = node_cfg(op.g);
+            ST_SD_DISPATCH(sd, if (tr) launch_pdl(k_fg_apply<SD, TZ, true>, c.grid, c.block, 0, s, op, z, zstore, w);
+                           else launch_pdl(k_fg_apply<SD, TZ, false>, c.grid, c.block, 0, s, op, z, zstore, w));
+        }
     }
     Ptrs<double> P{};
     for (int q = 0; q <= j; ++q) P.p[q] = V[q];
@@ -839,6 +851,13 @@ void launch_fg_residual(int sd, const OpL0<double>& op, bool tr, const double* f
         const MarchGrid mg = march_grid(op.g, grid, block);
         launch_pdl(km_fg_residual, grid, block, 0, s, op.g, op.st_coef[tr ? 1 : 0], op.st_dir, mg.chunk, f, x, r, fs, rb);
         return;
+    }
+    {
+        const void* vecs[3] = {f, x, r};
+        if (fg_march_usable(sd, op, vecs, 3)) {
+            launch_fg_march<double>(sd, 1, tr, op, x, nullptr, f, r, fs, rb, s);
+            return;
+        }
     }
     const LaunchCfg c = node_cfg(op.g);
     ST_SD_DISPATCH(sd, if (tr) launch_pdl(k_fg_residual<SD, true>, c.grid, c.block, 0, s, op, f, x, r, fs, rb);

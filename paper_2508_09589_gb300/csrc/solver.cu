@@ -554,8 +554,8 @@ st_status set_design(Mesh* m, const double* gamma, int layout, size_t count, int
         m->release(m->gsens);
         m->g64 = nullptr;
         m->g16 = nullptr;
-        CKS(m->alloc((void**)&m->g64, want * sizeof(double)));
-        // 8 values of padding: the level-0 marching kernels copy whole 16-byte chunks of it
+        // padding: the marching kernels copy whole 16-byte chunks of the designs
+        CKS(m->alloc((void**)&m->g64, (want + 8) * sizeof(double)));
         CKS(m->alloc((void**)&m->g16, (want + 8) * sizeof(__nv_bfloat16)));
         CKS(m->alloc((void**)&m->gin, want * sizeof(double)));
         CKS(m->alloc((void**)&m->gsens, want * sizeof(double)));

@@ -261,6 +261,14 @@ bool lcst_usable(const OpLc<float>& op, const void* const* vecs, int nvec);
 void launch_lcst(int mode, bool tr, const OpLc<float>& op, const float* u, const float* dinv, const float* b,
                  float* out, int j, int steps, SmState* st, RedBuf rb, cudaStream_t s);
 void launch_x2_blocks(const OpLc<double>& op, float* out, cudaStream_t s);
+// FP64 level-0 rows of the outer FGMRES for space-time 2-D and extruded 3-D designs as marching
+// kernels (k_fg_march.cu): mode 0 w = J z (z copied into zstore when given), mode 1
+// r = f - J x with ||r||^2 into the FGMRES state.  Usable for those designs with at least 64
+// nodes per plane, fewer than 2^31 nodes and 16-byte aligned vectors.
+bool fg_march_usable(int sd, const OpL0<double>& op, const void* const* vecs, int nvec);
+template <typename TZ>
+void launch_fg_march(int sd, int mode, bool tr, const OpL0<double>& op, const TZ* z, TZ* zstore, const double* f,
+                     double* out, FgState* fs, RedBuf rb, cudaStream_t s);
 // Fused FP32 Arnoldi step j -> j+1 on a stencil level (k_arnoldi.cu).
 void launch_arnoldi(const Geom& g, const float* coef, const unsigned char* dir, const float* dinv,
                     const Ptrs<float>& U, const float* w_in, float* w_out, int j, SmState* st, RedBuf rb,

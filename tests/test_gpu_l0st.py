@@ -1,13 +1,14 @@
-"""The time-marching element kernels of space-time 2-D designs in FP32: level 0 (k_l0st.cu) and
-the levels reached by coarsening space only (k_lcst.cu): operator apply, smoother apply and
-start, residual inside the mixed V-cycle, and mixed solves, against the oracle.  Cases: ragged 32 x 8 tiles in both axes, every boundary kind, one to few
-time slabs, and thread-block budgets that give each block the whole time axis or short time
-chunks with a ragged last chunk."""
+"""The time-marching element kernels of space-time 2-D designs in FP32: level 0 (k_l0st.cu) and the
+levels reached by coarsening space only (k_lcst.cu): operator apply, smoother apply and start,
+residual inside the mixed V-cycle, and mixed solves, against the oracle; and the FP64 outer
+operator on its marching kernel (k_fg_march.cu). Cases: ragged 32 x 8 tiles in both axes, every
+boundary kind, one to few time slabs, and thread-block budgets that give each block the whole
+time axis or short time chunks with a ragged last chunk."""
 import numpy as np
 import pytest
 
 from oracle import st_oracle as O
-from tests.gpu_common import (U32, bf16_round, ensure_built, galerkin_abs, gpu_mesh, parity_rtol, rel_err,
+from tests.gpu_common import (U32, U64, bf16_round, ensure_built, galerkin_abs, gpu_mesh, parity_rtol, rel_err,
                                rowwise_excess)
 
 pytestmark = pytest.mark.gpu
@@ -153,3 +154,23 @@ def test_fp32_coarse_apply_rowwise(i):
             assert np.array_equal(yv[mg[l].mask], x32[mg[l].mask])
         checked += 1
     assert checked >= 1
+
+
+@pytest.mark.parametrize("i", range(len(CASES)))
+def test_fp64_apply_rowwise(i):
+    """The FP64 outer operator on the marching kernels (k_fg_march.cu, space-time 2-D): y = J x and
+    J^T x from the FP64 design within 80 u64 (|J|_elem |x|)_i of the oracle row by row and 1e-13
+    of the largest entry, prescribed rows exact."""
+    om, g, gm = _case(i)
+    A = O.assemble(om, g)
+    B = O.abs_operator(om, g)
+    x = np.random.default_rng(41 + i).standard_normal(om.n_nodes)
+    mask = O.dirichlet_mask(om)
+    for tr in (False, True):
+        At = A.T.tocsr() if tr else A
+        y = torch.empty(om.n_nodes, dtype=torch.float64, device="cuda")
+        gm.apply(0, _dev(x), y, "fp64", tr)
+        yv = y.cpu().numpy()
+        assert rel_err(yv, At @ x) < 1e-13, tr
+        assert rowwise_excess(yv, At @ x, B.T.tocsr() if tr else B, x, 80, U64) <= 1.0, tr
+        assert np.array_equal(yv[mask], x[mask])
