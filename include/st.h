@@ -341,7 +341,9 @@ long long st_footprint_bytes(const st_mesh_desc* d, int precision, int restart);
  * (one double, written when the stream reaches the kernel).  No mesh is needed and nothing
  * is allocated: the only scratch is a static 32 KiB device array that every GPU loading
  * the library keeps until exit.  The first call on a device looks up that array's address
- * (cudaGetSymbolAddress), so make it before any stream capture.  Limits: the x-y plane may
+ * (cudaGetSymbolAddress), so make it before any stream capture; after it, a call can be
+ * captured into a CUDA graph and replayed.  The address is kept per device for the process,
+ * so a cudaDeviceReset of that device is not supported afterwards.  Limits: the x-y plane may
  * hold at most 4096 tiles of 32 x 8 nodes (e.g. 1024 x 1024 spatial elements) and the
  * mesh at most 2^31 - 1 nodes; larger sizes return ST_ERR_ARG.  All calls share the one
  * array (it keeps the last call's partial sums; the completion counter is cleared at the

@@ -5,7 +5,8 @@ stream capture or fixed memory pool, or a real-time loop).  For them the library
 r = f - J x and ||r||_2 with all scratch in a static device array.  This test calls it
 twice in a row through the C ABI and checks both results against the FP64 oracle's assembled
 operator (r = f - A x) and against the regular fine-level operator entry point (st_op_apply),
-within the FP64 operator tolerance of the other tests, for both sink-patch placements.
+within the FP64 operator tolerance of the other tests, for both sink-patch placements; and
+replays it from a CUDA graph captured on a side stream.
 This file sorts last so that a run stopping at the first failure has run everything else.
 """
 import ctypes as C
@@ -55,6 +56,48 @@ def test_residual_norm_noalloc_matches_oracle_and_operator_apply(ns, nt, layout,
         assert rel_err(r.cpu().numpy(), r_ref) < 1e-12
         assert rel_err(r.cpu().numpy(), r_op) < 1e-12
         assert abs(norm.item() - n_ref) <= 1e-12 * n_ref
+
+
+def test_residual_norm_noalloc_captured_in_a_graph():
+    """After one eager call on a side stream, the call is captured into a CUDA graph on that
+    stream and replayed twice: every replay gives the eager r and norm bit for bit, and both
+    match the oracle."""
+    L = ensure_built()
+    om = O.Mesh((40, 24), 20, mat=O.Material(), bc="patch_left", bc_width=0.3)
+    rng = np.random.default_rng(7)
+    g = rng.random(om.elem_shape)
+    gm = gpu_mesh(om, coarse_dof_cap=300)
+    x = torch.tensor(rng.standard_normal(om.n_nodes), dtype=torch.float64, device="cuda")
+    f = torch.tensor(rng.standard_normal(om.n_nodes), dtype=torch.float64, device="cuda")
+    gd = torch.tensor(np.ascontiguousarray(g).reshape(-1), dtype=torch.float64, device="cuda")
+    r = torch.empty_like(x)
+    norm = torch.empty(1, dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+
+    def call():
+        return L.st_residual_norm_noalloc(C.byref(gm.desc), C.c_void_p(gd.data_ptr()), LAYOUT["spacetime"],
+                                          C.c_void_p(x.data_ptr()), C.c_void_p(f.data_ptr()),
+                                          C.c_void_p(r.data_ptr()), C.c_void_p(norm.data_ptr()),
+                                          C.c_void_p(s.cuda_stream))
+
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        assert call() == 0, L.st_last_error()
+    torch.cuda.synchronize()
+    r0, n0 = r.clone(), norm.clone()
+    r_ref = f.cpu().numpy() - O.assemble(om, g) @ x.cpu().numpy()
+    assert rel_err(r0.cpu().numpy(), r_ref) < 1e-12
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        code = call()
+    assert code == 0, L.st_last_error()
+    for _ in range(2):
+        r.fill_(float("nan"))
+        norm.fill_(float("nan"))
+        torch.cuda.synchronize()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(r, r0) and torch.equal(norm, n0)
 
 
 def test_residual_norm_noalloc_rejects_planes_beyond_its_scratch():
