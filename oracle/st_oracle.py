@@ -284,14 +284,27 @@ def assemble(m: Mesh, gamma: np.ndarray, ngauss: int = 3) -> sp.csr_matrix:
 
 # ----------------------------------------------------------------------------
 # Source vector f_i = int N_i Q dV (Sec. 3.1.2), zero at prescribed nodes.
-# Reading: the time integral uses 2-point Gauss per element; for sources that
-# are uniform in space the spatial integral is then exact.
+# Reading: the integral uses 2-point Gauss per axis and element; for sources that
+# are uniform in space the spatial integral is then exact (the moving Gaussian of
+# Example 2 is integrated by the same rule).
 # ----------------------------------------------------------------------------
-def source_fn(kind: str, q0: float = 1.0, a: float = 1.0, b: float = 0.5, f: float = 4.0):
+def source_fn(kind: str, q0: float = 1.0, a: float = 1.0, b: float = 0.5, f: float = 4.0,
+              center: Tuple[float, float] = (0.5, 0.5)):
     if kind == "uniform":
         return lambda t, *x: q0 * np.ones_like(t)
     if kind == "sin_t":
         return lambda t, *x: q0 * (a + b * np.sin(2.0 * math.pi * f * t))
+    if kind == "gaussian":
+        # Example 2 (Sec. 2.3.2), two space dimensions: a Gaussian of peak q0 and width
+        # sigma = a whose centre moves on a circle of radius R = b about `center` (the middle of
+        # the domain) with angular frequency omega = f, starting at angle pi/2 (the top).
+        cx, cy = center
+
+        def gauss(t, y, x):
+            x1 = cx + b * np.cos(f * t + math.pi / 2.0)
+            x2 = cy + b * np.sin(f * t + math.pi / 2.0)
+            return q0 * np.exp(-((x - x1) ** 2 + (y - x2) ** 2) / (2.0 * a * a))
+        return gauss
     raise ValueError(kind)
 
 
@@ -831,3 +844,89 @@ def chain_rule(m: Mesh, dphi_dphys: np.ndarray, gamma_tilde: np.ndarray, r_x: fl
     """d phi / d gamma = F^T (H'(gamma~) * d phi / d gamma_bar).  F = E A^-1 T with T = v_e E^T and
     A symmetric, so F^T = F: the sensitivities pass through the same filter (Sec. 3.3.2)."""
     return pde_filter(m, heaviside_derivative(gamma_tilde, beta, eta) * dphi_dphys, r_x, r_t)
+
+
+# ----------------------------------------------------------------------------
+# Method of Moving Asymptotes (Svanberg 1987) for one constraint g1(x) <= 0, the
+# optimiser named in Sec. 3.3.3 (volume constraint of Sec. 3.3.1).  Readings (the
+# paper cites a modified form of Guest et al.'s initial asymptotes without values):
+# - asymptotes: the first two iterations at x -/+ MMA_S0 (x_max - x_min); later
+#   ones move by MMA_INCR where the last two steps kept their sign and MMA_DECR
+#   where it flipped, kept within 0.01 .. 10 (x_max - x_min) of x;
+# - bounds of the subproblem: alpha = max(x_min, L + 0.1 (x - L), x - MMA_MOVE span),
+#   beta = min(x_max, U - 0.1 (U - x), x + MMA_MOVE span);
+# - the convex approximations of Svanberg's later formulation:
+#   p = (U - x)^2 (1.001 df+ + 0.001 df- + MMA_RAA / span),
+#   q = (x - L)^2 (0.001 df+ + 1.001 df- + MMA_RAA / span);
+# - the subproblem solved through its dual: for a multiplier lam >= 0 each x_j
+#   minimises P_j / (U_j - x) + Q_j / (x - L_j) with P = p0 + lam p1, Q = q0 + lam q1,
+#   x_j = (sqrt(P) L + sqrt(Q) U) / (sqrt(P) + sqrt(Q)) clipped to [alpha, beta];
+#   lam = 0 when the approximated constraint holds there, else the root of the
+#   approximated constraint (decreasing in lam), by bisection; when it cannot be met
+#   inside [alpha, beta] (the paper's volume constraint only from an infeasible start),
+#   lam stops at MMA_LAM_MAX, the most feasible point of the subproblem.
+# ----------------------------------------------------------------------------
+MMA_S0, MMA_INCR, MMA_DECR, MMA_MOVE, MMA_RAA, MMA_LAM_MAX = 0.05, 1.2, 0.7, 0.2, 1e-5, 1e40
+
+
+def mma_asymptotes(it: int, x, xold1, xold2, low, upp, xmin: float = 0.0, xmax: float = 1.0):
+    """Asymptotes L, U of iteration it (1-based) of the readings above."""
+    span = xmax - xmin
+    if it <= 2:
+        return x - MMA_S0 * span, x + MMA_S0 * span
+    sgn = (x - xold1) * (xold1 - xold2)
+    fac = np.where(sgn > 0, MMA_INCR, np.where(sgn < 0, MMA_DECR, 1.0))
+    low = np.clip(x - fac * (xold1 - low), x - 10.0 * span, x - 0.01 * span)
+    upp = np.clip(x + fac * (upp - xold1), x + 0.01 * span, x + 10.0 * span)
+    return low, upp
+
+
+def mma_subproblem(x, low, upp, df0, g1: float, dg1, xmin: float = 0.0, xmax: float = 1.0):
+    """The convex separable subproblem at x: bounds alpha, beta and the terms p0, q0, p1, q1, r1
+    of f0 ~ sum p0 / (U - x) + q0 / (x - L) and g1 ~ sum p1 / (U - x) + q1 / (x - L) + r1."""
+    span = xmax - xmin
+    alpha = np.maximum(np.maximum(xmin, low + 0.1 * (x - low)), x - MMA_MOVE * span)
+    beta = np.minimum(np.minimum(xmax, upp - 0.1 * (upp - x)), x + MMA_MOVE * span)
+    ux2, xl2 = (upp - x) ** 2, (x - low) ** 2
+    reg = MMA_RAA / span
+
+    def pq(d):
+        dp, dm = np.maximum(d, 0.0), np.maximum(-d, 0.0)
+        return ux2 * (1.001 * dp + 0.001 * dm + reg), xl2 * (0.001 * dp + 1.001 * dm + reg)
+    p0, q0 = pq(np.asarray(df0, dtype=np.float64))
+    p1, q1 = pq(np.asarray(dg1, dtype=np.float64))
+    r1 = g1 - np.sum(p1 / (upp - x) + q1 / (x - low))
+    return alpha, beta, p0, q0, p1, q1, r1
+
+
+def mma_x_of(lam: float, low, upp, alpha, beta, p0, q0, p1, q1):
+    """The subproblem's minimiser for multiplier lam (closed form, clipped)."""
+    sp_, sq_ = np.sqrt(p0 + lam * p1), np.sqrt(q0 + lam * q1)
+    return np.clip((sp_ * low + sq_ * upp) / (sp_ + sq_), alpha, beta)
+
+
+def mma_update(it: int, x, xold1, xold2, low, upp, df0, g1: float, dg1, xmin: float = 0.0,
+               xmax: float = 1.0, rel_tol: float = 1e-15):
+    """One MMA iteration: returns (x_new, L, U, lam)."""
+    x = np.asarray(x, dtype=np.float64)
+    low, upp = mma_asymptotes(it, x, xold1, xold2, low, upp, xmin, xmax)
+    alpha, beta, p0, q0, p1, q1, r1 = mma_subproblem(x, low, upp, df0, g1, dg1, xmin, xmax)
+
+    def g_of(lam):
+        xs = mma_x_of(lam, low, upp, alpha, beta, p0, q0, p1, q1)
+        return np.sum(p1 / (upp - xs) + q1 / (xs - low)) + r1
+    lam = 0.0
+    if g_of(0.0) > 0.0:
+        lo, hi = 0.0, 1.0
+        while g_of(hi) > 0.0 and hi < MMA_LAM_MAX:
+            lo, hi = hi, 2.0 * hi
+        while hi - lo > rel_tol * hi:
+            mid = 0.5 * (lo + hi)
+            if mid <= lo or mid >= hi:
+                break
+            if g_of(mid) > 0.0:
+                lo = mid
+            else:
+                hi = mid
+        lam = hi
+    return mma_x_of(lam, low, upp, alpha, beta, p0, q0, p1, q1), low, upp, lam

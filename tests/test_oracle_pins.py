@@ -826,3 +826,132 @@ def test_filtered_projected_compliance_gradient_matches_central_differences(spac
         gm_[idx] -= h
         fd = (phi(gp)[0] - phi(gm_)[0]) / (2 * h)
         np.testing.assert_allclose(grad[idx], fd, rtol=2e-6, atol=1e-10 * abs(p0))
+
+
+# ---------------------------------------------------------------------------------------------
+# Example 2's moving Gaussian source (Sec. 2.3.2)
+
+def _ex2_source():
+    # the paper's parameters: peak 1, width 0.05, radius 0.25, angular frequency pi, L = 1
+    return O.source_fn("gaussian", 1.0, 0.05, 0.25, math.pi, center=(0.5, 0.5))
+
+
+def test_gaussian_source_integral_is_the_closed_form():
+    """The assembled (unconstrained) source sums to int int Q dx dt = q0 2 pi sigma^2 tau: the walls
+    lie five widths from the circle, so the Gaussian's tail beyond them is below 1e-6 of it; a
+    wrong normalisation (sigma for sigma^2, a missing 2) or peak fails by a factor."""
+    om = O.Mesh((48, 48), 12, mat=O.Material(), bc="all_walls", bc_width=0.1, tau=6.0)
+    f = O.assemble_source(om, _ex2_source(), nq=2, constrained=False)
+    exact = 1.0 * 2.0 * math.pi * 0.05 ** 2 * 6.0
+    assert abs(f.sum() / exact - 1.0) < 1e-6
+
+
+def test_gaussian_source_path_and_diameter():
+    """The paper's statements: the source starts at (L/2, 3L/4); one rotation takes 2 units of
+    time (omega = pi); its diameter is about 0.3 (at 0.15 from the centre it is near 1 % of the
+    peak).  The centroid of the assembled source on a time plane (a symmetric hat in time) sits at
+    the centre of that time: (0.5, 0.75) at t = 0 and t = 2, and, moving counter-clockwise from
+    the top, (0.25, 0.5) at t = 0.5 and (0.5, 0.25) at t = 1 (a swapped x / y axis in the
+    quadrature would mirror these)."""
+    Q = _ex2_source()
+    t0 = np.zeros(1)
+    assert abs(Q(t0, np.array([0.75]), np.array([0.5]))[0] - 1.0) < 1e-15
+    peak_ratio = Q(t0, np.array([0.75]), np.array([0.5 + 0.15]))[0]
+    assert 0.005 < peak_ratio < 0.02
+    ys, xs = np.meshgrid(np.linspace(0, 1, 41), np.linspace(0, 1, 41), indexing="ij")
+    assert np.allclose(Q(np.full(ys.shape, 2.0), ys, xs), Q(np.zeros(ys.shape), ys, xs), atol=1e-12)
+    om = O.Mesh((64, 64), 64, mat=O.Material(), bc="all_walls", bc_width=0.1, tau=4.0)
+    f = O.assemble_source(om, Q, nq=2, constrained=False).reshape(om.node_shape)
+    y, x = np.meshgrid(np.linspace(0, 1, 65), np.linspace(0, 1, 65), indexing="ij")
+    for n, (cx, cy) in [(8, (0.25, 0.5)), (16, (0.5, 0.25)), (24, (0.75, 0.5)), (32, (0.5, 0.75))]:
+        w = f[n] / f[n].sum()
+        assert abs((w * x).sum() - cx) < 2e-3 and abs((w * y).sum() - cy) < 2e-3, (n, (w * x).sum(), (w * y).sum())
+
+
+# ---------------------------------------------------------------------------------------------
+# Method of Moving Asymptotes (Sec. 3.3.3), one constraint
+
+def _mma_problem(seed=0, n=400):
+    rng = np.random.default_rng(seed)
+    return rng.random(n) + 0.1, 0.3
+
+
+def test_mma_converges_to_the_closed_form_optimum():
+    """min sum c_j / x_j  s.t.  mean(x) <= V,  1e-3 <= x <= 1: convex and separable, with the
+    optimum x_j = V n sqrt(c_j) / sum_k sqrt(c_k) (Lagrange; all inside the bounds here).  Forty
+    MMA iterations from x = V reach it to 1e-12; a wrong sign in either approximation term, a
+    swapped asymptote or a wrong root of the dual does not converge to it."""
+    c, V = _mma_problem()
+    n = c.size
+    x = np.full(n, V)
+    xo1, xo2, low, upp = x.copy(), x.copy(), x.copy(), x.copy()
+    for it in range(1, 41):
+        f0 = np.sum(c / x)
+        x_new, low, upp, lam = O.mma_update(it, x, xo1, xo2, low, upp, -c / x ** 2 / f0, x.mean() / V - 1.0,
+                                            np.full(n, 1.0 / (n * V)), xmin=1e-3, xmax=1.0)
+        xo2, xo1, x = xo1, x, x_new
+    exact = V * n * np.sqrt(c) / np.sqrt(c).sum()
+    assert np.abs(x - exact).max() < 1e-12
+    assert lam > 0 and abs(x.mean() / V - 1.0) < 1e-12
+
+
+def test_mma_subproblem_solution_satisfies_its_kkt_conditions():
+    """At the returned point: every free x_j is stationary for P / (U - x) + Q / (x - L); at a bound
+    the derivative points outward; the multiplier is positive only where the approximated
+    constraint is active (complementary slackness), and then it holds with equality."""
+    rng = np.random.default_rng(3)
+    n = 2000
+    x = rng.uniform(0.1, 0.9, n)
+    low, upp = O.mma_asymptotes(3, x, x - 0.02 * rng.random(n), x + 0.01, x - 0.1, x + 0.1)
+    df0 = rng.standard_normal(n)
+    dg1 = np.full(n, 1.0 / n)
+    for g1 in (0.01, -0.5):  # violated (lam > 0), inactive (lam = 0)
+        xs, L, U, lam = O.mma_update(3, x, x - 0.02 * rng.random(n), x + 0.01, x - 0.1, x + 0.1, df0, g1, dg1)
+        alpha, beta, p0, q0, p1, q1, r1 = O.mma_subproblem(x, L, U, df0, g1, dg1)
+        P, Q = p0 + lam * p1, q0 + lam * q1
+        d = P / (U - xs) ** 2 - Q / (xs - L) ** 2
+        scale = P / (U - xs) ** 2 + Q / (xs - L) ** 2
+        free = (xs > alpha + 1e-12) & (xs < beta - 1e-12)
+        assert np.all(np.abs(d[free]) <= 1e-9 * scale[free])
+        assert np.all(d[xs <= alpha + 1e-12] >= -1e-9 * scale[xs <= alpha + 1e-12])
+        assert np.all(d[xs >= beta - 1e-12] <= 1e-9 * scale[xs >= beta - 1e-12])
+        gval = np.sum(p1 / (U - xs) + q1 / (xs - L)) + r1
+        if g1 > 0:
+            assert lam > 0 and abs(gval) < 1e-10
+        else:
+            assert lam == 0 and gval <= 0
+
+
+def test_mma_dual_maximum_by_scan():
+    """The multiplier maximises the dual W(lam) = min_x [f0~ + lam g1~] over lam >= 0: a fine scan
+    around it finds no larger value."""
+    rng = np.random.default_rng(5)
+    n = 500
+    x = rng.uniform(0.2, 0.8, n)
+    df0, dg1 = rng.standard_normal(n), np.full(n, 1.0 / n)
+    xs, L, U, lam = O.mma_update(1, x, x, x, x, x, df0, 0.01, dg1)
+    assert 0 < lam < 1e30
+    alpha, beta, p0, q0, p1, q1, r1 = O.mma_subproblem(x, L, U, df0, 0.01, dg1)
+
+    def W(lmb):
+        xv = O.mma_x_of(lmb, L, U, alpha, beta, p0, q0, p1, q1)
+        return np.sum((p0 + lmb * p1) / (U - xv) + (q0 + lmb * q1) / (xv - L)) + lmb * r1
+    w0 = W(lam)
+    for lmb in lam * np.linspace(0.9, 1.1, 201):
+        assert W(lmb) <= w0 + 1e-12 * abs(w0)
+
+
+def test_mma_infeasible_step_takes_the_most_feasible_point():
+    """A violation the move limits cannot remove: the multiplier stops at its cap and the step goes
+    to the minimiser of the approximated constraint alone in the subproblem's box (its lam -> inf
+    limit: x = (sqrt(p1) L + sqrt(q1) U) / (sqrt(p1) + sqrt(q1)), clipped)."""
+    rng = np.random.default_rng(7)
+    n = 300
+    x = rng.uniform(0.3, 0.7, n)
+    df0, dg1 = rng.standard_normal(n), np.full(n, 1.0 / n)
+    xs, L, U, lam = O.mma_update(1, x, x, x, x, x, df0, 0.5, dg1)
+    alpha, beta, p0, q0, p1, q1, r1 = O.mma_subproblem(x, L, U, df0, 0.5, dg1)
+    assert np.isfinite(lam) and lam >= 1e39
+    limit = np.clip((np.sqrt(p1) * L + np.sqrt(q1) * U) / (np.sqrt(p1) + np.sqrt(q1)), alpha, beta)
+    assert np.allclose(xs, limit, rtol=0, atol=1e-12)
+    assert np.sum(p1 / (U - xs) + q1 / (xs - L)) + r1 > 0  # still violated: infeasible step
