@@ -57,7 +57,7 @@ enum { ST_BC_PATCH_LEFT = 0, ST_BC_PATCH_BOTTOM = 1, ST_BC_ALL_WALLS = 2, ST_BC_
 enum { ST_DESIGN_EXTRUDED = 0, ST_DESIGN_SPACETIME = 1 };
 enum { ST_MEM_HOST = 0, ST_MEM_DEVICE = 1 };
 enum { ST_PREC_MIXED = 0, ST_PREC_FP64 = 1 };
-enum { ST_SRC_UNIFORM = 0, ST_SRC_SIN_T = 1 };
+enum { ST_SRC_UNIFORM = 0, ST_SRC_SIN_T = 1, ST_SRC_GAUSSIAN = 2 };
 enum { ST_OBJ_COMPLIANCE = 0, ST_OBJ_PNORM = 1 };
 enum { ST_STATE_T = 0, ST_STATE_LAMBDA = 1, ST_STATE_RHS = 2, ST_STATE_ADJ_RHS = 3 };
 enum { ST_COARSEN_SEMI = 0, ST_COARSEN_FULL = 1 };
@@ -99,7 +99,12 @@ typedef struct {
 } st_mesh_desc;
 
 typedef struct {
-    int kind;                /* ST_SRC_UNIFORM: Q = q0; ST_SRC_SIN_T: Q = q0 (a + b sin(2 pi f t)) */
+    int kind;                /* ST_SRC_UNIFORM: Q = q0; ST_SRC_SIN_T: Q = q0 (a + b sin(2 pi f t));
+                                ST_SRC_GAUSSIAN (Example 2, Sec. 2.3.2; 2 space dimensions only):
+                                Q = q0 exp(-|x - c(t)|^2 / (2 a^2)), c(t) = centre of the domain
+                                + b (cos(f t + pi/2), sin(f t + pi/2)): width a > 0, radius b,
+                                angular frequency f.  Every kind is integrated by 2-point Gauss
+                                per axis and element. */
     double q0, a, b, f;
 } st_source;
 
@@ -329,6 +334,37 @@ st_status st_fp64_fma_rate(int device, double* tflops);
 
 /* Device-memory estimate used by admission control for a mesh description. */
 long long st_footprint_bytes(const st_mesh_desc* d, int precision, int restart);
+
+/* ---- Method of Moving Asymptotes with one constraint (Sec. 3.3.3) ----
+ * The optimiser of the topology-optimisation loop: min f0(x) s.t. g1(x) <= 0, x_min <= x <= x_max
+ * (the paper's volume constraint), Svanberg's method with the asymptote rule, move limits and
+ * convex approximations below, the subproblem solved through its one-multiplier dual.  The
+ * paper cites a modified form of Guest et al.'s initial asymptotes without values; s0 is that
+ * reading.  Parameters (st_mma_params_default): first two iterations' asymptotes at
+ * x -/+ s0 (x_max - x_min) (0.05); later ones moved by incr (1.2) where the last two steps kept
+ * their sign and decr (0.7) where it flipped; move limit `move` (0.2) of the span; regularisation
+ * raa (1e-5) of the approximation terms; multiplier cap lam_max (1e40), reached only when the
+ * approximated constraint cannot be met within the move limits (the step then goes to its most
+ * feasible point). */
+typedef struct {
+    double s0, incr, decr, move, raa, lam_max;
+} st_mma_params;
+typedef struct st_mma st_mma;
+
+void st_mma_params_default(st_mma_params* p);
+/* Device state for n variables on the current device (previous two iterates, asymptotes,
+ * subproblem terms: 10 n doubles).  p NULL: the defaults.  ST_ERR_ARG for n < 1 or parameters
+ * outside (s0 > 0, incr >= 1, 0 < decr <= 1, move > 0, raa > 0, lam_max > 1); ST_ERR_OOM. */
+st_status st_mma_create(long long n, const st_mma_params* p, st_mma** out);
+st_status st_mma_destroy(st_mma* h);
+/* One MMA iteration it (1, 2, 3, ... in order; the asymptote rule uses the two previous
+ * iterates the object keeps) on `stream`: x (device, n doubles) is replaced by the new iterate;
+ * df0 and dg1 (device, n doubles) are the gradients of the objective and the constraint at x,
+ * g1 the constraint's value there.  The multiplier goes to *lam (may be NULL).  The dual's
+ * bisection reads one partial sum per trial from the device, so the call returns after the
+ * update has completed.  ST_ERR_ARG for null pointers, it < 1, x_max <= x_min or a non-finite g1. */
+st_status st_mma_update(st_mma* h, int it, double* x, const double* df0, double g1, const double* dg1, double xmin,
+                        double xmax, void* stream, double* lam);
 
 /* ---- Allocation-free residual for callers that cannot allocate device memory ----
  * The paper has no counterpart; this entry point exists for callers that must not call

@@ -19,7 +19,7 @@ BC = {"patch_left": 0, "patch_bottom": 1, "all_walls": 2, "none": 3}
 LAYOUT = {"extruded": 0, "spacetime": 1}
 MEM_HOST, MEM_DEVICE = 0, 1
 PREC = {"mixed": 0, "fp64": 1}
-SRC = {"uniform": 0, "sin_t": 1}
+SRC = {"uniform": 0, "sin_t": 1, "gaussian": 2}
 OBJ = {"compliance": 0, "pnorm": 1}
 WHICH = {"T": 0, "lambda": 1, "rhs": 2, "adj_rhs": 3}
 COARSEN = {"semi": 0, "full": 1}
@@ -73,6 +73,11 @@ class LevelInfo(C.Structure):
 class Request(C.Structure):
     _fields_ = [("mesh", MeshDesc), ("gamma", C.POINTER(C.c_double)), ("layout", C.c_int), ("count", C.c_size_t),
                 ("source", Source), ("objective", Objective), ("options", Options), ("want_gradient", C.c_int)]
+
+
+class MmaParams(C.Structure):
+    _fields_ = [("s0", C.c_double), ("incr", C.c_double), ("decr", C.c_double), ("move", C.c_double),
+                ("raa", C.c_double), ("lam_max", C.c_double)]
 
 
 class Result(C.Structure):
@@ -136,6 +141,11 @@ SIGNATURES = {
     "st_fp64_fma_rate": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
     "st_residual_norm_noalloc": (C.c_int, [C.POINTER(MeshDesc), C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                                            C.c_void_p, C.c_void_p, C.c_void_p]),
+    "st_mma_params_default": (None, [C.POINTER(MmaParams)]),
+    "st_mma_create": (C.c_int, [C.c_longlong, C.POINTER(MmaParams), C.POINTER(C.c_void_p)]),
+    "st_mma_destroy": (C.c_int, [C.c_void_p]),
+    "st_mma_update": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_double,
+                                C.c_double, C.c_void_p, C.POINTER(C.c_double)]),
 }
 
 

@@ -445,3 +445,43 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+class MMA:
+    """Method of Moving Asymptotes with one constraint on the device (st_mma_*): the optimiser of
+    the topology-optimisation loop (Sec. 3.3.3).  x, df0 and dg1 are CUDA float64 tensors of n
+    values; update() replaces x by the next iterate and returns the dual multiplier."""
+
+    def __init__(self, n: int, **params):
+        p = L.MmaParams()
+        L.lib().st_mma_params_default(C.byref(p))
+        for k, v in params.items():
+            setattr(p, k, float(v))
+        self.n = int(n)
+        self.it = 0
+        h = C.c_void_p()
+        L.check(L.lib().st_mma_create(self.n, C.byref(p), C.byref(h)), "st_mma_create")
+        self._h = h
+
+    def update(self, x, df0, g1: float, dg1, xmin: float = 0.0, xmax: float = 1.0) -> float:
+        for t in (x, df0, dg1):
+            assert _is_torch(t) and t.is_cuda and t.dtype.__repr__().endswith("float64") and t.is_contiguous()
+            assert t.numel() == self.n
+        _sync_torch(x)
+        self.it += 1
+        lam = C.c_double()
+        L.check(L.lib().st_mma_update(self._h, self.it, C.c_void_p(x.data_ptr()), C.c_void_p(df0.data_ptr()),
+                                      float(g1), C.c_void_p(dg1.data_ptr()), float(xmin), float(xmax), None,
+                                      C.byref(lam)), "st_mma_update")
+        return lam.value
+
+    def close(self):
+        if self._h:
+            L.lib().st_mma_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

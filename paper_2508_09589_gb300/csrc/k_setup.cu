@@ -381,20 +381,52 @@ __global__ void k_rhs(Geom g, int kind, double q0, double a, double b, double f,
         }
         double vol = 1.0;
         for (int d = 0; d < SD; ++d) vol *= 0.5 * g.h[d];
-        double tf = 0.0;
         const double xi[2] = {0.5 - 0.5 / sqrt(3.0), 0.5 + 0.5 / sqrt(3.0)};
-        for (int sb = 0; sb < 2; ++sb) {
-            const int slab = n_ - 1 + sb;
-            if (slab < 0 || slab >= g.net) continue;
-            const int at = 1 - sb;
-            for (int gq = 0; gq < 2; ++gq) {
-                const double phi = at == 1 ? xi[gq] : 1.0 - xi[gq];
-                const double t = (slab + xi[gq]) * g.dt;
-                const double q = kind == ST_SRC_SIN_T ? q0 * (a + b * sin(2.0 * M_PI * f * t)) : q0;
-                tf += 0.5 * g.dt * phi * q;
+        if (SD == 2 && kind == ST_SRC_GAUSSIAN) {
+            // 2-point Gauss per axis in each of the (up to) eight space-time elements of the node:
+            // weights (h_x / 2)(h_y / 2)(dt / 2), the node's trilinear basis at each point
+            const double cx = 0.5 * g.nex * g.h[0], cy = 0.5 * g.ney * g.h[1];
+            const double inv2s2 = 1.0 / (2.0 * a * a);
+            for (int o = 0; o < 4; ++o) {
+                const int ex = i_ - 1 + (o & 1), ey = j_ - 1 + (o >> 1);
+                if (ex < 0 || ex >= g.nex || ey < 0 || ey >= g.ney) continue;
+                const int bx = 1 - (o & 1), by = 1 - (o >> 1);  // the node's corner in the element
+                for (int sb = 0; sb < 2; ++sb) {
+                    const int slab = n_ - 1 + sb;
+                    if (slab < 0 || slab >= g.net) continue;
+                    const int at = 1 - sb;
+                    for (int gt = 0; gt < 2; ++gt) {
+                        const double t = (slab + xi[gt]) * g.dt;
+                        const double nt_ = at == 1 ? xi[gt] : 1.0 - xi[gt];
+                        const double x1 = cx + b * cos(f * t + 0.5 * M_PI), x2 = cy + b * sin(f * t + 0.5 * M_PI);
+                        for (int gy = 0; gy < 2; ++gy) {
+                            const double y = (ey + xi[gy]) * g.h[1];
+                            const double ny_ = by == 1 ? xi[gy] : 1.0 - xi[gy];
+                            for (int gx = 0; gx < 2; ++gx) {
+                                const double x = (ex + xi[gx]) * g.h[0];
+                                const double nx_ = bx == 1 ? xi[gx] : 1.0 - xi[gx];
+                                const double r2 = (x - x1) * (x - x1) + (y - x2) * (y - x2);
+                                v += vol * 0.5 * g.dt * nx_ * ny_ * nt_ * q0 * exp(-r2 * inv2s2);
+                            }
+                        }
+                    }
+                }
             }
+        } else {
+            double tf = 0.0;
+            for (int sb = 0; sb < 2; ++sb) {
+                const int slab = n_ - 1 + sb;
+                if (slab < 0 || slab >= g.net) continue;
+                const int at = 1 - sb;
+                for (int gq = 0; gq < 2; ++gq) {
+                    const double phi = at == 1 ? xi[gq] : 1.0 - xi[gq];
+                    const double t = (slab + xi[gq]) * g.dt;
+                    const double q = kind == ST_SRC_SIN_T ? q0 * (a + b * sin(2.0 * M_PI * f * t)) : q0;
+                    tf += 0.5 * g.dt * phi * q;
+                }
+            }
+            v = nel * vol * tf;
         }
-        v = nel * vol * tf;
     }
     out[idx_] = v;
     ST_NODE_LOOP_END

@@ -1433,6 +1433,10 @@ struct st_mesh : public st::Mesh {};
 
 static Mesh* M(st_mesh* m) { return static_cast<Mesh*>(m); }
 
+namespace st {
+Mesh* mesh_of(st_mesh* m) { return M(m); }
+}  // namespace st
+
 static st_status finish_sync(Mesh* mm) {
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(mm->stream);
@@ -1471,6 +1475,17 @@ static st_status vcycle_entry(Mesh* mm, int transpose, const void* b, void* x) {
     const st_status r = finish_sync(mm);
     mm->timer_collect();
     return r;
+}
+
+// A source description the right-hand side kernel can integrate on this mesh.
+static st_status check_source(const st::Mesh* mm, const st_source& q) {
+    if (q.kind != ST_SRC_UNIFORM && q.kind != ST_SRC_SIN_T && q.kind != ST_SRC_GAUSSIAN)
+        return st::fail(ST_ERR_ARG, "unknown source kind");
+    if (!std::isfinite(q.q0) || !std::isfinite(q.a) || !std::isfinite(q.b) || !std::isfinite(q.f))
+        return st::fail(ST_ERR_ARG, "source parameters must be finite");
+    if (q.kind == ST_SRC_GAUSSIAN && (mm->sd != 2 || !(q.a > 0)))
+        return st::fail(ST_ERR_ARG, "the Gaussian source needs two space dimensions and a positive width");
+    return ST_OK;
 }
 
 extern "C" {
@@ -1586,9 +1601,7 @@ st_status st_solve_forward(st_mesh* m, const st_source* q, const st_options* o, 
     if (!m || !q) return fail(ST_ERR_ARG, "null argument");
     Mesh* mm = M(m);
     if (!mm->have_design) return fail(ST_ERR_STATE, "st_set_design must precede st_solve_forward");
-    if (q->kind != ST_SRC_UNIFORM && q->kind != ST_SRC_SIN_T) return fail(ST_ERR_ARG, "unknown source kind");
-    if (!std::isfinite(q->q0) || !std::isfinite(q->a) || !std::isfinite(q->b) || !std::isfinite(q->f))
-        return fail(ST_ERR_ARG, "source parameters must be finite");
+    CKS(check_source(mm, *q));
     cudaSetDevice(mm->device);
     st::launch_rhs(mm->sd, mm->lv[0].g, q->kind, q->q0, q->a, q->b, q->f, mm->f, mm->stream);
     st_status r = st::solve(mm, false, o, stats);
@@ -1672,9 +1685,7 @@ st_status st_solve_forward_batch(st_mesh* const* m, int count, const st_source* 
         if (!m[k]) return fail(ST_ERR_ARG, "null mesh in the batch");
         ms[k] = M(m[k]);
         if (!ms[k]->have_design) return fail(ST_ERR_STATE, "st_set_design must precede st_solve_forward_batch");
-        if (q[k].kind != ST_SRC_UNIFORM && q[k].kind != ST_SRC_SIN_T) return fail(ST_ERR_ARG, "unknown source kind");
-        if (!std::isfinite(q[k].q0) || !std::isfinite(q[k].a) || !std::isfinite(q[k].b) || !std::isfinite(q[k].f))
-            return fail(ST_ERR_ARG, "source parameters must be finite");
+        CKS(check_source(ms[k], q[k]));
     }
     for (int k = 0; k < count; ++k) {
         cudaSetDevice(ms[k]->device);

@@ -189,4 +189,7 @@ st_status solve_batch(Mesh* const* ms, int n, bool adjoint, const st_options* op
 st_status filter(Mesh* m, const double* in, double* out, size_t count, int mem, double rx, double rt, double rtol,
                  int max_it, int* iters);
 
+// the Mesh behind a C-ABI handle
+Mesh* mesh_of(st_mesh* m);
+
 }  // namespace st
