@@ -930,3 +930,74 @@ def mma_update(it: int, x, xold1, xold2, low, upp, df0, g1: float, dg1, xmin: fl
                 hi = mid
         lam = hi
     return mma_x_of(lam, low, upp, alpha, beta, p0, q0, p1, q1), low, upp, lam
+
+
+# ----------------------------------------------------------------------------
+# One design iteration of the optimisation problem (Sec. 3.3): the nested formulation solves the
+# state for the current design, then the objective (Sec. 3.3.1) and its adjoint, the
+# sensitivities with respect to the physical design (Sec. 3.3.3), the chain rule through the
+# projection and the filter (Sec. 3.3.2), the volume constraint and its gradient, and one MMA
+# step on gamma in [0, 1].  Readings:
+# - the volume constraint is taken on the physical design gamma_bar, so its gradient passes
+#   through the projection and the filter like the objective's;
+# - uniform elements: chi = mean(gamma_bar) / v_f - 1 and d chi / d gamma_bar_e = 1 / (v_f N_e);
+# - the objective enters MMA as TO_OBJ_SCALE * phi / phi_1, phi_1 its value at the first
+#   iteration (the paper gives no scaling; MMA's fixed regularisation needs one).
+# ----------------------------------------------------------------------------
+TO_OBJ_SCALE = 10.0
+
+
+def volume_constraint(gamma_bar: np.ndarray, vf: float):
+    """chi = sum_e gamma_bar_e v_e / (v_f |Pi|) - 1 and d chi / d gamma_bar (Sec. 3.3.1, 3.3.3)."""
+    g = np.asarray(gamma_bar, dtype=np.float64)
+    return float(g.mean() / vf - 1.0), np.full(g.shape, 1.0 / (vf * g.size))
+
+
+def topopt_gradients(m: Mesh, gamma: np.ndarray, vf: float, r_x: float, r_t: float, beta: float = 32.0,
+                     eta: float = 0.5, objective: str = "pnorm", P: int = 20, source: str = "uniform",
+                     q0: float = 1.0, **src) -> dict:
+    """phi, chi and their gradients with respect to the design variables gamma (filter and
+    projection included), with the intermediate fields."""
+    gb, gt = design_chain(m, gamma, r_x, r_t, beta, eta)
+    sol = forward(m, gb, source, q0, **src)
+    if objective == "pnorm":
+        phi, dphids = pnorm(m, sol.s, P)
+    else:
+        phi, dphids = compliance(sol.f, sol.s), sol.f
+    lam = adjoint(sol.A, dphids, dirichlet_mask(m), sol.lu)
+    dphys = sensitivities(m, gb, sol.s, lam)
+    chi, dchi_phys = volume_constraint(gb, vf)
+    return dict(phi=phi, chi=chi, dphi=chain_rule(m, dphys, gt, r_x, r_t, beta, eta),
+                dchi=chain_rule(m, dchi_phys, gt, r_x, r_t, beta, eta), gamma_tilde=gt, gamma_bar=gb,
+                s=sol.s, lam=lam)
+
+
+@dataclass
+class TopOptHistory:
+    """What the loop carries from one iteration to the next: the iteration count, phi_1 and the
+    MMA history (two previous iterates, asymptotes)."""
+    it: int = 0
+    phi1: float = 0.0
+    xold1: Optional[np.ndarray] = None
+    xold2: Optional[np.ndarray] = None
+    low: Optional[np.ndarray] = None
+    upp: Optional[np.ndarray] = None
+
+
+def topopt_step(m: Mesh, gamma: np.ndarray, hist: TopOptHistory, vf: float, r_x: float, r_t: float,
+                **kw) -> Tuple[np.ndarray, dict]:
+    """One design iteration from gamma: returns the next design and the iteration's fields
+    (phi and chi at gamma, gradients, the MMA multiplier lam_mma)."""
+    d = topopt_gradients(m, gamma, vf, r_x, r_t, **kw)
+    x = np.asarray(gamma, dtype=np.float64).reshape(-1)
+    if hist.it == 0:
+        hist.phi1 = d["phi"]
+        hist.xold1 = hist.xold2 = hist.low = hist.upp = np.zeros_like(x)
+    hist.it += 1
+    df0 = (TO_OBJ_SCALE / hist.phi1) * d["dphi"].reshape(-1)
+    xn, low, upp, lam = mma_update(hist.it, x, hist.xold1, hist.xold2, hist.low, hist.upp, df0, d["chi"],
+                                   d["dchi"].reshape(-1))
+    hist.xold2, hist.xold1, hist.low, hist.upp = hist.xold1, x.copy(), low, upp
+    d["lam_mma"] = lam
+    d["df0"] = df0
+    return xn.reshape(np.shape(gamma)), d
