@@ -366,6 +366,63 @@ st_status st_mma_destroy(st_mma* h);
 st_status st_mma_update(st_mma* h, int it, double* x, const double* df0, double g1, const double* dg1, double xmin,
                         double xmax, void* stream, double* lam);
 
+/* ---- Topology-optimisation loop (Sec. 3.3, the nested formulation of the optimisation
+ * problem): one design iteration per st_topopt_step, every step on the mesh's device and stream:
+ *   gamma~ = F gamma (PDE filter, Sec. 3.3.2), gamma_bar = H(gamma~) (projection),
+ *   st_set_design(gamma_bar), forward solve, objective phi and adjoint solve, d phi / d gamma_bar,
+ *   chain rule d phi / d gamma = F (H'(gamma~) d phi / d gamma_bar) (F symmetric: uniform
+ *   elements), the volume constraint chi = sum gamma_bar_e v_e / (v_f |Pi|) - 1 on the physical
+ *   design with d chi / d gamma = F (H'(gamma~) / (v_f N_e)) (Sec. 3.3.3), and one MMA update of
+ *   gamma in [0, 1] (st_mma_update).  The objective enters MMA scaled by obj_scale / phi_1, phi_1
+ *   its value at the first iteration.  From the second iteration on the forward and adjoint
+ *   solves start from the previous design's solutions when warm_start is set (Sec. 3.2). */
+typedef struct {
+    double vf;          /* volume fraction v_f, 0 < vf < 1 (paper: 0.3) */
+    double r_x, r_t;    /* filter radii; <= 0 selects the minimum 2.4 h and 2.4 dt */
+    double beta, eta;   /* projection sharpness and threshold (paper: 32, 0.5) */
+    int objective;      /* ST_OBJ_PNORM (paper, P = 20) or ST_OBJ_COMPLIANCE */
+    int P;              /* p-norm exponent */
+    double obj_scale;   /* MMA sees obj_scale * phi / phi_1 (default 10) */
+    double filter_rtol; /* filter CG tolerance (default 1e-10) */
+    int filter_max_it;  /* filter CG iteration cap (default 2000) */
+    int warm_start;     /* 1: warm-started solves from the second iteration (default 1) */
+    st_mma_params mma;  /* optimiser parameters (st_mma_params_default) */
+} st_topopt_params;
+typedef struct {
+    int iteration;      /* design iterations taken, this one included */
+    double phi;         /* objective at the design entering this iteration (unscaled) */
+    double chi;         /* volume constraint at that design (<= 0: satisfied) */
+    double lam;         /* MMA multiplier of the volume constraint */
+    double change;      /* max_e |gamma_e after - gamma_e before| */
+    st_stats forward;   /* the forward solve */
+    st_stats adjoint;   /* the adjoint solve */
+    int filter_its;     /* CG iterations of the three filter solves together */
+    double seconds;     /* host wall time of the iteration */
+} st_topopt_stats;
+typedef struct st_topopt st_topopt;
+enum { ST_TO_GAMMA = 0, ST_TO_GAMMA_TILDE = 1, ST_TO_GAMMA_BAR = 2, ST_TO_DPHI = 3, ST_TO_DCHI = 4 };
+
+void st_topopt_params_default(st_topopt_params* p);
+/* An optimisation of mesh m (which must outlive the handle) from the initial design gamma0
+ * (count values, layout ST_DESIGN_*, host or device per mem; clipped to [0, 1]).  The handle
+ * owns 8 count doubles of device memory plus an st_mma.  ST_ERR_ARG: count does not match the
+ * layout, vf outside (0, 1), beta <= 0, eta outside (0, 1), obj_scale <= 0, an unknown
+ * objective or P outside [1, 64]; ST_ERR_NUMERIC: a non-finite gamma0; ST_ERR_OOM. */
+st_status st_topopt_create(st_mesh* m, const st_topopt_params* p, const double* gamma0, int layout, size_t count,
+                           int mem, st_topopt** out);
+st_status st_topopt_destroy(st_topopt* h);
+/* One design iteration with source q and solver options o (NULL: defaults; o->warm_start is
+ * replaced by the handle's rule).  On return the handle holds the new design; stats (may be
+ * NULL) describe the iteration.  ST_ERR_NOT_CONVERGED: a solve or a filter stopped at its
+ * iteration cap; the iteration was still completed from its last iterate.  Other errors leave
+ * the design unchanged. */
+st_status st_topopt_step(st_topopt* h, const st_source* q, const st_options* o, st_topopt_stats* stats);
+/* Copy one field (ST_TO_*, count values: gamma, gamma~, gamma_bar, and the chain-ruled
+ * gradients d phi / d gamma and d chi / d gamma of the last iteration, the first scaled as MMA
+ * saw it) to out (host or device per mem).  ST_ERR_STATE for the fields an iteration makes
+ * before the first st_topopt_step. */
+st_status st_topopt_get(st_topopt* h, int which, double* out, size_t count, int mem);
+
 /* ---- Allocation-free residual for callers that cannot allocate device memory ----
  * The paper has no counterpart; this entry point exists for callers that must not call
  * cudaMalloc (code running inside another framework's stream capture or memory pool, or

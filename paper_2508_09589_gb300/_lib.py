@@ -80,6 +80,28 @@ class MmaParams(C.Structure):
                 ("raa", C.c_double), ("lam_max", C.c_double)]
 
 
+class TopOptParams(C.Structure):
+    _fields_ = [("vf", C.c_double), ("r_x", C.c_double), ("r_t", C.c_double), ("beta", C.c_double),
+                ("eta", C.c_double), ("objective", C.c_int), ("P", C.c_int), ("obj_scale", C.c_double),
+                ("filter_rtol", C.c_double), ("filter_max_it", C.c_int), ("warm_start", C.c_int),
+                ("mma", MmaParams)]
+
+
+class TopOptStats(C.Structure):
+    _fields_ = [("iteration", C.c_int), ("phi", C.c_double), ("chi", C.c_double), ("lam", C.c_double),
+                ("change", C.c_double), ("forward", Stats), ("adjoint", Stats), ("filter_its", C.c_int),
+                ("seconds", C.c_double)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("forward", "adjoint")}
+        d["forward"] = self.forward.as_dict()
+        d["adjoint"] = self.adjoint.as_dict()
+        return d
+
+
+TO_FIELD = {"gamma": 0, "gamma_tilde": 1, "gamma_bar": 2, "dphi": 3, "dchi": 4}
+
+
 class Result(C.Structure):
     _fields_ = [("status", C.c_int), ("phi", C.c_double), ("forward", Stats), ("adjoint", Stats),
                 ("latency_s", C.c_double), ("queue_s", C.c_double), ("footprint", C.c_longlong),
@@ -146,6 +168,12 @@ SIGNATURES = {
     "st_mma_destroy": (C.c_int, [C.c_void_p]),
     "st_mma_update": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_double,
                                 C.c_double, C.c_void_p, C.POINTER(C.c_double)]),
+    "st_topopt_params_default": (None, [C.POINTER(TopOptParams)]),
+    "st_topopt_create": (C.c_int, [C.c_void_p, C.POINTER(TopOptParams), C.c_void_p, C.c_int, C.c_size_t, C.c_int,
+                                   C.POINTER(C.c_void_p)]),
+    "st_topopt_destroy": (C.c_int, [C.c_void_p]),
+    "st_topopt_step": (C.c_int, [C.c_void_p, C.POINTER(Source), C.POINTER(Options), C.POINTER(TopOptStats)]),
+    "st_topopt_get": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.c_int]),
 }
 
 

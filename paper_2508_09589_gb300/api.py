@@ -485,3 +485,83 @@ class MMA:
             self.close()
         except Exception:
             pass
+
+
+class TopOpt:
+    """The topology-optimisation loop of Sec. 3.3 on a mesh (st_topopt_*): each step() is one
+    design iteration (filter, projection, design, forward and adjoint solves, chain rule,
+    volume constraint, MMA update), all in the library.  gamma0 is a numpy array or a CUDA
+    float64 tensor in the mesh's design layout.  Parameters: vf, r_x, r_t, beta, eta,
+    objective ("pnorm" or "compliance"), P, obj_scale, filter_rtol, filter_max_it, warm_start
+    and the MMA's (s0, incr, decr, move, raa, lam_max)."""
+
+    def __init__(self, mesh: Mesh, gamma0, layout: Optional[str] = None, **params):
+        p = L.TopOptParams()
+        L.lib().st_topopt_params_default(C.byref(p))
+        for k, v in params.items():
+            if k == "objective":
+                p.objective = L.OBJ[v]
+            elif k in ("P", "filter_max_it", "warm_start"):
+                setattr(p, k, int(v))
+            elif k in ("s0", "incr", "decr", "move", "raa", "lam_max"):
+                setattr(p.mma, k, float(v))
+            else:
+                if k not in dict(L.TopOptParams._fields_):
+                    raise TypeError(f"unknown parameter {k}")
+                setattr(p, k, float(v))
+        self.mesh = mesh
+        sp = int(np.prod(mesh.ns))
+        if _is_torch(gamma0):
+            assert gamma0.is_cuda and gamma0.dtype.__repr__().endswith("float64") and gamma0.is_contiguous()
+            n, ptr, mem = gamma0.numel(), gamma0.data_ptr(), L.MEM_DEVICE
+            _sync_torch(gamma0)
+        else:
+            arr = np.ascontiguousarray(np.asarray(gamma0, dtype=np.float64))
+            n, ptr, mem = arr.size, arr.ctypes.data, L.MEM_HOST
+        if layout is None:
+            layout = "extruded" if n == sp else "spacetime"
+        self.layout = layout
+        self.n = n
+        self.shape = tuple(reversed(mesh.ns)) if layout == "extruded" else (mesh.nt,) + tuple(reversed(mesh.ns))
+        h = C.c_void_p()
+        L.check(L.lib().st_topopt_create(mesh._h, C.byref(p), C.c_void_p(ptr), L.LAYOUT[layout], n, mem,
+                                         C.byref(h)), "st_topopt_create")
+        self._h = h
+        mesh.design_size = n
+        mesh.layout = layout
+
+    def step(self, src: Optional[L.Source] = None, opts: Optional[L.Options] = None,
+             allow_not_converged: bool = False, **kw) -> Dict:
+        """One design iteration; returns its statistics (phi, chi, lam, change, solver stats)."""
+        src = src or source(**{k: v for k, v in kw.items() if k in ("kind", "q0", "a", "b", "f")})
+        opts = opts or options(**{k: v for k, v in kw.items() if k not in ("kind", "q0", "a", "b", "f")})
+        st = L.TopOptStats()
+        code = L.lib().st_topopt_step(self._h, C.byref(src), C.byref(opts), C.byref(st))
+        L.check(code, "st_topopt_step", allow=(-3,) if allow_not_converged else ())
+        d = st.as_dict()
+        d["status"] = code
+        return d
+
+    def get(self, which: str = "gamma", out=None):
+        """A field of the loop (gamma, gamma_tilde, gamma_bar, dphi, dchi): into a CUDA tensor
+        `out`, else a new numpy array in the design's shape."""
+        if out is not None and _is_torch(out):
+            _sync_torch(out)
+            L.check(L.lib().st_topopt_get(self._h, L.TO_FIELD[which], C.c_void_p(out.data_ptr()), self.n,
+                                          L.MEM_DEVICE), "st_topopt_get")
+            return out
+        arr = np.empty(self.n, dtype=np.float64)
+        L.check(L.lib().st_topopt_get(self._h, L.TO_FIELD[which], C.c_void_p(arr.ctypes.data), self.n, L.MEM_HOST),
+                "st_topopt_get")
+        return arr.reshape(self.shape)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            L.lib().st_topopt_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
