@@ -256,6 +256,11 @@ def run_native(args):
                 line["serving"] = serving_bench(args)
             except Exception as e:  # noqa: BLE001
                 line["serving"] = {"error": f"{type(e).__name__}: {e}"}
+        if args.design_iters > 0:
+            try:
+                line["design_loop"] = design_loop(args)
+            except Exception as e:  # noqa: BLE001
+                line["design_loop"] = {"error": f"{type(e).__name__}: {e}"}
         if args.ablation:
             try:
                 line["coarsening_ablation"] = coarsening_ablation(args)
@@ -562,6 +567,35 @@ def coarsening_ablation(args):
     return out
 
 
+def design_loop(args):
+    """Design iterations of the optimisation loop (Sec. 3.3) on the headline workload's mesh and
+    source: from the homogeneous design gamma = 0.5, v_f = 0.3, the paper's outer tolerance 1e-5
+    and warm-started solves; one untimed iteration, then args.design_iters timed ones (wall time
+    per iteration, with its forward, adjoint and filter + MMA shares)."""
+    from paper_2508_09589_gb300 import Mesh, TopOpt, options, source
+    w = W.WORKLOADS[args.workload]
+    mesh = Mesh(w.ns, w.nt, material=w.material, bc=w.bc, bc_width=w.bc_width, tau=w.tau)
+    shape = tuple(reversed(w.ns)) if w.extruded else (w.nt,) + tuple(reversed(w.ns))
+    to = TopOpt(mesh, np.full(shape, 0.5), "extruded" if w.extruded else "spacetime", vf=0.3)
+    src = source(w.source, w.source_q0, w.source_a, w.source_b, w.source_f)
+    opt = options(rtol=1e-5, precision="mixed", max_it=200)
+    to.step(src, opt)
+    its = [to.step(src, opt) for _ in range(args.design_iters)]
+    sec = statistics.median(st["seconds"] for st in its)
+    fwd = statistics.median(st["forward"]["seconds"] for st in its)
+    adj = statistics.median(st["adjoint"]["seconds"] for st in its)
+    out = {"mesh": list(w.ns) + [w.nt], "design_vars": int(np.prod(shape)), "iterations_timed": len(its),
+           "ms_per_design_iteration": 1e3 * sec, "forward_ms": 1e3 * fwd, "adjoint_ms": 1e3 * adj,
+           "filter_mma_rest_ms": 1e3 * (sec - fwd - adj),
+           "outer_its_fwd": [st["forward"]["outer_its"] for st in its],
+           "outer_its_adj": [st["adjoint"]["outer_its"] for st in its],
+           "filter_cg_its": [st["filter_its"] for st in its],
+           "phi": [st["phi"] for st in its], "chi": [st["chi"] for st in its]}
+    to.close()
+    mesh.close()
+    return out
+
+
 def run_vcycles(args):
     """Kernel-profiling mode: design set-up and K mixed-precision V-cycles on the workload
     (no Krylov solve, so only the multigrid storage is resident: a few GB at 256^2 x 256)."""
@@ -679,6 +713,8 @@ def main():
                     help="Poisson arrival rates as fractions of saturation (mixed precision)")
     ap.add_argument("--serve-fp64-loads", type=lambda v: [float(x) for x in v.split(",") if x], default=[0.7],
                     help="Poisson arrival rates as fractions of saturation (all-FP64)")
+    ap.add_argument("--design-iters", type=int, default=3,
+                    help="timed design iterations of the optimisation loop after one warm-up (0 skips)")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--vcycles", type=int, default=0,
                     help="profiling mode: only K mixed V-cycles on the workload, no solve")
