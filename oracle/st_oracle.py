@@ -1001,3 +1001,100 @@ def topopt_step(m: Mesh, gamma: np.ndarray, hist: TopOptHistory, vf: float, r_x:
     d["lam_mma"] = lam
     d["df0"] = df0
     return xn.reshape(np.shape(gamma)), d
+
+
+# ----------------------------------------------------------------------------
+# Reference time stepping (Sec. 4): the comparison solver takes first-order backward
+# differences (BDF1) in time on the spatial mesh.  Reading: consistent, capacity-weighted mass,
+#   (M_C + dt K_k) T^{n+1} = M_C T^n + dt F(t_{n+1}),   T^0 = 0,
+# with M_C = sum_e C_e M_e and K_k = sum_e k_e K_e from the design of slab n (a space-time design
+# changes from step to step), F_i(t) = int N_i Q(t, x) dx by 2-point Gauss per axis, and the
+# spatial sink prescribed (T = 0) at every step.
+# ----------------------------------------------------------------------------
+def spatial_element_matrices(h: Sequence[float], ngauss: int = 2) -> Tuple[np.ndarray, np.ndarray]:
+    """int N_a N_b and int grad N_a . grad N_b on one h_1 x ... brick (Gauss quadrature, exact
+    for these multilinear products with 2 points)."""
+    sd = len(h)
+    nv = 2 ** sd
+    gp, gw = gauss_1d(ngauss)
+    Me = np.zeros((nv, nv))
+    Ke = np.zeros((nv, nv))
+    for q in itertools.product(range(ngauss), repeat=sd):
+        wq = np.prod([gw[qi] * h[d] for d, qi in enumerate(q)])
+        N = np.ones(nv)
+        dN = np.ones((sd, nv))
+        for a in range(nv):
+            for d in range(sd):
+                phi, dphi = _basis_1d(gp[q[d]])
+                bit = (a >> d) & 1
+                N[a] *= phi[bit]
+                for dd in range(sd):
+                    dN[dd, a] *= (dphi[bit] / h[d]) if dd == d else phi[bit]
+        Me += wq * np.outer(N, N)
+        Ke += wq * dN.T @ dN
+    return Me, Ke
+
+
+def spatial_connectivity(m: Mesh) -> np.ndarray:
+    """conn[e, a] = spatial node of local node a (bits x, y, [z]) of spatial element e; the
+    spatial node numbering is that of one time plane."""
+    return element_connectivity(with_size(m, m.ns, 1))[:, : 2 ** m.sd]
+
+
+def bdf1_matrices(m: Mesh, gamma_slab: np.ndarray) -> Tuple[sp.csr_matrix, sp.csr_matrix]:
+    """M_C and K_k on the spatial nodes for one slab's design (spatial element order)."""
+    Me, Ke = spatial_element_matrices(m.h)
+    conn = spatial_connectivity(m)
+    ge = np.asarray(gamma_slab, dtype=np.float64).reshape(-1)
+    nv = conn.shape[1]
+    n_sp = int(np.prod([n + 1 for n in m.ns]))
+    rows = np.repeat(conn, nv, axis=1).reshape(-1)
+    cols = np.tile(conn, (1, nv)).reshape(-1)
+    C = simp_C(m.mat, ge)
+    k = simp_k(m.mat, ge)
+    Mc = sp.csr_matrix(((C[:, None, None] * Me[None]).reshape(-1), (rows, cols)), shape=(n_sp, n_sp))
+    Kk = sp.csr_matrix(((k[:, None, None] * Ke[None]).reshape(-1), (rows, cols)), shape=(n_sp, n_sp))
+    return Mc, Kk
+
+
+def bdf1_load(m: Mesh, Q: Callable, t: float, nq: int = 2) -> np.ndarray:
+    """F_i(t) = int N_i(x) Q(t, x) dx by nq-point Gauss per axis."""
+    sd = m.sd
+    gp, gw = gauss_1d(nq)
+    conn = spatial_connectivity(m)
+    eidx = np.indices(tuple(reversed(m.ns))).reshape(sd, -1)  # ([z], y, x)
+    F = np.zeros(int(np.prod([n + 1 for n in m.ns])))
+    for q in itertools.product(range(nq), repeat=sd):
+        wq = np.prod([gw[qi] * m.h[d] for d, qi in enumerate(q)])
+        xs = [(eidx[sd - 1 - d] + gp[q[d]]) * m.h[d] for d in range(sd)]  # x, y, (z)
+        Qv = Q(np.full(eidx.shape[1], t), *reversed(xs))
+        for a in range(2 ** sd):
+            Na = 1.0
+            for d in range(sd):
+                Na *= (1.0 - gp[q[d]]) if ((a >> d) & 1) == 0 else gp[q[d]]
+            np.add.at(F, conn[:, a], wq * Na * Qv)
+    return F
+
+
+def bdf1_forward(m: Mesh, gamma: np.ndarray, source: str = "uniform", q0: float = 1.0, **src) -> np.ndarray:
+    """BDF1 trajectory T (nt + 1 planes of spatial nodes, plane n at t = n dt), direct sparse
+    solve per step."""
+    Q = source_fn(source, q0, **src)
+    n_sp = int(np.prod([n + 1 for n in m.ns]))
+    dm = dirichlet_mask(m).reshape(m.nt + 1, n_sp)[1]
+    eg = element_gamma(m, gamma).reshape(m.nt, -1)
+    extruded = np.asarray(gamma).size == int(np.prod(m.ns))
+    keep = sp.diags((~dm).astype(np.float64))
+    T = np.zeros(n_sp)
+    traj = [T]
+    lu = Mc = None
+    for n in range(m.nt):
+        if lu is None or not extruded:
+            Mc, Kk = bdf1_matrices(m, eg[n])
+            A = (keep @ (Mc + m.dt * Kk) @ keep + sp.diags(dm.astype(np.float64))).tocsr()
+            lu = factor(A)
+        r = Mc @ T + m.dt * bdf1_load(m, Q, (n + 1) * m.dt)
+        r[dm] = 0.0
+        T = solve_direct(A, r, lu)
+        traj.append(T)
+    return np.array(traj)

@@ -236,6 +236,8 @@ def test_difference_to_implicit_euler_is_first_order():
             T = np.linalg.solve(Lhs, r)
             traj.append(T)
         traj = np.array(traj)
+        # the oracle's BDF1 reference solver (Sec. 4) is this scheme
+        np.testing.assert_allclose(O.bdf1_forward(m, g, "uniform", 1.0), traj, rtol=0, atol=1e-13 * np.abs(traj).max())
         st = sol.s.reshape(nt + 1, 81)
         diffs.append(np.abs(st[: nt] - traj[: nt]).max())  # last plane excluded (half step)
     orders = [math.log2(diffs[i] / diffs[i + 1]) for i in range(3)]
