@@ -261,6 +261,11 @@ def run_native(args):
                 line["design_loop"] = design_loop(args)
             except Exception as e:  # noqa: BLE001
                 line["design_loop"] = {"error": f"{type(e).__name__}: {e}"}
+        if args.bdf1:
+            try:
+                line["bdf1_comparison"] = bdf1_comparison(args)
+            except Exception as e:  # noqa: BLE001
+                line["bdf1_comparison"] = {"error": f"{type(e).__name__}: {e}"}
         if args.ablation:
             try:
                 line["coarsening_ablation"] = coarsening_ablation(args)
@@ -596,6 +601,50 @@ def design_loop(args):
     return out
 
 
+def bdf1_comparison(args):
+    """The paper's comparison (Sec. 4) on one GPU: the forward solve of the headline workload by the
+    all-at-once solver and by the BDF1 time-stepping reference (one FGMRES + spatial multigrid
+    solve per step, warm-started from the previous step), both to the paper's outer tolerance
+    1e-5 in mixed precision; one untimed run each, then one timed; the largest difference of
+    the two trajectories relative to the solution's maximum."""
+    import torch
+    from paper_2508_09589_gb300 import BDF1, Mesh, options, source
+    w = W.WORKLOADS[args.workload]
+    g = torch.tensor(W.make_design(w).reshape(-1), dtype=torch.float64, device="cuda")
+    layout = "extruded" if w.extruded else "spacetime"
+    src = source(w.source, w.source_q0, w.source_a, w.source_b, w.source_f)
+    opt = options(rtol=1e-5, precision="mixed", max_it=200)
+    kw = dict(material=w.material, bc=w.bc, bc_width=w.bc_width, tau=w.tau)
+    mesh = Mesh(w.ns, w.nt, **kw)
+    mesh.set_design(g, layout)
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        f = mesh.solve_forward(src, opt)
+        torch.cuda.synchronize()
+        t_st = time.perf_counter() - t0
+    Ts = torch.empty(mesh.n_nodes, dtype=torch.float64, device="cuda")
+    mesh.state("T", out=Ts)
+    out = {"mesh": list(w.ns) + [w.nt], "dofs": mesh.n_nodes,
+           "all_at_once": {"ms": 1e3 * t_st, "outer_its": f["outer_its"], "dof_per_s": mesh.n_nodes / t_st}}
+    mesh.close()
+    b = BDF1(w.ns, w.nt, **kw)
+    b.set_design(g, layout)
+    Tb = torch.empty_like(Ts)
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, st = b.forward(src, opt, out=Tb)
+        torch.cuda.synchronize()
+        t_b = time.perf_counter() - t0
+    b.close()
+    out["bdf1"] = {"ms": 1e3 * t_b, "steps": st["steps"], "outer_its": st["outer_its"],
+                   "max_outer_its_per_step": st["max_outer_its"], "dof_per_s": Ts.numel() / t_b}
+    out["all_at_once_speedup"] = t_b / t_st
+    out["max_rel_diff"] = float((Ts - Tb).abs().max() / Ts.abs().max())
+    return out
+
+
 def run_vcycles(args):
     """Kernel-profiling mode: design set-up and K mixed-precision V-cycles on the workload
     (no Krylov solve, so only the multigrid storage is resident: a few GB at 256^2 x 256)."""
@@ -715,6 +764,8 @@ def main():
                     help="Poisson arrival rates as fractions of saturation (all-FP64)")
     ap.add_argument("--design-iters", type=int, default=3,
                     help="timed design iterations of the optimisation loop after one warm-up (0 skips)")
+    ap.add_argument("--no-bdf1", dest="bdf1", action="store_false",
+                    help="skip the all-at-once against BDF1 time-stepping comparison")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--vcycles", type=int, default=0,
                     help="profiling mode: only K mixed V-cycles on the workload, no solve")

@@ -423,6 +423,38 @@ st_status st_topopt_step(st_topopt* h, const st_source* q, const st_options* o, 
  * before the first st_topopt_step. */
 st_status st_topopt_get(st_topopt* h, int which, double* out, size_t count, int mem);
 
+/* ---- Reference time stepping (Sec. 4): the comparison solver of the paper, first-order
+ * backward differences (BDF1) on the spatial mesh with consistent capacity-weighted mass,
+ *   (M_C + dt K_k) T^{n+1} = M_C T^n + dt F(t_{n+1}),  T^0 = 0,  dt = tau / n_t,
+ * step n taking the design of slab n and F_i(t) = Q(t) int N_i (uniform and sine sources), the
+ * spatial sink prescribed at every step.  Each step is one FGMRES solve preconditioned by the
+ * library's multigrid on a one-slab mesh whose upper-plane block is exactly M_C + dt K_k
+ * (conductivities tripled, final time dt): Algorithm 1 coarsens it in space only, the paper's
+ * spatial multigrid for time stepping.  Each solve starts from the previous plane. */
+typedef struct {
+    int steps;              /* steps taken */
+    long long outer_its;    /* FGMRES iterations of all steps */
+    int max_outer_its;      /* of the worst step */
+    double max_rel_res;     /* largest true relative residual at a step's exit */
+    double seconds;         /* host wall time of the call */
+} st_bdf1_stats;
+typedef struct st_bdf1 st_bdf1;
+/* The solver for the space-time problem d (its n_t steps, tau, material, sink, hierarchy
+ * options; the step mesh copies d with n_t = 1).  Holds the step mesh, the design and the
+ * trajectory ((n_t + 1) planes) on the device.  Errors as st_create_mesh; ST_ERR_OOM. */
+st_status st_bdf1_create(const st_mesh_desc* d, st_bdf1** out);
+st_status st_bdf1_destroy(st_bdf1* h);
+/* The design (layout ST_DESIGN_*, count values, host or device per mem; clipped to [0, 1]).
+ * ST_ERR_NUMERIC for a NaN or infinite value in the first slab (later slabs are checked at
+ * their step). */
+st_status st_bdf1_set_design(st_bdf1* h, const double* gamma, int layout, size_t count, int mem);
+/* Run the n_t steps with source q (ST_SRC_UNIFORM or ST_SRC_SIN_T; others ST_ERR_ARG) and the
+ * step solves' options o (NULL: defaults; warm_start is always on).  T (may be NULL; host or
+ * device per mem) receives the trajectory, count = (n_t + 1) * nodes per plane, plane n at
+ * t = n dt.  ST_ERR_NOT_CONVERGED: a step stopped at max_it (the trajectory is complete). */
+st_status st_bdf1_forward(st_bdf1* h, const st_source* q, const st_options* o, double* T, size_t count, int mem,
+                          st_bdf1_stats* stats);
+
 /* ---- Allocation-free residual for callers that cannot allocate device memory ----
  * The paper has no counterpart; this entry point exists for callers that must not call
  * cudaMalloc (code running inside another framework's stream capture or memory pool, or

@@ -99,6 +99,14 @@ class TopOptStats(C.Structure):
         return d
 
 
+class Bdf1Stats(C.Structure):
+    _fields_ = [("steps", C.c_int), ("outer_its", C.c_longlong), ("max_outer_its", C.c_int),
+                ("max_rel_res", C.c_double), ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 TO_FIELD = {"gamma": 0, "gamma_tilde": 1, "gamma_bar": 2, "dphi": 3, "dchi": 4}
 
 
@@ -174,6 +182,11 @@ SIGNATURES = {
     "st_topopt_destroy": (C.c_int, [C.c_void_p]),
     "st_topopt_step": (C.c_int, [C.c_void_p, C.POINTER(Source), C.POINTER(Options), C.POINTER(TopOptStats)]),
     "st_topopt_get": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.c_int]),
+    "st_bdf1_create": (C.c_int, [C.POINTER(MeshDesc), C.POINTER(C.c_void_p)]),
+    "st_bdf1_destroy": (C.c_int, [C.c_void_p]),
+    "st_bdf1_set_design": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_size_t, C.c_int]),
+    "st_bdf1_forward": (C.c_int, [C.c_void_p, C.POINTER(Source), C.POINTER(Options), C.c_void_p, C.c_size_t,
+                                  C.c_int, C.POINTER(Bdf1Stats)]),
 }
 
 

@@ -565,3 +565,66 @@ class TopOpt:
             self.close()
         except Exception:
             pass
+
+
+class BDF1:
+    """The paper's time-stepping reference solver (st_bdf1_*, Sec. 4): backward Euler with
+    consistent mass on the spatial mesh of the space-time problem (ns, nt, **mesh keywords as
+    for Mesh), each step solved by FGMRES with the library's spatial multigrid."""
+
+    def __init__(self, ns: Sequence[int], nt: int, **kw):
+        self.desc = mesh_desc(ns, nt, **kw)
+        self.ns = tuple(int(v) for v in ns)
+        self.nt = int(nt)
+        h = C.c_void_p()
+        L.check(L.lib().st_bdf1_create(C.byref(self.desc), C.byref(h)), "st_bdf1_create")
+        self._h = h
+
+    @property
+    def plane_shape(self):
+        return tuple(n + 1 for n in reversed(self.ns))
+
+    def set_design(self, gamma, layout: Optional[str] = None):
+        sp = int(np.prod(self.ns))
+        if _is_torch(gamma):
+            assert gamma.is_cuda and gamma.dtype.__repr__().endswith("float64") and gamma.is_contiguous()
+            n, ptr, mem = gamma.numel(), gamma.data_ptr(), L.MEM_DEVICE
+            _sync_torch(gamma)
+        else:
+            arr = np.ascontiguousarray(np.asarray(gamma, dtype=np.float64))
+            n, ptr, mem = arr.size, arr.ctypes.data, L.MEM_HOST
+        if layout is None:
+            layout = "extruded" if n == sp else "spacetime"
+        L.check(L.lib().st_bdf1_set_design(self._h, C.c_void_p(ptr), L.LAYOUT[layout], n, mem), "st_bdf1_set_design")
+
+    def forward(self, src: Optional[L.Source] = None, opts: Optional[L.Options] = None, out=None,
+                allow_not_converged: bool = False, **kw):
+        """Run the steps; returns (trajectory, stats).  The trajectory (nt + 1 planes) goes to the
+        CUDA tensor `out` when given, else to a new numpy array."""
+        src = src or source(**{k: v for k, v in kw.items() if k in ("kind", "q0", "a", "b", "f")})
+        opts = opts or options(**{k: v for k, v in kw.items() if k not in ("kind", "q0", "a", "b", "f")})
+        n = (self.nt + 1) * int(np.prod(self.plane_shape))
+        st = L.Bdf1Stats()
+        if out is not None and _is_torch(out):
+            assert out.numel() == n
+            _sync_torch(out)
+            ptr, mem, res = out.data_ptr(), L.MEM_DEVICE, out
+        else:
+            res = np.empty((self.nt + 1,) + self.plane_shape, dtype=np.float64)
+            ptr, mem = res.ctypes.data, L.MEM_HOST
+        code = L.lib().st_bdf1_forward(self._h, C.byref(src), C.byref(opts), C.c_void_p(ptr), n, mem, C.byref(st))
+        L.check(code, "st_bdf1_forward", allow=(-3,) if allow_not_converged else ())
+        d = st.as_dict()
+        d["status"] = code
+        return res, d
+
+    def close(self):
+        if getattr(self, "_h", None):
+            L.lib().st_bdf1_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

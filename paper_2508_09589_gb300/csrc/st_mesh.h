@@ -192,4 +192,11 @@ st_status filter(Mesh* m, const double* in, double* out, size_t count, int mem, 
 // the Mesh behind a C-ABI handle
 Mesh* mesh_of(st_mesh* m);
 
+// the bodies of st_create_mesh, st_set_design and the forward (adjoint = false) or adjoint solve
+// of the right-hand side already in m->f (m->adjrhs), from the state in m->s (m->lam) when
+// o->warm_start is set
+st_status create_mesh(const st_mesh_desc* d, Mesh** out);
+st_status set_design(Mesh* m, const double* gamma, int layout, size_t count, int mem);
+st_status solve(Mesh* m, bool adjoint, const st_options* op, st_stats* stats);
+
 }  // namespace st
