@@ -1098,3 +1098,46 @@ def bdf1_forward(m: Mesh, gamma: np.ndarray, source: str = "uniform", q0: float 
         T = solve_direct(A, r, lu)
         traj.append(T)
     return np.array(traj)
+
+
+def bdf1_adjoint(m: Mesh, gamma: np.ndarray, traj: np.ndarray, P: int = 20):
+    """Discrete adjoint of bdf1_forward for the p-norm objective of Sec. 3.3.1 taken over the
+    space-time elements of the trajectory.  Step n is the constraint
+    A_n T^{n+1} - M_n T^n - dt F^{n+1} = 0 (A_n = M_C + dt K_k of slab n, prescribed rows and
+    columns removed), so the multipliers solve, from the last step backwards,
+      A_{m-1} Lambda^m = d phi / d T^m + M_m Lambda^{m+1},   Lambda^{N+1} = 0,
+    zero at prescribed nodes, and for element e of slab n
+      d phi / d gamma_e = -Lambda^{n+1}_e . (C'_e M_e (T^{n+1} - T^n)_e + dt k'_e K_e T^{n+1}_e),
+    summed over the slabs for an extruded design.  Returns (phi, Lambda, sensitivities)."""
+    n_sp = int(np.prod([n + 1 for n in m.ns]))
+    traj = np.asarray(traj, dtype=np.float64).reshape(m.nt + 1, n_sp)
+    phi, dphids = pnorm(m, traj.reshape(-1), P)
+    g = dphids.reshape(m.nt + 1, n_sp)
+    dm = dirichlet_mask(m).reshape(m.nt + 1, n_sp)[1]
+    keep = sp.diags((~dm).astype(np.float64))
+    eg = element_gamma(m, gamma).reshape(m.nt, -1)
+    lam = np.zeros((m.nt + 2, n_sp))
+    for mm_ in range(m.nt, 0, -1):
+        Mc_prev, Kk_prev = bdf1_matrices(m, eg[mm_ - 1])
+        A = (keep @ (Mc_prev + m.dt * Kk_prev) @ keep + sp.diags(dm.astype(np.float64))).tocsr()
+        r = g[mm_].copy()
+        if mm_ < m.nt:
+            Mc_next, _ = bdf1_matrices(m, eg[mm_])
+            r += Mc_next @ lam[mm_ + 1]
+        r[dm] = 0.0
+        lam[mm_] = solve_direct(A, r)
+    Me, Ke = spatial_element_matrices(m.h)
+    conn = spatial_connectivity(m)
+    dC = simp_dC(m.mat, eg)
+    dk = simp_dk(m.mat, eg)
+    sens = np.zeros((m.nt, conn.shape[0]))
+    for n in range(m.nt):
+        le = lam[n + 1][conn]
+        dT = (traj[n + 1] - traj[n])[conn]
+        T1 = traj[n + 1][conn]
+        sens[n] = -(dC[n] * np.einsum("ea,ab,eb->e", le, Me, dT) +
+                    m.dt * dk[n] * np.einsum("ea,ab,eb->e", le, Ke, T1))
+    sens = sens.reshape(m.elem_shape)
+    if np.asarray(gamma).size == int(np.prod(m.ns)):
+        sens = sens.sum(axis=0)
+    return phi, lam[: m.nt + 1], sens

@@ -64,3 +64,31 @@ def test_spatial_element_matrices_closed_forms():
     k1 = lambda hh: np.array([[1.0, -1.0], [-1.0, 1.0]]) / hh
     np.testing.assert_allclose(Me, np.kron(m1(h[1]), m1(h[0])), rtol=1e-14)
     np.testing.assert_allclose(Ke, np.kron(m1(h[1]), k1(h[0])) + np.kron(k1(h[1]), m1(h[0])), rtol=1e-13)
+
+
+@pytest.mark.parametrize("spacetime", [False, True])
+def test_adjoint_sensitivities_match_central_differences(spacetime):
+    """d phi / d gamma of bdf1_adjoint (the p-norm of the trajectory's element means) equals central
+    differences of phi(gamma) through the whole stepping; a wrong slab in M_m Lambda^{m+1}, a
+    missing capacity term or a sign error fails it."""
+    m = O.Mesh((4, 3), 5, mat=O.Material(C_ins=0.5, C_con=1.0, k_ins=0.03, k_con=3.0, p_c=2, p_k=3),
+               bc="patch_left", bc_width=0.5, tau=1.5)
+    rng = np.random.default_rng(12)
+    g = 0.2 + 0.6 * rng.random(m.elem_shape if spacetime else (3, 4))
+    kw = dict(source="sin_t", q0=1.0, a=1.0, b=0.8, f=1.0)
+    T = O.bdf1_forward(m, g, **kw)
+    phi, lam, sens = O.bdf1_adjoint(m, g, T, P=6)
+    assert sens.shape == g.shape
+    assert np.all(lam[0] == 0.0)
+
+    def value(gam):
+        return O.pnorm(m, O.bdf1_forward(m, gam, **kw).reshape(-1), 6)[0]
+
+    assert value(g) == pytest.approx(phi, rel=1e-14)
+    h = 1e-6
+    for flat in rng.choice(g.size, 6, replace=False):
+        idx = np.unravel_index(flat, g.shape)
+        gp, gm_ = g.copy(), g.copy()
+        gp[idx] += h
+        gm_[idx] -= h
+        np.testing.assert_allclose(sens[idx], (value(gp) - value(gm_)) / (2 * h), rtol=1e-6, atol=1e-10 * phi)
