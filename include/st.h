@@ -454,6 +454,18 @@ st_status st_bdf1_set_design(st_bdf1* h, const double* gamma, int layout, size_t
  * t = n dt.  ST_ERR_NOT_CONVERGED: a step stopped at max_it (the trajectory is complete). */
 st_status st_bdf1_forward(st_bdf1* h, const st_source* q, const st_options* o, double* T, size_t count, int mem,
                           st_bdf1_stats* stats);
+/* Discrete adjoint of the stepping for the p-norm objective of Sec. 3.3.1 (exponent P in [1, 64])
+ * over the space-time elements of the last forward trajectory: from the last step backwards
+ *   A_{m-1} Lambda^m = d phi / d T^m + M_m Lambda^{m+1},  Lambda^{n_t + 1} = 0,
+ * (A_n = M_C + dt K_k and M_n = M_C of slab n), each solve started from Lambda^{m+1}.  *phi
+ * (may be NULL) receives the objective; Lambda (may be NULL; host or device per mem, count =
+ * (n_t + 1) plane nodes) the multipliers, plane 0 zero.  ST_ERR_STATE without a forward run. */
+st_status st_bdf1_adjoint(st_bdf1* h, int P, const st_options* o, double* phi, double* Lambda, size_t count, int mem,
+                          st_bdf1_stats* stats);
+/* d phi / d gamma_e = -Lambda^{n+1}_e . (C'_e M_e (T^{n+1} - T^n)_e + dt k'_e K_e T^{n+1}_e) for
+ * element e of slab n, summed over the slabs for an extruded design; count = the design size.
+ * ST_ERR_STATE without an adjoint run. */
+st_status st_bdf1_sensitivities(st_bdf1* h, double* out, size_t count, int mem);
 
 /* ---- Allocation-free residual for callers that cannot allocate device memory ----
  * The paper has no counterpart; this entry point exists for callers that must not call

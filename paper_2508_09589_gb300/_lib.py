@@ -187,6 +187,9 @@ SIGNATURES = {
     "st_bdf1_set_design": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_size_t, C.c_int]),
     "st_bdf1_forward": (C.c_int, [C.c_void_p, C.POINTER(Source), C.POINTER(Options), C.c_void_p, C.c_size_t,
                                   C.c_int, C.POINTER(Bdf1Stats)]),
+    "st_bdf1_adjoint": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Options), C.POINTER(C.c_double), C.c_void_p,
+                                  C.c_size_t, C.c_int, C.POINTER(Bdf1Stats)]),
+    "st_bdf1_sensitivities": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int]),
 }
 
 

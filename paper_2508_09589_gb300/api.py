@@ -596,6 +596,7 @@ class BDF1:
         if layout is None:
             layout = "extruded" if n == sp else "spacetime"
         L.check(L.lib().st_bdf1_set_design(self._h, C.c_void_p(ptr), L.LAYOUT[layout], n, mem), "st_bdf1_set_design")
+        self._design_size = n
 
     def forward(self, src: Optional[L.Source] = None, opts: Optional[L.Options] = None, out=None,
                 allow_not_converged: bool = False, **kw):
@@ -617,6 +618,41 @@ class BDF1:
         d = st.as_dict()
         d["status"] = code
         return res, d
+
+    def adjoint(self, P: int = 20, opts: Optional[L.Options] = None, out=None, allow_not_converged: bool = False,
+                **kw):
+        """The discrete adjoint for the p-norm objective; returns (phi, multipliers, stats), the
+        multipliers into the CUDA tensor `out` when given, else a new numpy array."""
+        opts = opts or options(**kw)
+        n = (self.nt + 1) * int(np.prod(self.plane_shape))
+        st = L.Bdf1Stats()
+        phi = C.c_double()
+        if out is not None and _is_torch(out):
+            assert out.numel() == n
+            _sync_torch(out)
+            ptr, mem, res = out.data_ptr(), L.MEM_DEVICE, out
+        else:
+            res = np.empty((self.nt + 1,) + self.plane_shape, dtype=np.float64)
+            ptr, mem = res.ctypes.data, L.MEM_HOST
+        code = L.lib().st_bdf1_adjoint(self._h, int(P), C.byref(opts), C.byref(phi), C.c_void_p(ptr), n, mem,
+                                       C.byref(st))
+        L.check(code, "st_bdf1_adjoint", allow=(-3,) if allow_not_converged else ())
+        d = st.as_dict()
+        d["status"] = code
+        return phi.value, res, d
+
+    def sensitivities(self, out=None):
+        """d phi / d gamma of the last adjoint, in the design's layout (CUDA tensor `out` or numpy)."""
+        n = self._design_size
+        if out is not None and _is_torch(out):
+            _sync_torch(out)
+            L.check(L.lib().st_bdf1_sensitivities(self._h, C.c_void_p(out.data_ptr()), n, L.MEM_DEVICE),
+                    "st_bdf1_sensitivities")
+            return out
+        arr = np.empty(n, dtype=np.float64)
+        L.check(L.lib().st_bdf1_sensitivities(self._h, C.c_void_p(arr.ctypes.data), n, L.MEM_HOST),
+                "st_bdf1_sensitivities")
+        return arr
 
     def close(self):
         if getattr(self, "_h", None):

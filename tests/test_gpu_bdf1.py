@@ -1,6 +1,7 @@
 """The time-stepping reference solver on the device (st_bdf1_*, Sec. 4) against the oracle's
 BDF1 (direct solve per step): whole trajectories for extruded and space-time designs, 2-D and
-3-D, uniform and sine sources, both multigrid precisions; the gap to the all-at-once solution as
+3-D, uniform and sine sources, both multigrid precisions; the discrete adjoint and the design
+sensitivities of the p-norm; the gap to the all-at-once solution as
 dt shrinks; argument and state checks."""
 import numpy as np
 import pytest
@@ -56,6 +57,37 @@ def test_trajectory_matches_the_oracle(ns, nt, layout, kind, precision):
     b.close()
 
 
+ADJ_CASES = [
+    ((30, 26), 10, "extruded", "mixed"),
+    ((30, 26), 8, "spacetime", "fp64"),
+    ((8, 6, 6), 6, "extruded", "mixed"),
+    ((8, 6, 6), 5, "spacetime", "mixed"),
+]
+
+
+@pytest.mark.parametrize("ns,nt,layout,precision", ADJ_CASES)
+def test_adjoint_and_sensitivities_match_the_oracle(ns, nt, layout, precision):
+    om = O.Mesh(ns, nt, mat=MAT, bc="patch_left", bc_width=0.3, tau=1.0)
+    rng = np.random.default_rng(7 * nt + len(ns))
+    g = 0.1 + 0.8 * rng.random(tuple(reversed(ns)) if layout == "extruded" else om.elem_shape)
+    src = dict(q0=1.0, a=1.0, b=0.5, f=2.0)
+    T_ref = O.bdf1_forward(om, g, "sin_t", **src)
+    phi_ref, lam_ref, sens_ref = O.bdf1_adjoint(om, g, T_ref, P=20)
+    b = _bdf1(om, coarse_dof_cap=300)
+    b.set_design(g, layout)
+    b.forward(kind="sin_t", rtol=1e-13, precision=precision, max_it=300, **src)
+    phi, lam, st = b.adjoint(P=20, rtol=1e-13, precision=precision, max_it=300)
+    assert st["steps"] == nt and st["max_rel_res"] <= 1e-13
+    np.testing.assert_allclose(phi, phi_ref, rtol=1e-11)
+    assert rel_err(lam.reshape(lam_ref.shape), lam_ref) < 1e-9
+    sens = b.sensitivities()
+    assert rel_err(sens, sens_ref.reshape(-1)) < 1e-9
+    out = torch.empty(sens.size, dtype=torch.float64, device="cuda")
+    b.sensitivities(out)
+    np.testing.assert_array_equal(out.cpu().numpy(), sens)
+    b.close()
+
+
 def test_gap_to_the_all_at_once_solution_shrinks_with_dt():
     """For a time-constant design the all-at-once and the BDF1 trajectories on the same mesh differ
     (the space-time scheme couples time non-causally) by a gap that shrinks as dt is halved; the
@@ -97,6 +129,17 @@ def test_arguments_and_state():
     with pytest.raises(L.STError) as e:
         b.forward(kind="gaussian", a=0.05, b=0.25, f=3.0)
     assert e.value.code == -1
+    with pytest.raises(L.STError) as e:
+        b.adjoint()
+    assert e.value.code == -8
     T, st = b.forward(rtol=1e-10)
     assert st["steps"] == 4 and np.all(T[0] == 0.0) and T[-1].max() > 0
+    with pytest.raises(L.STError) as e:
+        b.sensitivities()
+    assert e.value.code == -8
+    with pytest.raises(L.STError):
+        b.adjoint(P=0)
+    phi, lam, _ = b.adjoint(P=4, rtol=1e-10)
+    assert phi > 0 and np.all(lam[0] == 0.0)
+    assert b.sensitivities().shape == (64,)
     b.close()
