@@ -652,25 +652,49 @@ def gmres_jacobi(A: sp.spmatrix, b: np.ndarray, x0: np.ndarray, m: int = 10,
     return x0 + dinv * (V[:k].T @ y)
 
 
+# A cheaper smoother, one of the variants the paper's outlook names (Sec. 6, "cheaper
+# smoothers"): damped (weighted) Jacobi, x <- x + omega D^{-1} (b - A x), nu sweeps.
+# Reading: the same nu for pre- and post-smoothing, pre-smoothing from zero (its first sweep
+# is x = omega D^{-1} b), omega fixed per hierarchy.
+def jacobi_smooth(A: sp.spmatrix, b: np.ndarray, x0: np.ndarray, nu: int, omega: float,
+                  dtype=np.float64) -> np.ndarray:
+    """nu damped Jacobi sweeps from x0 (every vector operation in dtype)."""
+    A = sp.csr_matrix(A).astype(dtype)
+    dinv = (dtype(1.0) / A.diagonal()).astype(dtype)
+    x = np.asarray(x0).astype(dtype)
+    b = np.asarray(b).astype(dtype)
+    w = dtype(omega)
+    for _ in range(nu):
+        x = x + w * (dinv * (b - A @ x))
+    return x
+
+
 def vcycle(mg: List[MGLevel], b: np.ndarray, l: int = 0, nsmooth: int = 10,
-           transpose: bool = False, dtype=np.float64) -> np.ndarray:
+           transpose: bool = False, dtype=np.float64, smoother: str = "gmres",
+           omega: float = 0.7) -> np.ndarray:
     """One V-cycle for A_l x = b (A_l^T for transpose=True, which uses the same
     hierarchy since (P^T A P)^T = P^T A^T P).
 
     dtype = float32 runs the smoothing, residuals and transfers in single precision and
     keeps the coarsest solve in float64 (its result rounded to float32), the precision
-    split of a mixed-precision multigrid; float64 is the oracle proper."""
+    split of a mixed-precision multigrid; float64 is the oracle proper.  smoother "gmres"
+    is the paper's Jacobi-GMRES(nsmooth); "jacobi" takes nsmooth damped Jacobi sweeps."""
     A = mg[l].A.T.tocsr() if transpose else mg[l].A
     b = np.asarray(b).astype(dtype)
     if l == len(mg) - 1:
         return np.linalg.solve(A.toarray(), b.astype(np.float64)).astype(dtype)
     A = sp.csr_matrix(A).astype(dtype)
-    x = gmres_jacobi(A, b, np.zeros_like(b), nsmooth, dtype=dtype)
+
+    def smooth(x0):
+        if smoother == "jacobi":
+            return jacobi_smooth(A, b, x0, nsmooth, omega, dtype=dtype)
+        return gmres_jacobi(A, b, x0, nsmooth, dtype=dtype)
+    x = smooth(np.zeros_like(b))
     r = b - A @ x
     Pt = mg[l].Pt.astype(dtype)
-    xc = vcycle(mg, Pt.T @ r, l + 1, nsmooth, transpose, dtype)
+    xc = vcycle(mg, Pt.T @ r, l + 1, nsmooth, transpose, dtype, smoother, omega)
     x = x + Pt @ xc
-    return gmres_jacobi(A, b, x, nsmooth, dtype=dtype)
+    return smooth(x)
 
 
 def abs_operator(m: Mesh, gamma: np.ndarray, ngauss: int = 3) -> sp.csr_matrix:

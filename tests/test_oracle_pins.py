@@ -957,3 +957,54 @@ def test_mma_infeasible_step_takes_the_most_feasible_point():
     limit = np.clip((np.sqrt(p1) * L + np.sqrt(q1) * U) / (np.sqrt(p1) + np.sqrt(q1)), alpha, beta)
     assert np.allclose(xs, limit, rtol=0, atol=1e-12)
     assert np.sum(p1 / (U - xs) + q1 / (xs - L)) + r1 > 0  # still violated: infeasible step
+
+
+# ---------------------------------------------------------------- damped Jacobi smoother (variant)
+def test_jacobi_damps_laplacian_modes_by_the_closed_form():
+    """On the 1-D Dirichlet Laplacian (D = 2/h^2) each sine mode sin(k pi x) is an eigenvector
+    of I - omega D^{-1} A with eigenvalue 1 - omega (1 - cos(k pi h)): nu sweeps from the mode
+    (b = 0) multiply it by that factor to the nu-th power."""
+    n = 31
+    h = 1.0 / (n + 1)
+    A = sp.diags([-np.ones(n - 1), 2 * np.ones(n), -np.ones(n - 1)], [-1, 0, 1]) / h ** 2
+    xg = np.arange(1, n + 1) * h
+    for k, omega, nu in ((1, 0.7, 3), (7, 0.5, 2), (30, 0.8, 4)):
+        e = np.sin(k * np.pi * xg)
+        out = O.jacobi_smooth(A, np.zeros(n), e, nu, omega)
+        fac = (1.0 - omega * (1.0 - np.cos(k * np.pi * h))) ** nu
+        np.testing.assert_allclose(out, fac * e, rtol=1e-12, atol=1e-14)
+
+
+def test_jacobi_fixed_point_and_first_sweep():
+    """The solution is a fixed point of the sweep; from zero the first sweep is omega D^{-1} b."""
+    rng = np.random.default_rng(5)
+    A = sp.random(40, 40, density=0.1, random_state=5) + sp.diags(5.0 + rng.random(40))
+    b = rng.standard_normal(40)
+    x = np.linalg.solve(A.toarray(), b)
+    np.testing.assert_allclose(O.jacobi_smooth(A, b, x, 3, 0.7), x, rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(O.jacobi_smooth(A, b, np.zeros(40), 1, 0.6), 0.6 * b / A.diagonal(), rtol=1e-15)
+
+
+def test_jacobi_vcycle_contracts_and_single_level_is_two_smoothings():
+    """With damped Jacobi smoothing the V-cycle of a space-time problem contracts (rate below 0.7
+    over eight cycles); on a two-level hierarchy it equals the hand composition."""
+    mat = O.Material(C_ins=0.5, C_con=1.0, k_ins=0.03, k_con=3.0, p_c=2, p_k=3)
+    m = O.Mesh((16, 16), 16, mat=mat, bc="patch_left", bc_width=0.2)
+    g = np.random.default_rng(2).random((16, 16))
+    mg = O.build_mg(m, g, O.hierarchy(m, coarse_cap=300))
+    A = mg[0].A
+    f = O.assemble_source(m, O.source_fn("uniform", 1.0))
+    x = np.zeros_like(f)
+    res = [np.linalg.norm(f)]
+    for _ in range(8):
+        x = x + O.vcycle(mg, f - A @ x, nsmooth=2, smoother="jacobi", omega=0.7)
+        res.append(np.linalg.norm(f - A @ x))
+    assert (res[-1] / res[0]) ** (1 / 8) < 0.7, res
+    two = O.build_mg(m, g, O.hierarchy(m, n_levels=2))
+    b = np.random.default_rng(3).standard_normal(m.n_nodes)
+    b[two[0].mask] = 0
+    A0, Pt = two[0].A, two[0].Pt
+    x1 = O.jacobi_smooth(A0, b, np.zeros_like(b), 2, 0.7)
+    xc = np.linalg.solve(two[1].A.toarray(), Pt.T @ (b - A0 @ x1))
+    x2 = O.jacobi_smooth(A0, b, x1 + Pt @ xc, 2, 0.7)
+    np.testing.assert_allclose(O.vcycle(two, b, nsmooth=2, smoother="jacobi", omega=0.7), x2, rtol=1e-13, atol=1e-15)
