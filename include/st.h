@@ -66,6 +66,8 @@ enum { ST_COARSEN_SEMI = 0, ST_COARSEN_FULL = 1 };
  * GMRES = FP64 right-Jacobi-preconditioned restarted GMRES(16), the paper's coarsest solve
  * (Sec. 3.2), stopped at coarse_rtol or after coarse_max_it iterations. */
 enum { ST_COARSE_AUTO = 0, ST_COARSE_DENSE = 1, ST_COARSE_GMRES = 2 };
+/* Multigrid smoother of the levels above the coarsest (st_mesh_desc.smoother). */
+enum { ST_SMOOTH_GMRES = 0, ST_SMOOTH_JACOBI = 1 };
 
 /* Modified SIMP (Sec. 2.2): C = C_ins + (C_con - C_ins) g^p_c, k = k_ins + (k_con - k_ins) g^p_k.
  * Integer powers p_c, p_k >= 1. */
@@ -96,6 +98,11 @@ typedef struct {
     int march_blocks;        /* tuning: thread-block budget of the time-marching stencil kernels
                                 (0: 912, two waves on 152 SMs; at most 4096); a smaller budget
                                 gives each block a longer time chunk */
+    int smoother;            /* ST_SMOOTH_GMRES: the paper's Jacobi-GMRES; ST_SMOOTH_JACOBI: damped
+                                Jacobi sweeps x += omega D^-1 (b - J x), a cheaper variant (the
+                                paper's outlook); st_options.smooth_steps counts sweeps */
+    double smoother_omega;   /* Jacobi damping omega in (0, 1] (default 0.5; 0.7 lets the V-cycle
+                                diverge on some space-time designs) */
 } st_mesh_desc;
 
 typedef struct {

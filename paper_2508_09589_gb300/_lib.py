@@ -17,6 +17,7 @@ STATUS = {0: "ST_OK", -1: "ST_ERR_ARG", -2: "ST_ERR_OOM", -3: "ST_ERR_NOT_CONVER
           -10: "ST_ERR_CANCELLED"}
 BC = {"patch_left": 0, "patch_bottom": 1, "all_walls": 2, "none": 3}
 LAYOUT = {"extruded": 0, "spacetime": 1}
+SMOOTHER = {"gmres": 0, "jacobi": 1}
 MEM_HOST, MEM_DEVICE = 0, 1
 PREC = {"mixed": 0, "fp64": 1}
 SRC = {"uniform": 0, "sin_t": 1, "gaussian": 2}
@@ -36,7 +37,8 @@ class MeshDesc(C.Structure):
                 ("tau", C.c_double), ("mat", Material), ("bc", C.c_int), ("bc_width", C.c_double),
                 ("lambda_crit", C.c_double), ("coarse_dof_cap", C.c_longlong), ("max_levels", C.c_int),
                 ("coarsening", C.c_int), ("device", C.c_int), ("coarse_solver", C.c_int),
-                ("coarse_max_it", C.c_int), ("coarse_rtol", C.c_double), ("march_blocks", C.c_int)]
+                ("coarse_max_it", C.c_int), ("coarse_rtol", C.c_double), ("march_blocks", C.c_int),
+                ("smoother", C.c_int), ("smoother_omega", C.c_double)]
 
 
 class Source(C.Structure):

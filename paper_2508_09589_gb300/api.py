@@ -41,7 +41,8 @@ def mesh_desc(ns: Sequence[int], nt: int, *, ext: Optional[Sequence[float]] = No
               material: Optional[dict] = None, bc: str = "patch_left", bc_width: float = 0.1,
               lambda_crit: float = 0.5, coarse_dof_cap: int = 2000, max_levels: int = 0,
               coarsening: str = "semi", device: int = 0, coarse_solver: str = "auto",
-              coarse_max_it: int = 0, coarse_rtol: float = 0.0, march_blocks: int = 0) -> L.MeshDesc:
+              coarse_max_it: int = 0, coarse_rtol: float = 0.0, march_blocks: int = 0,
+              smoother: str = "gmres", smoother_omega: float = 0.5) -> L.MeshDesc:
     d = L.MeshDesc()
     L.lib().st_mesh_desc_default(C.byref(d))
     d.ndim_space = len(ns)
@@ -64,6 +65,8 @@ def mesh_desc(ns: Sequence[int], nt: int, *, ext: Optional[Sequence[float]] = No
     d.coarse_max_it = int(coarse_max_it)
     d.coarse_rtol = float(coarse_rtol)
     d.march_blocks = int(march_blocks)
+    d.smoother = L.SMOOTHER[smoother]
+    d.smoother_omega = float(smoother_omega)
     return d
 
 

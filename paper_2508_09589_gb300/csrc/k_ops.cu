@@ -777,6 +777,30 @@ void launch_smooth(int sd, int lvl, const OpL0<T>& o0, const OpLc<T>& oc, bool t
     }
 }
 
+// x = (add ? x : 0) + omega D^-1 r, element by element
+template <typename T>
+__global__ void __launch_bounds__(256) k_jac_update(long long n, T omega, const T* __restrict__ dinv,
+                                                    const T* __restrict__ r, T* __restrict__ x, int add) {
+    pdl_enter();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const T v = omega * dinv[i] * r[i];
+        x[i] = add ? x[i] + v : v;
+    }
+}
+
+template <typename T>
+void launch_jacobi_smooth(int sd, int lvl, const OpL0<T>& o0, const OpLc<T>& oc, bool tr, const T* b, T* x,
+                          const T* dinv, T* r, int sweeps, bool zero_init, T omega, cudaStream_t s) {
+    const long long N = (lvl == 0 ? o0.g : oc.g).nnodes;
+    const int blocks = (int)std::min<long long>(4LL * 1216, (N + 255) / 256);
+    for (int k = 0; k < sweeps; ++k) {
+        const bool first = k == 0 && zero_init;
+        if (!first) launch_residual<T>(sd, lvl, o0, oc, tr, b, x, r, s);
+        note_launch(s);
+        launch_pdl(k_jac_update<T>, blocks, 256, 0, s, N, omega, dinv, first ? b : (const T*)r, x, first ? 0 : 1);
+    }
+}
+
 template <typename T>
 void launch_coarse_solve(const double* Ainv, int n, bool tr, const T* b, T* x, cudaStream_t s) {
     note_launch(s);
@@ -895,6 +919,8 @@ void launch_mask_copy(int sd, const Geom& g, const double* src, double* dst, cud
     template void launch_smooth<T>(int, int, const OpL0<T>&, const OpLc<T>&, bool, const T*, T*, const T*, Basis<T>, \
                                    T*, T*, int, bool, SmState*, RedBuf, cudaStream_t, cudaEvent_t*, const T*);      \
     template void launch_coarse_solve<T>(const double*, int, bool, const T*, T*, cudaStream_t);                     \
+    template void launch_jacobi_smooth<T>(int, int, const OpL0<T>&, const OpLc<T>&, bool, const T*, T*, const T*,   \
+                                          T*, int, bool, T, cudaStream_t);                                           \
     template void launch_fg_apply_dots<T>(int, const OpL0<double>&, bool, const T*, T*, double*, double* const*,    \
                                           int, FgState*, RedBuf, cudaStream_t);                                      \
     template void launch_fg_normalize<T>(const Geom&, const double*, double*, T*, int, FgState*, cudaStream_t);     \

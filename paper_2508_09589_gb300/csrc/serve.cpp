@@ -60,6 +60,8 @@ std::string desc_key(const st_mesh_desc& d) {
     put(k, d.coarse_max_it);
     put(k, d.coarse_rtol);
     put(k, d.march_blocks);
+    put(k, d.smoother);
+    put(k, d.smoother_omega);
     return k;
 }
 

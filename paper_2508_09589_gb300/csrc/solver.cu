@@ -325,6 +325,9 @@ st_status validate_desc(const st_mesh_desc* d) {
         return fail(ST_ERR_ARG, "unknown coarse_solver");
     if (d->coarse_max_it < 0 || d->coarse_rtol < 0 || !(d->coarse_rtol < 1))
         return fail(ST_ERR_ARG, "coarse_max_it must be >= 0 and coarse_rtol in [0, 1)");
+    if (d->smoother != ST_SMOOTH_GMRES && d->smoother != ST_SMOOTH_JACOBI) return fail(ST_ERR_ARG, "unknown smoother");
+    if (d->smoother == ST_SMOOTH_JACOBI && !(d->smoother_omega > 0 && d->smoother_omega <= 1))
+        return fail(ST_ERR_ARG, "Jacobi damping must be in (0, 1]");
     if (d->coarse_dof_cap < 1 || d->coarse_dof_cap > kMaxCoarse)
         return fail(ST_ERR_ARG, "coarse_dof_cap must be in [1, " + std::to_string(kMaxCoarse) + "]");
     long long nn = d->n_t + 1;
@@ -674,7 +677,7 @@ st_status Mesh::ensure_mg(int steps) {
         W.ready = true;
         W.dinv_version = -1;
     }
-    if (steps + 1 > W.nbasis) {
+    if (desc.smoother == ST_SMOOTH_GMRES && steps + 1 > W.nbasis) {  // Jacobi sweeps keep no Krylov basis
         drop_graphs();
         ws_version++;
         for (int l = 0; l < L - 1; ++l) {
@@ -791,6 +794,11 @@ void Mesh::coarse_gmres(bool tr) {
 template <typename T>
 void Mesh::smooth(int l, bool tr, bool zero_init, int steps) {
     MGWork<T>& W = work<T>();
+    if (desc.smoother == ST_SMOOTH_JACOBI) {  // the residual vector of the level is free during smoothing
+        launch_jacobi_smooth<T>(sd, l, op0<T>(), opc<T>(l), tr, W.b[l], W.x[l], W.dinv[l], W.r[l], steps, zero_init,
+                                (T)desc.smoother_omega, stream);
+        return;
+    }
     cudaEvent_t* ev = nullptr;
     if (at_on && l == 0 && l < (int)lv.size() - 1) {
         ev = at_ev + (zero_init ? 0 : 2 * kMaxSmooth);
@@ -818,7 +826,8 @@ void Mesh::vcycle_rec(int l, bool tr, int steps) {
     auto mark = [&](int k) {
         if (timing) cudaEventRecord(tev[l * 4 + k], stream);
     };
-    if (l == vt_first && W.d_vt && W.steps_uploaded == steps && !vt_failed) {
+    const bool vt_ok = desc.smoother == ST_SMOOTH_GMRES;  // the persistent tail smooths with GMRES only
+    if (vt_ok && l == vt_first && W.d_vt && W.steps_uploaded == steps && !vt_failed) {
         mark(0);
         if (launch_vtail<T>(sd, tr, W.d_vt, d_bar, stream) < 0) {
             // the cooperative launch was refused (for example not all blocks can be resident in
@@ -828,7 +837,7 @@ void Mesh::vcycle_rec(int l, bool tr, int steps) {
             if (getenv("ST_VERBOSE")) fprintf(stderr, "st: persistent coarse tail refused; one launch per phase\n");
         }
     }
-    if (l == vt_first && W.d_vt && W.steps_uploaded == steps && !vt_failed) {
+    if (vt_ok && l == vt_first && W.d_vt && W.steps_uploaded == steps && !vt_failed) {
         if (timing) {
             cudaEvent_t e;
             cudaEventCreate(&e);
@@ -1517,6 +1526,8 @@ void st_mesh_desc_default(st_mesh_desc* d) {
     d->max_levels = 0;
     d->coarsening = ST_COARSEN_SEMI;
     d->device = 0;
+    d->smoother = ST_SMOOTH_GMRES;
+    d->smoother_omega = 0.5;
 }
 
 void st_options_default(st_options* o) {

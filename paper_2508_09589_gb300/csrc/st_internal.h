@@ -207,6 +207,11 @@ template <typename T>
 void launch_prolong(const Geom& gf, const Geom& gc, int kind, int sd, const T* xc, T* xf, cudaStream_t s);
 
 // Jacobi-GMRES smoother on one level (w2: second scratch vector for the fused FP32 steps).
+// `sweeps` damped Jacobi sweeps x += omega D^-1 (b - A x) (A^T if tr) on level lvl, the first
+// one from x = 0 when zero_init (then x = omega D^-1 b); r is scratch for the residual.
+template <typename T>
+void launch_jacobi_smooth(int sd, int lvl, const OpL0<T>& o0, const OpLc<T>& oc, bool tr, const T* b, T* x,
+                          const T* dinv, T* r, int sweeps, bool zero_init, T omega, cudaStream_t s);
 template <typename T>
 void launch_smooth(int sd, int lvl, const OpL0<T>& o0, const OpLc<T>& oc, bool tr, const T* b, T* x,
                    const T* dinv, Basis<T> U, T* w, T* w2, int steps, bool zero_init, SmState* st, RedBuf rb,

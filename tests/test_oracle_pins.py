@@ -1008,3 +1008,21 @@ def test_jacobi_vcycle_contracts_and_single_level_is_two_smoothings():
     xc = np.linalg.solve(two[1].A.toarray(), Pt.T @ (b - A0 @ x1))
     x2 = O.jacobi_smooth(A0, b, x1 + Pt @ xc, 2, 0.7)
     np.testing.assert_allclose(O.vcycle(two, b, nsmooth=2, smoother="jacobi", omega=0.7), x2, rtol=1e-13, atol=1e-15)
+
+
+def test_jacobi_damping_half_keeps_a_space_time_vcycle_convergent():
+    """The reading of the default damping: on a space-time design (paper material, 40 x 24 x 20)
+    the stationary Jacobi-smoothed V-cycle (nu = 2) contracts with omega = 0.5 and diverges with
+    omega = 0.7."""
+    m = O.Mesh((40, 24), 20, mat=O.Material(), bc="patch_left", bc_width=0.3)
+    g = np.random.default_rng(100).random(m.elem_shape)
+    mg = O.build_mg(m, g, O.hierarchy(m, coarse_cap=300))
+    A = mg[0].A
+    f = O.assemble_source(m, O.source_fn("uniform", 1.0))
+    ratio = {}
+    for w in (0.5, 0.7):
+        x = np.zeros_like(f)
+        for _ in range(8):
+            x = x + O.vcycle(mg, f - A @ x, nsmooth=2, smoother="jacobi", omega=w)
+        ratio[w] = np.linalg.norm(f - A @ x) / np.linalg.norm(f)
+    assert ratio[0.5] < 0.05 and ratio[0.7] > 100.0, ratio
