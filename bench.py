@@ -617,7 +617,7 @@ def design_loop(args):
     and warm-started solves; one untimed iteration, then args.design_iters timed ones (wall time
     per iteration, with its forward, adjoint and filter + MMA shares)."""
     from paper_2508_09589_gb300 import Mesh, TopOpt, options, source
-    w = W.WORKLOADS[args.workload]
+    w = W.WORKLOADS[args.design_workload or args.workload]
     mesh = Mesh(w.ns, w.nt, material=w.material, bc=w.bc, bc_width=w.bc_width, tau=w.tau)
     shape = tuple(reversed(w.ns)) if w.extruded else (w.nt,) + tuple(reversed(w.ns))
     to = TopOpt(mesh, np.full(shape, 0.5), "extruded" if w.extruded else "spacetime", vf=0.3)
@@ -628,7 +628,8 @@ def design_loop(args):
     sec = statistics.median(st["seconds"] for st in its)
     fwd = statistics.median(st["forward"]["seconds"] for st in its)
     adj = statistics.median(st["adjoint"]["seconds"] for st in its)
-    out = {"mesh": list(w.ns) + [w.nt], "design_vars": int(np.prod(shape)), "iterations_timed": len(its),
+    out = {"workload": w.name, "mesh": list(w.ns) + [w.nt], "design_vars": int(np.prod(shape)),
+           "iterations_timed": len(its),
            "ms_per_design_iteration": 1e3 * sec, "forward_ms": 1e3 * fwd, "adjoint_ms": 1e3 * adj,
            "filter_mma_rest_ms": 1e3 * (sec - fwd - adj),
            "outer_its_fwd": [st["forward"]["outer_its"] for st in its],
@@ -810,6 +811,8 @@ def main():
                     help="Poisson arrival rates as fractions of saturation (mixed precision)")
     ap.add_argument("--serve-fp64-loads", type=lambda v: [float(x) for x in v.split(",") if x], default=[0.7],
                     help="Poisson arrival rates as fractions of saturation (all-FP64)")
+    ap.add_argument("--design-workload", default="", choices=[""] + sorted(W.WORKLOADS),
+                    help="workload of the design-loop leg (default: --workload)")
     ap.add_argument("--design-iters", type=int, default=3,
                     help="timed design iterations of the optimisation loop after one warm-up (0 skips)")
     ap.add_argument("--smoother-variant", action="store_true",
