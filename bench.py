@@ -632,6 +632,9 @@ def design_loop(args):
            "iterations_timed": len(its),
            "ms_per_design_iteration": 1e3 * sec, "forward_ms": 1e3 * fwd, "adjoint_ms": 1e3 * adj,
            "filter_mma_rest_ms": 1e3 * (sec - fwd - adj),
+           "filter_ms": 1e3 * statistics.median(st["filter_seconds"] for st in its),
+           "projection_set_design_ms": 1e3 * statistics.median(st["design_seconds"] for st in its),
+           "mma_ms": 1e3 * statistics.median(st["mma_seconds"] for st in its),
            "outer_its_fwd": [st["forward"]["outer_its"] for st in its],
            "outer_its_adj": [st["adjoint"]["outer_its"] for st in its],
            "filter_cg_its": [st["filter_its"] for st in its],

@@ -405,6 +405,9 @@ typedef struct {
     st_stats adjoint;   /* the adjoint solve */
     int filter_its;     /* CG iterations of the three filter solves together */
     double seconds;     /* host wall time of the iteration */
+    double filter_seconds;  /* of which: the three filter solves */
+    double design_seconds;  /* projection and st_set_design */
+    double mma_seconds;     /* volume sum and the MMA update */
 } st_topopt_stats;
 typedef struct st_topopt st_topopt;
 enum { ST_TO_GAMMA = 0, ST_TO_GAMMA_TILDE = 1, ST_TO_GAMMA_BAR = 2, ST_TO_DPHI = 3, ST_TO_DCHI = 4 };

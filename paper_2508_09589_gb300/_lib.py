@@ -92,7 +92,8 @@ class TopOptParams(C.Structure):
 class TopOptStats(C.Structure):
     _fields_ = [("iteration", C.c_int), ("phi", C.c_double), ("chi", C.c_double), ("lam", C.c_double),
                 ("change", C.c_double), ("forward", Stats), ("adjoint", Stats), ("filter_its", C.c_int),
-                ("seconds", C.c_double)]
+                ("seconds", C.c_double), ("filter_seconds", C.c_double), ("design_seconds", C.c_double),
+                ("mma_seconds", C.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("forward", "adjoint")}

@@ -8,8 +8,9 @@
 // of the objective and the constraint.  The subproblem is solved through its dual: for a
 // multiplier lam the minimiser is x_j = (sqrt(P) L + sqrt(Q) U) / (sqrt(P) + sqrt(Q)) clipped to
 // [alpha, beta] with P = p0 + lam p1, Q = q0 + lam q1; lam = 0 when the approximated constraint
-// holds there, else its root by doubling and bisection on the host (each trial one kernel and a
-// deterministic block-partial sum), capped at lam_max (the most feasible point).
+// holds there, else its root to 1e-15 relative by doubling and Illinois regula falsi on the host
+// (each trial one kernel and a deterministic block-partial sum), capped at the first power of two
+// at or above lam_max (the most feasible point).
 #include <math.h>
 
 #include <algorithm>
@@ -203,23 +204,49 @@ st_status st_mma_update(st_mma* h, int it, double* x, const double* df0, double 
     double lam = 0.0, g = 0.0;
     if (!g_of(0.0, g)) return ST_ERR_CUDA;
     if (g > 0.0) {
-        double lo = 0.0, hi = 1.0;
-        for (;;) {
-            if (!g_of(hi, g)) return ST_ERR_CUDA;
-            if (!(g > 0.0) || hi >= h->pr.lam_max) break;
-            lo = hi;
-            hi *= 2.0;
+        // the bracket: powers of two from 1 up to the first at or above lam_max.  When the
+        // approximated constraint still fails there, the root search would end at that power
+        // (g decreases in lam), so it is tested first and taken at once.
+        double cap = 1.0;
+        while (cap < h->pr.lam_max) cap *= 2.0;
+        double gcap = 0.0;
+        if (!g_of(cap, gcap)) return ST_ERR_CUDA;
+        if (gcap > 0.0) {
+            lam = cap;
+        } else {
+            double lo = 0.0, hi = 1.0, glo = g, ghi = 0.0;
+            for (;;) {
+                if (!g_of(hi, ghi)) return ST_ERR_CUDA;
+                if (!(ghi > 0.0)) break;
+                lo = hi;
+                glo = ghi;
+                hi *= 2.0;
+            }
+            // root of g in (lo, hi] to 1e-15 relative: regula falsi with the Illinois
+            // modification (the value kept at an end twice in a row is halved), falling back to
+            // the midpoint when the secant point leaves the bracket
+            int side = 0;
+            for (int k = 0; k < 400 && hi - lo > 1e-15 * hi; ++k) {
+                double mid = hi - ghi * (hi - lo) / (ghi - glo);
+                if (!(mid > lo && mid < hi)) mid = 0.5 * (lo + hi);
+                if (mid <= lo || mid >= hi) break;
+                double gm = 0.0;
+                if (!g_of(mid, gm)) return ST_ERR_CUDA;
+                if (gm > 0.0) {
+                    lo = mid;
+                    glo = gm;
+                    if (side < 0) ghi *= 0.5;
+                    side = -1;
+                } else {
+                    hi = mid;
+                    ghi = gm;
+                    if (gm == 0.0) break;
+                    if (side > 0) glo *= 0.5;
+                    side = 1;
+                }
+            }
+            lam = hi;
         }
-        while (hi - lo > 1e-15 * hi) {
-            const double mid = 0.5 * (lo + hi);
-            if (mid <= lo || mid >= hi) break;
-            if (!g_of(mid, g)) return ST_ERR_CUDA;
-            if (g > 0.0)
-                lo = mid;
-            else
-                hi = mid;
-        }
-        lam = hi;
     }
     st::k_mma_final<<<blocks, st::kMmaThreads, 0, s>>>(n, lam, x, h->a);
     st::note_launch(s);

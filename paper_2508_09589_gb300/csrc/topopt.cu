@@ -228,12 +228,25 @@ st_status st_topopt_step(st_topopt* h, const st_source* q, const st_options* o, 
     };
     int its = 0;
     st_status r;
+    // host wall time of a part (every part ends with a stream synchronisation)
+    auto since = [](std::chrono::steady_clock::time_point a) {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - a).count();
+    };
+    auto filter = [&](const double* in, double* out) {
+        const auto tf = std::chrono::steady_clock::now();
+        const st_status fr =
+            soft(st::filter(mm, in, out, n, ST_MEM_DEVICE, p.r_x, p.r_t, p.filter_rtol, p.filter_max_it, &its));
+        S.filter_its += its;
+        S.filter_seconds += since(tf);
+        return fr;
+    };
     // design chain: gamma~ = F gamma, gamma_bar = H(gamma~), H'(gamma~)
-    r = soft(st::filter(mm, h->gamma, h->gt, n, ST_MEM_DEVICE, p.r_x, p.r_t, p.filter_rtol, p.filter_max_it, &its));
-    if (r != ST_OK) return r;
-    S.filter_its += its;
+    if ((r = filter(h->gamma, h->gt)) != ST_OK) return r;
+    const auto td = std::chrono::steady_clock::now();
     st::launch_heaviside(n, h->gt, h->gb, h->dh, p.beta, p.eta, s);
     if ((r = st_set_design(h->mesh, h->gb, h->layout, n, ST_MEM_DEVICE)) != ST_OK) return r;
+    cudaStreamSynchronize(s);
+    S.design_seconds = since(td);
     // state, objective and adjoint
     st_options opt;
     st_options_default(&opt);
@@ -250,10 +263,9 @@ st_status st_topopt_step(st_topopt* h, const st_source* q, const st_options* o, 
     if ((r = st_sensitivities(h->mesh, h->tmp, n, ST_MEM_DEVICE)) != ST_OK) return r;
     st::k_to_scale<<<blocks, st::kToThreads, 0, s>>>(n, p.obj_scale / phi1, h->dh, h->tmp, h->tmp);
     st::note_launch(s);
-    r = soft(st::filter(mm, h->tmp, h->df0, n, ST_MEM_DEVICE, p.r_x, p.r_t, p.filter_rtol, p.filter_max_it, &its));
-    if (r != ST_OK) return r;
-    S.filter_its += its;
+    if ((r = filter(h->tmp, h->df0)) != ST_OK) return r;
     // chi = mean(gamma_bar) / v_f - 1 (uniform elements) and d chi / d gamma = F (H' / (v_f N))
+    const auto tm = std::chrono::steady_clock::now();
     st::k_to_sum<<<blocks, st::kToThreads, 0, s>>>(n, h->gb, h->part);
     st::note_launch(s);
     double vol = 0.0;
@@ -261,10 +273,10 @@ st_status st_topopt_step(st_topopt* h, const st_source* q, const st_options* o, 
     const double chi = vol / (p.vf * (double)n) - 1.0;
     st::k_to_scale<<<blocks, st::kToThreads, 0, s>>>(n, 1.0 / (p.vf * (double)n), h->dh, nullptr, h->tmp);
     st::note_launch(s);
-    r = soft(st::filter(mm, h->tmp, h->dg1, n, ST_MEM_DEVICE, p.r_x, p.r_t, p.filter_rtol, p.filter_max_it, &its));
-    if (r != ST_OK) return r;
-    S.filter_its += its;
+    S.mma_seconds = since(tm);
+    if ((r = filter(h->tmp, h->dg1)) != ST_OK) return r;
     // MMA step on gamma in [0, 1]
+    const auto tu = std::chrono::steady_clock::now();
     if (cudaMemcpyAsync(h->gprev, h->gamma, n * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return fail(ST_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
     double lam = 0.0;
@@ -274,6 +286,7 @@ st_status st_topopt_step(st_topopt* h, const st_source* q, const st_options* o, 
     st::note_launch(s);
     double change = 0.0;
     if ((r = h->reduce(blocks, true, change)) != ST_OK) return r;
+    S.mma_seconds += since(tu);
     h->it += 1;
     h->phi1 = phi1;
     S.iteration = h->it;

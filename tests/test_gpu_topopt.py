@@ -1,9 +1,11 @@
 """The design loop on the device (st_topopt_*, Sec. 3.3) against the oracle's design iteration:
 iteration by iteration from the GPU's own designs (objective, constraint, the gradients MMA
-receives and the next design), for an extruded and a space-time design; a longer run on a
+receives and the next design), for an extruded and a space-time design and for Example 2's
+all-walls problem with the moving Gaussian source; a longer run on a
 larger mesh that must meet the volume constraint and beat the homogeneous design; and the
 argument and state checks."""
 import ctypes as C
+import math
 
 import numpy as np
 import pytest
@@ -24,15 +26,27 @@ def _lib():
     assert torch.cuda.is_available()
 
 
-@pytest.mark.parametrize("layout,precision", [("extruded", "mixed"), ("spacetime", "mixed"), ("extruded", "fp64")])
-def test_design_iterations_match_the_oracle(layout, precision):
+# Example 2 (Sec. 2.3.2): all walls cold, the moving Gaussian source, a space-time design
+EX2 = dict(q0=1.0, a=0.05, b=0.25, f=math.pi)
+
+
+@pytest.mark.parametrize("layout,precision,example",
+                         [("extruded", "mixed", 1), ("spacetime", "mixed", 1), ("extruded", "fp64", 1),
+                          ("spacetime", "mixed", 2)])
+def test_design_iterations_match_the_oracle(layout, precision, example):
     from paper_2508_09589_gb300 import TopOpt
-    om = O.Mesh((24, 20), 12, mat=MAT, bc="patch_left", bc_width=0.1, tau=20.0)
-    vf, r_x, r_t = 0.3, 2.4 / 20, 2.4 * 20.0 / 12
+    if example == 1:
+        om = O.Mesh((24, 20), 12, mat=MAT, bc="patch_left", bc_width=0.1, tau=20.0)
+        src_o, src_g = dict(source="uniform", q0=1.0), dict(kind="uniform", q0=1.0)
+    else:
+        om = O.Mesh((24, 24), 12, mat=MAT, bc="all_walls", bc_width=0.1, tau=2.0)
+        src_o = dict(source="gaussian", center=(0.5, 0.5), **EX2)
+        src_g = dict(kind="gaussian", **EX2)
+    vf, r_x, r_t = 0.3, 2.4 / om.ns[1], 2.4 * om.tau / om.nt
     shape = tuple(reversed(om.ns)) if layout == "extruded" else om.elem_shape
     g0 = np.full(shape, 0.5)
     g0 += 0.05 * np.random.default_rng(5).standard_normal(shape)  # break the symmetry a little
-    sol0 = O.forward(om, np.clip(g0, 0, 1), "uniform", 1.0)
+    sol0 = O.forward(om, np.clip(g0, 0, 1), **src_o)
     rt = parity_rtol(sol0.A, sol0.s, sol0.f)
     gm = gpu_mesh(om, coarse_dof_cap=300)
     to = TopOpt(gm, g0, layout, vf=vf, r_x=r_x, r_t=r_t, filter_rtol=1e-13)
@@ -40,9 +54,9 @@ def test_design_iterations_match_the_oracle(layout, precision):
     g = np.clip(g0, 0.0, 1.0)
     np.testing.assert_array_equal(to.get("gamma"), g)
     for it in range(1, 5):
-        st = to.step(rtol=rt, precision=precision, max_it=400, allow_not_converged=True)
+        st = to.step(rtol=rt, precision=precision, max_it=400, allow_not_converged=True, **src_g)
         assert st["forward"]["rel_res"] <= 10 * rt and st["adjoint"]["rel_res"] <= 10 * rt
-        g_next, d = O.topopt_step(om, g, hist, vf, r_x, r_t)
+        g_next, d = O.topopt_step(om, g, hist, vf, r_x, r_t, **src_o)
         assert st["iteration"] == it
         np.testing.assert_allclose(st["phi"], d["phi"], rtol=1e-9)
         assert abs(st["chi"] - d["chi"]) < 1e-10
