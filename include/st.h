@@ -361,7 +361,7 @@ typedef struct st_mma st_mma;
 void st_mma_params_default(st_mma_params* p);
 /* Device state for n variables on the current device (previous two iterates, asymptotes,
  * subproblem terms: 10 n doubles).  p NULL: the defaults.  ST_ERR_ARG for n < 1 or parameters
- * outside (s0 > 0, incr >= 1, 0 < decr <= 1, move > 0, raa > 0, lam_max > 1); ST_ERR_OOM. */
+ * outside (s0 > 0, incr >= 1, 0 < decr <= 1, move > 0, raa > 0, lam_max > 1, all finite); ST_ERR_OOM. */
 st_status st_mma_create(long long n, const st_mma_params* p, st_mma** out);
 st_status st_mma_destroy(st_mma* h);
 /* One MMA iteration it (1, 2, 3, ... in order; the asymptote rule uses the two previous

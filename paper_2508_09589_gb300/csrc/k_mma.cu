@@ -138,7 +138,8 @@ st_status st_mma_create(long long n, const st_mma_params* p, st_mma** out) {
     else
         st_mma_params_default(&h->pr);
     if (!(h->pr.s0 > 0) || !(h->pr.incr >= 1) || !(h->pr.decr > 0 && h->pr.decr <= 1) || !(h->pr.move > 0) ||
-        !(h->pr.raa > 0) || !(h->pr.lam_max > 1)) {
+        !(h->pr.raa > 0) || !(h->pr.lam_max > 1) || !std::isfinite(h->pr.lam_max) || !std::isfinite(h->pr.incr) ||
+        !std::isfinite(h->pr.s0) || !std::isfinite(h->pr.move) || !std::isfinite(h->pr.raa)) {
         delete h;
         return ST_ERR_ARG;
     }

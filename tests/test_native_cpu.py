@@ -111,3 +111,24 @@ def test_full_coarsening_planner_matches_oracle(L, ns, nt, cap):
                          coarse_dof_cap=cap, coarsening="full")
     assert [(tuple(L_.ns), L_.nt, L_.to_next) for L_ in ref] == [(g["ns"], g["nt"], g["to_next"]) for g in got]
     assert all(g["to_next"] in ("full", "") for g in got)
+
+
+def test_optimiser_loop_and_reference_argument_checks_without_a_gpu(L):
+    """Host-side argument checks of the MMA, the design loop, the BDF1 reference and the smoother
+    option, each refused before any device work."""
+    import ctypes as C
+    from paper_2508_09589_gb300 import _lib as LB, mesh_desc, plan_hierarchy, STError
+    h = C.c_void_p()
+    assert L.st_mma_create(0, None, C.byref(h)) == -1
+    for field, bad in (("decr", 1.5), ("lam_max", float("inf")), ("move", float("nan")), ("s0", 0.0)):
+        p = LB.MmaParams()
+        L.st_mma_params_default(C.byref(p))
+        setattr(p, field, bad)
+        assert L.st_mma_create(10, C.byref(p), C.byref(h)) == -1, field
+    g = np.full(16, 0.5)
+    assert L.st_topopt_create(None, None, C.c_void_p(g.ctypes.data), 0, 16, 0, C.byref(h)) == -1
+    d = mesh_desc((8, 8), 0)
+    assert L.st_bdf1_create(C.byref(d), C.byref(h)) == -1
+    with pytest.raises(STError):
+        plan_hierarchy((64, 64), 8, smoother="jacobi", smoother_omega=1.5)
+    assert len(plan_hierarchy((64, 64), 8, smoother="jacobi", smoother_omega=0.5)) >= 2
