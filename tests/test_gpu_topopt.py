@@ -1,7 +1,7 @@
 """The design loop on the device (st_topopt_*, Sec. 3.3) against the oracle's design iteration:
 iteration by iteration from the GPU's own designs (objective, constraint, the gradients MMA
 receives and the next design), for an extruded and a space-time design and for Example 2's
-all-walls problem with the moving Gaussian source; a longer run on a
+all-walls problem with the moving Gaussian source, and for an extruded 3-D design; a longer run on a
 larger mesh that must meet the volume constraint and beat the homogeneous design; and the
 argument and state checks."""
 import ctypes as C
@@ -32,11 +32,14 @@ EX2 = dict(q0=1.0, a=0.05, b=0.25, f=math.pi)
 
 @pytest.mark.parametrize("layout,precision,example",
                          [("extruded", "mixed", 1), ("spacetime", "mixed", 1), ("extruded", "fp64", 1),
-                          ("spacetime", "mixed", 2)])
+                          ("spacetime", "mixed", 2), ("extruded", "mixed", 3)])
 def test_design_iterations_match_the_oracle(layout, precision, example):
     from paper_2508_09589_gb300 import TopOpt
     if example == 1:
         om = O.Mesh((24, 20), 12, mat=MAT, bc="patch_left", bc_width=0.1, tau=20.0)
+        src_o, src_g = dict(source="uniform", q0=1.0), dict(kind="uniform", q0=1.0)
+    elif example == 3:  # 3+1-D: an extruded design on a 3-D spatial mesh
+        om = O.Mesh((8, 6, 6), 6, mat=MAT, bc="patch_left", bc_width=0.3, tau=5.0)
         src_o, src_g = dict(source="uniform", q0=1.0), dict(kind="uniform", q0=1.0)
     else:
         om = O.Mesh((24, 24), 12, mat=MAT, bc="all_walls", bc_width=0.1, tau=2.0)
