@@ -70,3 +70,26 @@ def test_design_loop_meets_the_volume_and_beats_the_homogeneous_design():
     hom = O.forward(m, np.full((16, 16), vf), "uniform", 1.0)
     phi_hom = O.pnorm(m, hom.s, 20)[0]
     assert phi_opt < 0.5 * phi_hom, (phi_opt, phi_hom)
+
+
+def test_example2_time_varying_design_beats_the_extruded_one():
+    """Example 2 (Sec. 2.3.2; all walls cold, a Gaussian source circling the centre): forty
+    iterations from gamma = eta.  Both designs meet the volume and beat the homogeneous design;
+    the space-time design, free to move its material with the source, reaches a p-norm
+    temperature below a fifth of the extruded design's (the oracle gives 0.0076 against 0.038)."""
+    import math
+    m = O.Mesh((16, 16), 16, mat=MAT, bc="all_walls", bc_width=0.1, tau=2.0)
+    src = dict(source="gaussian", q0=1.0, a=0.05, b=0.25, f=math.pi, center=(0.5, 0.5))
+    vf, r_x, r_t = 0.3, 2.4 / 16, 2.4 * 2.0 / 16
+    phi_hom = O.pnorm(m, O.forward(m, np.full((16, 16), vf), **src).s, 20)[0]
+    phi = {}
+    for layout, shape in (("extruded", (16, 16)), ("spacetime", m.elem_shape)):
+        g = np.full(shape, 0.5)
+        hist = O.TopOptHistory()
+        for _ in range(40):
+            g, _d = O.topopt_step(m, g, hist, vf, r_x, r_t, **src)
+        gb, _ = O.design_chain(m, g, r_x, r_t)
+        assert O.volume_constraint(gb, vf)[0] <= 1e-3
+        phi[layout] = O.pnorm(m, O.forward(m, gb, **src).s, 20)[0]
+    assert phi["extruded"] < 0.5 * phi_hom, (phi, phi_hom)
+    assert phi["spacetime"] < 0.2 * phi["extruded"], (phi, phi_hom)
