@@ -332,7 +332,8 @@ long long st_footprint_bytes(const st_mesh_desc* d, int precision, int restart) 
             bytes += ne * NV * 12;  // FP64 + FP32 element blocks
             if (sd == 2 && space_only) bytes += ne * 128;  // M, K rows of the marching kernels
         }
-        bytes += N * (long long)tsz * 16;  // b, x, r, dinv, w and 11 basis vectors
+        // b, x, r, dinv, w and, with the GMRES smoother, its 11 basis vectors
+        bytes += N * (long long)tsz * (d->smoother == ST_SMOOTH_JACOBI ? 5 : 16);
         nc = N;
         bool can_s = true;
         for (int q = 0; q < sd; ++q) can_s = can_s && n[q] % 2 == 0 && n[q] >= 4;

@@ -84,6 +84,9 @@ def test_footprint_model_and_argument_validation(L):
     b = footprint_bytes((128, 128), 64)
     c = footprint_bytes((64, 64), 64, precision="fp64")
     assert 0 < a < b and a < c
+    # a Jacobi-smoothed hierarchy keeps no Krylov basis on its levels
+    j = footprint_bytes((64, 64), 64, smoother="jacobi")
+    assert 0 < j < a
     with pytest.raises(STError):
         plan_hierarchy((64, 64), 0)
     with pytest.raises(STError):
