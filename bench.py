@@ -261,6 +261,11 @@ def run_native(args):
                 line["smoother_variant"] = smoother_variant(args)
             except Exception as e:  # noqa: BLE001
                 line["smoother_variant"] = {"error": f"{type(e).__name__}: {e}"}
+        if args.example2_iters > 0:
+            try:
+                line["example2_designs"] = example2_designs(args)
+            except Exception as e:  # noqa: BLE001
+                line["example2_designs"] = {"error": f"{type(e).__name__}: {e}"}
         if args.design_iters > 0:
             try:
                 line["design_loop"] = design_loop(args)
@@ -611,6 +616,44 @@ def smoother_variant(args):
     return out
 
 
+def example2_designs(args):
+    """Example 2 (Sec. 2.3.2) through the optimisation loop: all walls cold, the moving Gaussian
+    source (sigma 0.05, radius 0.25, angular frequency pi, tau = 2), v_f = 0.3, an n^2 x n mesh;
+    args.example2_iters iterations from gamma = 0.5 at the outer tolerance 1e-5 for an extruded and
+    for a space-time design, each final physical design re-evaluated at 1e-8 on a fresh mesh; the
+    p-norm temperatures against the homogeneous design of the same volume."""
+    from paper_2508_09589_gb300 import Mesh, TopOpt, options, source
+    n = args.example2_size
+    kw = dict(tau=2.0, material=dict(C_ins=0.5, C_con=1.0, k_ins=1e-3, k_con=1.0, p_c=1, p_k=3), bc="all_walls",
+              bc_width=0.1)
+    src = source("gaussian", 1.0, 0.05, 0.25, math.pi)
+    tight = options(rtol=1e-8, max_it=300)
+
+    def pnorm_of(design, layout):
+        e = Mesh((n, n), n, **kw)
+        e.set_design(design, layout)
+        e.solve_forward(src, tight)
+        phi, _ = e.solve_adjoint("pnorm", P=20, opts=tight)
+        e.close()
+        return phi
+    phi_h = pnorm_of(np.full((n, n), 0.3), "extruded")
+    out = {"mesh": [n, n, n], "iterations": args.example2_iters, "phi_homogeneous": phi_h}
+    for layout, shape in (("extruded", (n, n)), ("spacetime", (n, n, n))):
+        m = Mesh((n, n), n, **kw)
+        to = TopOpt(m, np.full(shape, 0.5), layout, vf=0.3)
+        t0 = time.perf_counter()
+        for _ in range(args.example2_iters):
+            to.step(src, options(rtol=1e-5, max_it=200))
+        sec = (time.perf_counter() - t0) / max(1, args.example2_iters)
+        gb = to.get("gamma_bar")
+        to.close()
+        m.close()
+        phi = pnorm_of(gb, layout)
+        out[layout] = {"phi": phi, "ratio_to_homogeneous": phi / phi_h, "chi": float(gb.mean() / 0.3 - 1.0),
+                       "s_per_design_iteration": sec}
+    return out
+
+
 def design_loop(args):
     """Design iterations of the optimisation loop (Sec. 3.3) on the headline workload's mesh and
     source: from the homogeneous design gamma = 0.5, v_f = 0.3, the paper's outer tolerance 1e-5
@@ -818,6 +861,9 @@ def main():
                     help="workload of the design-loop leg (default: --workload)")
     ap.add_argument("--design-iters", type=int, default=3,
                     help="timed design iterations of the optimisation loop after one warm-up (0 skips)")
+    ap.add_argument("--example2-iters", type=int, default=0,
+                    help="design iterations of the Example 2 leg (extruded against space-time designs; 0 skips)")
+    ap.add_argument("--example2-size", type=int, default=128, help="n of the Example 2 leg's n^2 x n mesh")
     ap.add_argument("--smoother-variant", action="store_true",
                     help="also time the damped-Jacobi smoother variant on the headline workload (off by default: "
                          "it does not reach 1e-8 there within 600 outer iterations)")
